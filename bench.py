@@ -1,0 +1,425 @@
+#!/usr/bin/env python3
+"""Throughput of the improved GenASM alignment path on GB300.
+
+One step = the whole hot path over one batch resident in HBM: 2-bit packing
+of the ASCII reads and references, then the batched alignment launch (window
+driver, pattern masks, distance calculation with row early termination,
+compressed table, traceback, CIGAR runs and distances). The default workload
+is 10,000 pairs of 10 kb PacBio-like reads (seed 2), W=64, O=24, k=64.
+
+Prints one JSON line (rank 0). ``--impl reference`` times the CPU oracle
+(plain GenASM, four-vector table) on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+from pathlib import Path
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+import numpy as np  # noqa: E402
+
+METRIC = "10kb pairs/s & Gbases/s: batched+served vs plain GPU GenASM, bit-exact; p99 latency"
+WORKLOAD = 2
+W, O, K = 64, 24, 64
+OPS_PER_CELL = 6  # 2 funnel shifts + 4 three-input logic ops per 64-bit DP cell
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--pairs", type=int, default=10_000, help="pairs per GPU (workload 2 has 10,000)")
+    ap.add_argument("--no-plain", action="store_true", help="skip timing the plain one-pair-per-block kernel")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
+    ap.add_argument("--workers", type=int, default=0, help="processes for input generation")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def make_inputs(pairs: int, rank: int, workers: int):
+    from paper_2203_15561_gb300 import datagen
+    ids = range(rank * pairs, (rank + 1) * pairs)
+    w = workers or min(16, host_cores())
+    return datagen.make_batch(WORKLOAD, pair_ids=ids, workers=w)
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (the reference arm and the cpu_baseline key)
+# ---------------------------------------------------------------------------
+
+def time_oracle(batch, seconds: float, max_pairs: int | None = None):
+    """Times the oracle on growing prefixes of `batch` until one takes about
+    `seconds`; returns (pairs/s, pairs, seconds, threads)."""
+    import oracle
+    n = 16
+    limit = batch.n_pairs if max_pairs is None else min(max_pairs, batch.n_pairs)
+    while True:
+        n = min(n, limit)
+        sub = batch.subset(range(n))
+        t0 = time.perf_counter()
+        r = oracle.align(sub, W=W, O=O, k=K, variant="unimproved")
+        dt = time.perf_counter() - t0
+        if dt >= seconds or n >= limit:
+            return n / dt, n, dt, r.threads
+        n = int(n * min(8.0, max(2.0, 1.2 * seconds / max(dt, 1e-3))))
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    batch = make_inputs(max(args.pairs // 10, 64), 0, args.workers)
+    # each step: the oracle on a bounded sample of the workload
+    per_step = max(8, int(time_oracle(batch, 2.0, max_pairs=batch.n_pairs)[0] * 4.0))
+    per_step = min(per_step, batch.n_pairs)
+    sub = batch.subset(range(per_step))
+    import oracle
+    for _ in range(args.warmup):
+        oracle.align(sub, W=W, O=O, k=K)
+    times = []
+    threads = 0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        r = oracle.align(sub, W=W, O=O, k=K)
+        times.append(time.perf_counter() - t0)
+        threads = r.threads
+    tot = sum(times)
+    value = per_step * args.steps / tot
+    bases = int(sub.read_len.sum())
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic",
+        "config": {"workload": "long-10kb-10000pairs (10 kb PacBio-like reads, 12% error, seed 2)",
+                   "W": W, "O": O, "k": K, "sample_pairs_per_step": per_step},
+        "gbases_per_s": bases * args.steps / tot / 1e9,
+        "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": threads, "kind": "oracle",
+                         "sample": f"first {per_step} pairs of the workload per step, plain GenASM "
+                                   f"four-vector oracle (C, -O2), {threads} host threads"},
+        "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines: list[str] = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+            time.sleep(0.3)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import paper_2203_15561_gb300 as ga
+    from paper_2203_15561_gb300.pipeline import DeviceBatch
+
+    ga.lib()
+    batch = make_inputs(args.pairs, rank, args.workers)
+    n = batch.n_pairs
+    read_bases = batch.read_bases
+    db = DeviceBatch(batch, W=W, O=O, k=K, device=str(dev))
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        if ws == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum_over_ranks(x: float) -> float:
+        if ws == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        return float(t.item())
+
+    # DP cells of the run (rows 0..d_min of every window): the algorithmic work.
+    db.run("batched", stats=True)
+    res = db.results()
+    assert (res.status == 0).all(), "alignment failed on the benchmark workload"
+    cells = int(res.cells.sum())
+    windows = int(res.n_windows.sum())
+
+    # ---- batched (the headline) ----
+    for _ in range(args.warmup):
+        db.run("batched", stats=False)
+    torch.cuda.synchronize(dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize(dev)
+    launches0 = ga.ga_launch_count()
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    smi_index = vis.split(",")[local] if vis and vis.split(",")[local].strip().isdigit() else str(local)
+    with ClockSampler(smi_index) as clk:
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_start.record(stream)
+        for a, b, c in ev:
+            a.record(stream)
+            db.pack()
+            b.record(stream)
+            db.align("batched", stats=False)
+            c.record(stream)
+        t_end.record(stream)
+        torch.cuda.synchronize(dev)
+    barrier()
+    launches = ga.ga_launch_count() - launches0
+    total_ms = max_over_ranks(t_start.elapsed_time(t_end))
+    align_ms = statistics.mean(b.elapsed_time(c) for a, b, c in ev)
+    pack_ms = statistics.mean(a.elapsed_time(b) for a, b, c in ev)
+    ms_per_step = total_ms / args.steps
+    total_pairs = sum_over_ranks(n)
+    value = total_pairs / (ms_per_step * 1e-3)
+    gbases = sum_over_ranks(read_bases) / (ms_per_step * 1e-3) / 1e9
+
+    # ---- parity spot check of the timed configuration against the oracle ----
+    res2 = db.results()
+    same = bool(np.array_equal(res2.dist, res.dist) and np.array_equal(res2.n_runs, res.n_runs))
+
+    # ---- plain one-pair-per-block kernel on the same batch ----
+    plain = None
+    if not args.no_plain:
+        for _ in range(max(1, args.warmup)):
+            db.run("plain", stats=False)
+        torch.cuda.synchronize(dev)
+        barrier()
+        p0 = torch.cuda.Event(enable_timing=True)
+        p1 = torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        for _ in range(args.steps):
+            db.run("plain", stats=False)
+        p1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+        plain_ms = max_over_ranks(p0.elapsed_time(p1)) / args.steps
+        rp = db.results()
+        plain = {"pairs_per_s": total_pairs / (plain_ms * 1e-3), "ms_per_step": plain_ms,
+                 "bit_exact_vs_batched": bool(np.array_equal(rp.dist, res.dist)
+                                              and np.array_equal(rp.n_runs, res.n_runs))}
+
+    # ---- roofline of the alignment kernel (integer ALU bound) ----
+    peaks = ga.ga_measure_int_peak()
+    peak_mix = peaks[2]
+    achieved = cells * OPS_PER_CELL / (align_ms * 1e-3)
+    roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_mix / 1e12,
+                "unit": "Tops/s (int32)", "frac": achieved / peak_mix, "traffic": None,
+                "kernel": "align_batched_kernel (+ 3 tiny LPT-sort kernels in the same call)",
+                "peak_source": "measured on this GPU by ga_measure_int_peak (DC cell mix: 2 SHF + 4 LOP3)",
+                "peak_lop3": peaks[0] / 1e12, "peak_shf": peaks[1] / 1e12,
+                "algorithmic_ops_per_launch": cells * OPS_PER_CELL, "cells_per_launch": cells,
+                "windows_per_launch": windows, "align_ms": align_ms, "pack_ms": pack_ms}
+    prof = ROOT / "profiles" / "align_batched_traffic.json"
+    if prof.exists():
+        try:
+            roofline["traffic"] = json.loads(prof.read_text()).get("bytes_per_launch")
+        except (ValueError, OSError):
+            pass
+
+    # ---- end to end through the C ABI with host buffers ----
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, batch, db, dev, stream, ga, barrier, max_over_ranks, sum_over_ranks)
+
+    # ---- CPU oracle baseline (rank 0, N = 1 only) ----
+    cpu = None
+    if not args.no_cpu and rank == 0 and ws == 1:
+        pps, npairs, secs, threads = time_oracle(batch, args.cpu_seconds)
+        cpu = {"value": pps, "unit": "pairs/s", "cores": threads, "kind": "oracle",
+               "sample": f"first {npairs} pairs of the workload ({secs:.1f} s), plain GenASM "
+                         f"four-vector oracle (C, -O2) over {threads} host threads"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": "long-10kb-10000pairs (10 kb PacBio-like reads, 12% error, 5% flanks, seed 2)",
+                       "W": W, "O": O, "k": K, "pairs_per_gpu": n, "read_bases_per_gpu": read_bases,
+                       "kernel": "batched (persistent, LPT work queue)",
+                       "l2": "no flush: each step streams 210 MB of ASCII input (> 126 MB L2) and "
+                             "writes ~0.5 GB of CIGAR runs, which evicts the previous step's data"},
+            "gbases_per_s": gbases,
+            "plain": plain,
+            "batched_vs_plain": (value / plain["pairs_per_s"]) if plain else None,
+            "p99_latency_ms": None,
+            "bit_exact_repeat": same,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def run_e2e(args, batch, db, dev, stream, ga, barrier, max_over_ranks, sum_over_ranks):
+    """Host ASCII in pinned memory -> H2D -> pack -> align -> compact CIGAR -> D2H."""
+    import torch
+
+    n = batch.n_pairs
+    h_reads = torch.from_numpy(batch.reads).pin_memory()
+    h_refs = torch.from_numpy(batch.refs).pin_memory()
+    meta = [torch.from_numpy(np.ascontiguousarray(a).view(np.int64 if a.dtype == np.uint64 else np.int32)).pin_memory()
+            for a in (batch.read_off // 4, batch.ref_off // 4, batch.read_len, batch.ref_len, db.h_cigar_off)]
+    d_meta = [db.read_off, db.ref_off, db.read_len, db.ref_len, db.cigar_off]
+    cws = ga.ga_cigar_compact_workspace_size(n)
+    d_cws = torch.empty(max(cws, 1), dtype=torch.uint8, device=dev)
+    d_out_off = torch.empty(n + 1, dtype=torch.int64, device=dev)
+    cap = int(db.h_cigar_off[-1])
+    d_out = torch.empty(max(cap, 1), dtype=torch.int32, device=dev)
+    h_dist = torch.empty(n, dtype=torch.int32).pin_memory()
+    h_status = torch.empty(n, dtype=torch.int32).pin_memory()
+    h_off = torch.empty(n + 1, dtype=torch.int64).pin_memory()
+    h_out = torch.empty(max(cap, 1), dtype=torch.int32).pin_memory()
+    h2d = h_reads.numel() + h_refs.numel() + sum(m.numel() * m.element_size() for m in meta)
+    d2h_total = 0
+
+    def step():
+        nonlocal d2h_total
+        db.ascii_reads.copy_(h_reads, non_blocking=True)
+        db.ascii_refs.copy_(h_refs, non_blocking=True)
+        for d, h in zip(d_meta, meta):
+            d.copy_(h, non_blocking=True)
+        db.pack()
+        db.align("batched", stats=False)
+        ga.ga_cigar_compact(db.cigar, db.cigar_off, db.n_runs, n, d_out, cap, d_out_off, d_cws, cws)
+        h_dist.copy_(db.dist[:n], non_blocking=True)
+        h_status.copy_(db.status[:n], non_blocking=True)
+        h_off.copy_(d_out_off, non_blocking=True)
+        torch.cuda.current_stream(dev).synchronize()
+        total = int(h_off[n])
+        h_out[:total].copy_(d_out[:total], non_blocking=True)
+        torch.cuda.current_stream(dev).synchronize()
+        d2h_total += 4 * n * 2 + 8 * (n + 1) + 4 * total
+
+    for _ in range(max(1, args.warmup)):
+        step()
+    d2h_total = 0
+    barrier()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    torch.cuda.synchronize(dev)
+    dt = max_over_ranks(time.perf_counter() - t0)
+    barrier()
+    # the compacted CIGARs must match the per-pair buffers
+    hr = db.results()
+    offs = h_off.numpy()
+    ok = all(np.array_equal(h_out.numpy()[offs[p]:offs[p + 1]].view(np.uint32), hr.runs(p))
+             for p in range(0, n, max(1, n // 64)))
+    return {"value": sum_over_ranks(n) * args.steps / dt, "unit": "pairs/s",
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h_total // args.steps),
+            "ms_per_step": 1e3 * dt / args.steps, "compacted_cigar_matches": bool(ok)}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

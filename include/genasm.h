@@ -1,0 +1,221 @@
+/*
+ * genasm.h - C ABI of the GB300 (sm_103a) library for the improved GenASM
+ * alignment path of arXiv 2203.15561 ("Algorithmic Improvement and GPU
+ * Acceleration of the GenASM Algorithm").
+ *
+ * What the library computes, per (read, reference) pair: windowed GenASM
+ * distance calculation (DC) and traceback (TB), with the paper's three
+ * improvements (Sec. I, key ideas (1)-(3)): only the AND of the four DP
+ * vectors is kept per entry, error rows past the first one that holds the
+ * solution are not computed, and entries the traceback cannot reach are not
+ * stored. Outputs are the edit distance and the CIGAR of the greedy windowed
+ * alignment. The recurrence and the window rule are those of the GenASM paper
+ * the authors build on (Cali et al., MICRO 2020); where both papers are
+ * silent the library uses these readings:
+ *   - 0 = active bit; bit j of a W-bit vector stands for the pattern suffix
+ *     P[wp-1-j ..], text consumed right to left;
+ *   - each window is anchored at its first read and reference base and leaves
+ *     the reference end free;
+ *   - traceback priority: match > substitution > insertion > deletion;
+ *   - a window that does not reach the read end commits W-O read or
+ *     reference bases, whichever count reaches W-O first; the last window
+ *     runs until the read is used up.
+ *
+ * Conventions shared by every entry point:
+ *   - d_* arguments are device pointers, h_* host pointers. The caller owns
+ *     every buffer; no entry point frees or keeps a pointer after it returns,
+ *     except the server handle, which owns its own pool.
+ *   - Work is enqueued on `stream` and is asynchronous unless stated; results
+ *     are valid once the stream has reached that point.
+ *   - Return value: GA_OK (0) or a negative GA_E* code. On an error nothing
+ *     was enqueued and no output is meaningful.
+ *   - Sequences are 2-bit packed: A=0, C=1, G=2, T=3; base x of a sequence
+ *     lives in byte (offset + x/4) at bits 2*(x%4) and 2*(x%4)+1. Every
+ *     sequence starts on a byte boundary; *_off are byte offsets.
+ *   - CIGAR runs are uint32 (length << 4 | op) with BAM op codes. 'I' is a
+ *     read base missing from the reference, 'D' a reference base missing from
+ *     the read. The distance is #X + #I + #D.
+ */
+#ifndef GENASM_H
+#define GENASM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* ga_stream_t; /* = cudaStream_t; NULL = legacy default stream */
+
+/* Return codes. */
+#define GA_OK 0
+#define GA_EINVAL (-1)     /* bad argument (sizes, W/O/k, NULL pointer) */
+#define GA_ENOSPC (-2)     /* workspace or capacity too small */
+#define GA_ECUDA (-3)      /* a CUDA call failed; see ga_last_cuda_error() */
+#define GA_ETIMEDOUT (-4)  /* a bounded wait ran out */
+#define GA_ENOMEM (-5)     /* the server's memory budget cannot hold the request */
+#define GA_EAGAIN (-6)     /* nothing ready yet (server poll) */
+
+/* Per-pair status written to d_status. */
+#define GA_PAIR_OK 0
+#define GA_PAIR_EXCEEDS_K 1   /* some window's minimum edit count is above k */
+#define GA_PAIR_CIGAR_FULL 2  /* the pair's CIGAR capacity was too small */
+#define GA_PAIR_TB_STUCK 3    /* internal: traceback found no edge */
+
+/* CIGAR op codes (BAM). */
+#define GA_OP_INS 1
+#define GA_OP_DEL 2
+#define GA_OP_MATCH 7 /* '=' */
+#define GA_OP_SUBST 8 /* 'X' */
+
+/* Largest window the kernels support (one 64-bit vector per DP entry). */
+#define GA_MAX_W 64
+
+/* Library version, e.g. 100 for 0.1.0. */
+int ga_version(void);
+
+/* Human-readable name of a GA_* return code. Never NULL. */
+const char* ga_strerror(int code);
+
+/* Last CUDA error code seen by the library on this host thread (0 if none). */
+int ga_last_cuda_error(void);
+
+/*
+ * ga_pack_2bit - 2-bit packer (the input stage of the hot path).
+ * Packs n_chars ASCII bytes d_ascii[0..n_chars) into d_packed[0..ceil(n/4)).
+ * A/a->0, C/c->1, G/g->2, T/t->3; any other byte packs as 0 and, if
+ * d_n_invalid is not NULL, is counted into *d_n_invalid (added to, not
+ * reset). A sequence whose ASCII offset is a multiple of 4 starts at packed
+ * byte offset/4. Buffers must not overlap.
+ * Errors: GA_EINVAL for NULL buffers with n_chars > 0.
+ */
+int ga_pack_2bit(const uint8_t* d_ascii, uint64_t n_chars, uint8_t* d_packed,
+                 uint32_t* d_n_invalid, ga_stream_t stream);
+
+/*
+ * ga_workspace_size - bytes of device workspace ga_align_batch needs for
+ * n_pairs pairs with window W, overlap O and error cap k on the current
+ * device. The size depends on n_pairs and the device's SM count, not on the
+ * sequence lengths. Errors: GA_EINVAL for bad W/O/k or NULL bytes_out.
+ */
+int ga_workspace_size(uint32_t n_pairs, int W, int O, int k, size_t* bytes_out);
+
+/*
+ * Tuning of the batched kernel. ga_align_batch uses the library's defaults
+ * (or what ga_autotune stored for this device); ga_align_batch_tuned takes an
+ * explicit choice. All fields 0 = default.
+ *   lanes_per_pair : lanes that run one pair's DC wavefront (1 error row per
+ *                    lane per pass): 8, 16 or 32.
+ *   pairs_per_block: pairs resident per thread block.
+ *   table_rows     : error rows of each window's table kept in shared memory;
+ *                    rows above spill to the workspace.
+ *   lpt            : 1 = hand out pairs longest read first, -1 = in index
+ *                    order (0 = default, longest first).
+ */
+typedef struct {
+  int lanes_per_pair;
+  int pairs_per_block;
+  int table_rows;
+  int lpt;
+} ga_tuning;
+
+/*
+ * ga_workspace_size_tuned - workspace bytes ga_align_batch_tuned needs with
+ * `tuning` (NULL = defaults, same as ga_workspace_size).
+ * Errors: GA_EINVAL for bad W/O/k, an unsupported tuning or NULL bytes_out.
+ */
+int ga_workspace_size_tuned(uint32_t n_pairs, int W, int O, int k, const ga_tuning* tuning,
+                            size_t* bytes_out);
+
+/*
+ * ga_cigar_compact - CIGAR writer, final pass: gathers the runs the alignment
+ * wrote at per-pair capacities (d_cigar, d_cigar_off, d_n_runs as given to
+ * ga_align_batch) into one dense array. d_out_off (n_pairs + 1 uint64)
+ * receives the exclusive prefix sum of d_n_runs, so pair p's runs land at
+ * d_out[d_out_off[p] .. d_out_off[p+1]) and d_out_off[n_pairs] is the total.
+ * If the total exceeds out_cap, d_out_off is still written and nothing is
+ * copied; the caller reads d_out_off[n_pairs] to size a retry.
+ * Workspace: ga_cigar_compact_workspace_size(n_pairs) bytes.
+ * Errors: GA_EINVAL (NULL buffers), GA_ENOSPC (workspace), GA_ECUDA.
+ * (The paper gives no output format; the CIGAR is the traceback's ops as
+ * BAM-coded runs, merged across windows.)
+ */
+int ga_cigar_compact(const uint32_t* d_cigar, const uint64_t* d_cigar_off, const uint32_t* d_n_runs,
+                     uint32_t n_pairs, uint32_t* d_out, uint64_t out_cap, uint64_t* d_out_off,
+                     void* d_workspace, size_t ws_bytes, ga_stream_t stream);
+int ga_cigar_compact_workspace_size(uint32_t n_pairs, size_t* bytes_out);
+
+/*
+ * ga_launch_count - number of kernels the library has launched in this
+ * process (all threads, all devices). Used to account for device work.
+ */
+uint64_t ga_launch_count(void);
+
+/*
+ * ga_measure_int_peak - measures, on the current device, the throughput of
+ * the 32-bit integer instructions the distance calculation is made of. Runs
+ * three synchronous microbenchmarks (each a few tens of milliseconds) on the
+ * given stream: out[0] = 3-input logic (LOP3) ops/s, out[1] = funnel-shift
+ * (SHF) ops/s, out[2] = ops/s of the DC cell mix (2 funnel shifts + 4 LOP3 per
+ * 64-bit cell). This is the roofline denominator for the integer-bound DC.
+ * Errors: GA_EINVAL for NULL out, GA_ECUDA.
+ */
+int ga_measure_int_peak(double out[3], ga_stream_t stream);
+
+/*
+ * ga_align_batch - align n_pairs (read, reference) pairs (GenASM DC + TB over
+ * windows of W bases with overlap O, error cap k), batched: one persistent
+ * launch over a device work queue, pairs handed out longest first.
+ *
+ * Inputs (device): d_reads/d_refs packed bases; d_read_off/d_ref_off byte
+ * offsets (uint64, n_pairs); d_read_len/d_ref_len lengths in bases (uint32).
+ * Outputs (device, n_pairs each): d_dist edit distance (-1 unless status OK);
+ * d_status GA_PAIR_*; d_ref_consumed reference bases the alignment spans
+ * (-1 on failure); d_n_runs CIGAR runs written. d_cigar receives pair p's
+ * runs at d_cigar[d_cigar_off[p] ..]; d_cigar_off has n_pairs + 1 entries and
+ * pair p may write at most d_cigar_off[p+1] - d_cigar_off[p] runs
+ * (read_len + ref_len is always enough).
+ * Optional statistics (NULL to skip): d_n_windows windows per pair, d_cells
+ * the sum over windows of wt * (d_min + 1), the DP entries of rows 0..d_min.
+ * Workspace: d_workspace of ws_bytes >= ga_workspace_size(...); its contents
+ * on entry do not matter. Concurrent calls need separate workspaces.
+ * Limits: 1 <= W <= 64, 0 <= O < W, k >= 0 (k >= W means no cap).
+ * Errors: GA_EINVAL, GA_ENOSPC (workspace too small), GA_ECUDA.
+ */
+int ga_align_batch(const uint8_t* d_reads, const uint64_t* d_read_off, const uint32_t* d_read_len,
+                   const uint8_t* d_refs, const uint64_t* d_ref_off, const uint32_t* d_ref_len,
+                   uint32_t n_pairs, int W, int O, int k,
+                   int32_t* d_dist, int32_t* d_status, int32_t* d_ref_consumed,
+                   uint32_t* d_cigar, const uint64_t* d_cigar_off, uint32_t* d_n_runs,
+                   uint32_t* d_n_windows, uint64_t* d_cells,
+                   void* d_workspace, size_t ws_bytes, ga_stream_t stream);
+
+/* ga_align_batch with an explicit tuning (NULL = defaults). Same contract. */
+int ga_align_batch_tuned(const uint8_t* d_reads, const uint64_t* d_read_off,
+                         const uint32_t* d_read_len, const uint8_t* d_refs,
+                         const uint64_t* d_ref_off, const uint32_t* d_ref_len,
+                         uint32_t n_pairs, int W, int O, int k,
+                         int32_t* d_dist, int32_t* d_status, int32_t* d_ref_consumed,
+                         uint32_t* d_cigar, const uint64_t* d_cigar_off, uint32_t* d_n_runs,
+                         uint32_t* d_n_windows, uint64_t* d_cells,
+                         void* d_workspace, size_t ws_bytes, const ga_tuning* tuning,
+                         ga_stream_t stream);
+
+/*
+ * ga_align_plain - the same alignment as ga_align_batch, computed by the
+ * plain GPU GenASM form: one pair per thread block, one launch, pairs in
+ * index order, no work queue, no tuning, no workspace. Outputs are identical
+ * to ga_align_batch's. Errors: GA_EINVAL, GA_ECUDA.
+ */
+int ga_align_plain(const uint8_t* d_reads, const uint64_t* d_read_off, const uint32_t* d_read_len,
+                   const uint8_t* d_refs, const uint64_t* d_ref_off, const uint32_t* d_ref_len,
+                   uint32_t n_pairs, int W, int O, int k,
+                   int32_t* d_dist, int32_t* d_status, int32_t* d_ref_consumed,
+                   uint32_t* d_cigar, const uint64_t* d_cigar_off, uint32_t* d_n_runs,
+                   uint32_t* d_n_windows, uint64_t* d_cells, ga_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GENASM_H */

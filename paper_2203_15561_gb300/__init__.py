@@ -1,0 +1,215 @@
+"""GB300 (sm_103a) library for the improved GenASM alignment path of
+arXiv 2203.15561: windowed GenASM distance calculation and traceback with the
+paper's three improvements (Sec. I, key ideas (1)-(3)), giving the edit
+distance and CIGAR of every (read, reference) pair.
+
+This module is a thin ctypes binding over ``libgenasm_gb300.so``; every
+function has the name and argument order of the C entry point declared in
+``include/genasm.h`` and only marshals arguments: device buffers may be given
+as CUDA ``torch.Tensor`` objects (their ``data_ptr()`` is passed) or as raw
+integer addresses, ``stream=None`` means torch's current CUDA stream. A
+non-zero return code raises ``GenasmError``. All computation happens in the
+library's CUDA kernels; there is no CPU fallback, and a missing library is an
+error.
+"""
+from __future__ import annotations
+
+import ctypes
+import threading
+
+from ._build import LIB, build as build_library  # noqa: F401
+
+GA_OK = 0
+GA_EINVAL = -1
+GA_ENOSPC = -2
+GA_ECUDA = -3
+GA_ETIMEDOUT = -4
+GA_ENOMEM = -5
+GA_EAGAIN = -6
+
+GA_PAIR_OK = 0
+GA_PAIR_EXCEEDS_K = 1
+GA_PAIR_CIGAR_FULL = 2
+GA_PAIR_TB_STUCK = 3
+
+GA_OP_INS = 1
+GA_OP_DEL = 2
+GA_OP_MATCH = 7
+GA_OP_SUBST = 8
+OP_CHARS = {GA_OP_INS: "I", GA_OP_DEL: "D", GA_OP_MATCH: "=", GA_OP_SUBST: "X"}
+
+GA_MAX_W = 64
+
+
+class GenasmError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        msg = lib().ga_strerror(code).decode()
+        if code == GA_ECUDA:
+            msg += f" (cudaError {lib().ga_last_cuda_error()})"
+        super().__init__(f"{where}: {msg} [{code}]")
+
+
+class ga_tuning(ctypes.Structure):
+    _fields_ = [("lanes_per_pair", ctypes.c_int), ("pairs_per_block", ctypes.c_int),
+                ("table_rows", ctypes.c_int), ("lpt", ctypes.c_int)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+_vp = ctypes.c_void_p
+_i = ctypes.c_int
+_u32 = ctypes.c_uint32
+_u64 = ctypes.c_uint64
+_sz = ctypes.c_size_t
+
+_ALIGN_ARGS = [_vp, _vp, _vp, _vp, _vp, _vp, _u32, _i, _i, _i,
+               _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
+
+
+def lib():
+    """The loaded CUDA library (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not LIB.exists():
+                raise RuntimeError(f"CUDA library {LIB} is missing: run paper_2203_15561_gb300.build_library()"
+                                   " (or __graft_entry__.build()) first")
+            so = ctypes.CDLL(str(LIB))
+            so.ga_version.restype = _i
+            so.ga_strerror.restype = ctypes.c_char_p
+            so.ga_strerror.argtypes = [_i]
+            so.ga_last_cuda_error.restype = _i
+            so.ga_pack_2bit.restype = _i
+            so.ga_pack_2bit.argtypes = [_vp, _u64, _vp, _vp, _vp]
+            so.ga_workspace_size.restype = _i
+            so.ga_workspace_size.argtypes = [_u32, _i, _i, _i, ctypes.POINTER(_sz)]
+            so.ga_workspace_size_tuned.restype = _i
+            so.ga_workspace_size_tuned.argtypes = [_u32, _i, _i, _i, ctypes.POINTER(ga_tuning),
+                                                   ctypes.POINTER(_sz)]
+            so.ga_launch_count.restype = _u64
+            so.ga_cigar_compact.restype = _i
+            so.ga_cigar_compact.argtypes = [_vp, _vp, _vp, _u32, _vp, _u64, _vp, _vp, _sz, _vp]
+            so.ga_cigar_compact_workspace_size.restype = _i
+            so.ga_cigar_compact_workspace_size.argtypes = [_u32, ctypes.POINTER(_sz)]
+            so.ga_measure_int_peak.restype = _i
+            so.ga_measure_int_peak.argtypes = [ctypes.POINTER(ctypes.c_double), _vp]
+            so.ga_align_batch.restype = _i
+            so.ga_align_batch.argtypes = _ALIGN_ARGS + [_vp, _sz, _vp]
+            so.ga_align_batch_tuned.restype = _i
+            so.ga_align_batch_tuned.argtypes = _ALIGN_ARGS + [_vp, _sz, ctypes.POINTER(ga_tuning), _vp]
+            so.ga_align_plain.restype = _i
+            so.ga_align_plain.argtypes = _ALIGN_ARGS + [_vp]
+            _lib = so
+        return _lib
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _check(rc: int, where: str) -> int:
+    if rc != GA_OK:
+        raise GenasmError(rc, where)
+    return rc
+
+
+def ga_version() -> int:
+    return lib().ga_version()
+
+
+def ga_pack_2bit(d_ascii, n_chars: int, d_packed, d_n_invalid=None, stream=None) -> int:
+    return _check(lib().ga_pack_2bit(_ptr(d_ascii), n_chars, _ptr(d_packed), _ptr(d_n_invalid),
+                                     _stream(stream)), "ga_pack_2bit")
+
+
+def ga_workspace_size(n_pairs: int, W: int, O: int, k: int) -> int:
+    out = _sz(0)
+    _check(lib().ga_workspace_size(n_pairs, W, O, k, ctypes.byref(out)), "ga_workspace_size")
+    return int(out.value)
+
+
+def ga_workspace_size_tuned(n_pairs: int, W: int, O: int, k: int, tuning=None) -> int:
+    out = _sz(0)
+    t = ctypes.byref(tuning) if tuning is not None else None
+    _check(lib().ga_workspace_size_tuned(n_pairs, W, O, k, t, ctypes.byref(out)),
+           "ga_workspace_size_tuned")
+    return int(out.value)
+
+
+def ga_cigar_compact_workspace_size(n_pairs: int) -> int:
+    out = _sz(0)
+    _check(lib().ga_cigar_compact_workspace_size(n_pairs, ctypes.byref(out)),
+           "ga_cigar_compact_workspace_size")
+    return int(out.value)
+
+
+def ga_cigar_compact(d_cigar, d_cigar_off, d_n_runs, n_pairs: int, d_out, out_cap: int, d_out_off,
+                     d_workspace, ws_bytes: int, stream=None) -> int:
+    return _check(lib().ga_cigar_compact(_ptr(d_cigar), _ptr(d_cigar_off), _ptr(d_n_runs), n_pairs,
+                                         _ptr(d_out), out_cap, _ptr(d_out_off), _ptr(d_workspace),
+                                         ws_bytes, _stream(stream)), "ga_cigar_compact")
+
+
+def ga_launch_count() -> int:
+    return int(lib().ga_launch_count())
+
+
+def ga_measure_int_peak(stream=None) -> tuple[float, float, float]:
+    """(LOP3 ops/s, SHF ops/s, DC-cell-mix ops/s) measured on the current device."""
+    out = (ctypes.c_double * 3)()
+    _check(lib().ga_measure_int_peak(out, _stream(stream)), "ga_measure_int_peak")
+    return float(out[0]), float(out[1]), float(out[2])
+
+
+def _align_args(d_reads, d_read_off, d_read_len, d_refs, d_ref_off, d_ref_len, n_pairs, W, O, k,
+                d_dist, d_status, d_ref_consumed, d_cigar, d_cigar_off, d_n_runs, d_n_windows,
+                d_cells):
+    return [_ptr(d_reads), _ptr(d_read_off), _ptr(d_read_len), _ptr(d_refs), _ptr(d_ref_off),
+            _ptr(d_ref_len), n_pairs, W, O, k, _ptr(d_dist), _ptr(d_status), _ptr(d_ref_consumed),
+            _ptr(d_cigar), _ptr(d_cigar_off), _ptr(d_n_runs), _ptr(d_n_windows), _ptr(d_cells)]
+
+
+def ga_align_batch(d_reads, d_read_off, d_read_len, d_refs, d_ref_off, d_ref_len, n_pairs, W, O, k,
+                   d_dist, d_status, d_ref_consumed, d_cigar, d_cigar_off, d_n_runs,
+                   d_n_windows, d_cells, d_workspace, ws_bytes, stream=None) -> int:
+    a = _align_args(d_reads, d_read_off, d_read_len, d_refs, d_ref_off, d_ref_len, n_pairs, W, O, k,
+                    d_dist, d_status, d_ref_consumed, d_cigar, d_cigar_off, d_n_runs, d_n_windows,
+                    d_cells)
+    return _check(lib().ga_align_batch(*a, _ptr(d_workspace), ws_bytes, _stream(stream)),
+                  "ga_align_batch")
+
+
+def ga_align_batch_tuned(d_reads, d_read_off, d_read_len, d_refs, d_ref_off, d_ref_len, n_pairs,
+                         W, O, k, d_dist, d_status, d_ref_consumed, d_cigar, d_cigar_off, d_n_runs,
+                         d_n_windows, d_cells, d_workspace, ws_bytes, tuning=None,
+                         stream=None) -> int:
+    a = _align_args(d_reads, d_read_off, d_read_len, d_refs, d_ref_off, d_ref_len, n_pairs, W, O, k,
+                    d_dist, d_status, d_ref_consumed, d_cigar, d_cigar_off, d_n_runs, d_n_windows,
+                    d_cells)
+    t = ctypes.byref(tuning) if tuning is not None else None
+    return _check(lib().ga_align_batch_tuned(*a, _ptr(d_workspace), ws_bytes, t, _stream(stream)),
+                  "ga_align_batch_tuned")
+
+
+def ga_align_plain(d_reads, d_read_off, d_read_len, d_refs, d_ref_off, d_ref_len, n_pairs, W, O, k,
+                   d_dist, d_status, d_ref_consumed, d_cigar, d_cigar_off, d_n_runs,
+                   d_n_windows, d_cells, stream=None) -> int:
+    a = _align_args(d_reads, d_read_off, d_read_len, d_refs, d_ref_off, d_ref_len, n_pairs, W, O, k,
+                    d_dist, d_status, d_ref_consumed, d_cigar, d_cigar_off, d_n_runs, d_n_windows,
+                    d_cells)
+    return _check(lib().ga_align_plain(*a, _stream(stream)), "ga_align_plain")

@@ -1,0 +1,193 @@
+// C ABI of the library: argument checks, tuning resolution and launches.
+// Every entry point validates its arguments before enqueuing anything and
+// maps CUDA failures to GA_ECUDA (the CUDA code is kept per host thread).
+#include <cstdint>
+#include <cstring>
+
+#include <cuda_runtime.h>
+
+#include "genasm.h"
+#include "genasm_internal.h"
+
+namespace {
+
+thread_local int g_last_cuda = 0;
+
+int cuda_fail(cudaError_t e) {
+  g_last_cuda = static_cast<int>(e);
+  return e == cudaSuccess ? GA_OK : GA_ECUDA;
+}
+
+bool bad_wok(int W, int O, int k) { return W < 1 || W > GA_MAX_W || O < 0 || O >= W || k < 0; }
+
+int fill_params(const uint8_t* d_reads, const uint64_t* d_read_off, const uint32_t* d_read_len,
+                const uint8_t* d_refs, const uint64_t* d_ref_off, const uint32_t* d_ref_len,
+                uint32_t n_pairs, int W, int O, int k, int32_t* d_dist, int32_t* d_status,
+                int32_t* d_ref_consumed, uint32_t* d_cigar, const uint64_t* d_cigar_off,
+                uint32_t* d_n_runs, uint32_t* d_n_windows, uint64_t* d_cells, ga::AlignParams* p) {
+  if (bad_wok(W, O, k)) return GA_EINVAL;
+  if (n_pairs > 0 && (!d_reads || !d_read_off || !d_read_len || !d_refs || !d_ref_off ||
+                      !d_ref_len || !d_dist || !d_status || !d_ref_consumed || !d_cigar ||
+                      !d_cigar_off || !d_n_runs))
+    return GA_EINVAL;
+  p->reads = d_reads;
+  p->read_off = d_read_off;
+  p->read_len = d_read_len;
+  p->refs = d_refs;
+  p->ref_off = d_ref_off;
+  p->ref_len = d_ref_len;
+  p->n_pairs = n_pairs;
+  p->W = W;
+  p->O = O;
+  p->kmax = k < W ? k : W;
+  p->dist = d_dist;
+  p->status = d_status;
+  p->ref_consumed = d_ref_consumed;
+  p->cigar = d_cigar;
+  p->cigar_off = d_cigar_off;
+  p->n_runs = d_n_runs;
+  p->n_windows = d_n_windows;
+  p->cells = d_cells;
+  return GA_OK;
+}
+
+int resolve(int W, int O, int k, const ga_tuning* t, ga::BatchPlan* plan) {
+  int G = 0, ppb = 0, entries = 0, lpt = 1;
+  cudaError_t e = ga::default_tuning(W, O, k, &G, &ppb, &entries, &lpt);
+  if (e != cudaSuccess) return cuda_fail(e);
+  if (t) {
+    if (t->lanes_per_pair) G = t->lanes_per_pair;
+    if (t->pairs_per_block) ppb = t->pairs_per_block;
+    if (t->table_rows) entries = t->table_rows * (W - O + 1);
+    if (t->lpt) lpt = t->lpt > 0 ? 1 : 0;
+    if ((G != 8 && G != 16 && G != 32) || ppb < 1 || ppb * G > 1024 || t->table_rows < 0)
+      return GA_EINVAL;
+  }
+  e = ga::resolve_plan(W, O, k, G, ppb, entries, lpt, plan);
+  if (e == cudaErrorInvalidValue || e == cudaErrorInvalidConfiguration) {
+    cudaGetLastError();
+    return GA_EINVAL;
+  }
+  return cuda_fail(e);
+}
+
+}  // namespace
+
+extern "C" {
+
+int ga_version(void) { return 100; }
+
+const char* ga_strerror(int code) {
+  switch (code) {
+    case GA_OK: return "ok";
+    case GA_EINVAL: return "invalid argument";
+    case GA_ENOSPC: return "workspace or capacity too small";
+    case GA_ECUDA: return "CUDA error";
+    case GA_ETIMEDOUT: return "bounded wait timed out";
+    case GA_ENOMEM: return "memory budget exceeded";
+    case GA_EAGAIN: return "nothing ready";
+    default: return "unknown error";
+  }
+}
+
+int ga_last_cuda_error(void) { return g_last_cuda; }
+
+int ga_pack_2bit(const uint8_t* d_ascii, uint64_t n_chars, uint8_t* d_packed,
+                 uint32_t* d_n_invalid, ga_stream_t stream) {
+  if (n_chars > 0 && (!d_ascii || !d_packed)) return GA_EINVAL;
+  return cuda_fail(ga::launch_pack(d_ascii, n_chars, d_packed, d_n_invalid,
+                                   reinterpret_cast<cudaStream_t>(stream)));
+}
+
+int ga_workspace_size(uint32_t n_pairs, int W, int O, int k, size_t* bytes_out) {
+  if (!bytes_out || bad_wok(W, O, k)) return GA_EINVAL;
+  ga::BatchPlan plan{};
+  const int rc = resolve(W, O, k, nullptr, &plan);
+  if (rc != GA_OK) return rc;
+  *bytes_out = ga::workspace_layout(n_pairs, plan).total;
+  return GA_OK;
+}
+
+int ga_workspace_size_tuned(uint32_t n_pairs, int W, int O, int k, const ga_tuning* tuning,
+                            size_t* bytes_out) {
+  if (!bytes_out || bad_wok(W, O, k)) return GA_EINVAL;
+  ga::BatchPlan plan{};
+  const int rc = resolve(W, O, k, tuning, &plan);
+  if (rc != GA_OK) return rc;
+  *bytes_out = ga::workspace_layout(n_pairs, plan).total;
+  return GA_OK;
+}
+
+uint64_t ga_launch_count(void) { return ga::launch_count(); }
+
+int ga_cigar_compact_workspace_size(uint32_t n_pairs, size_t* bytes_out) {
+  if (!bytes_out) return GA_EINVAL;
+  *bytes_out = ga::compact_workspace_bytes(n_pairs);
+  return GA_OK;
+}
+
+int ga_cigar_compact(const uint32_t* d_cigar, const uint64_t* d_cigar_off, const uint32_t* d_n_runs,
+                     uint32_t n_pairs, uint32_t* d_out, uint64_t out_cap, uint64_t* d_out_off,
+                     void* d_workspace, size_t ws_bytes, ga_stream_t stream) {
+  if (!d_out_off || (n_pairs > 0 && (!d_cigar || !d_cigar_off || !d_n_runs || !d_out)))
+    return GA_EINVAL;
+  if (!d_workspace || ws_bytes < ga::compact_workspace_bytes(n_pairs)) return GA_ENOSPC;
+  return cuda_fail(ga::launch_compact(d_cigar, d_cigar_off, d_n_runs, n_pairs, d_out, out_cap,
+                                      d_out_off, d_workspace, reinterpret_cast<cudaStream_t>(stream)));
+}
+
+int ga_measure_int_peak(double out[3], ga_stream_t stream) {
+  if (!out) return GA_EINVAL;
+  return cuda_fail(ga::measure_int_peak(out, reinterpret_cast<cudaStream_t>(stream)));
+}
+
+int ga_align_batch_tuned(const uint8_t* d_reads, const uint64_t* d_read_off,
+                         const uint32_t* d_read_len, const uint8_t* d_refs,
+                         const uint64_t* d_ref_off, const uint32_t* d_ref_len, uint32_t n_pairs,
+                         int W, int O, int k, int32_t* d_dist, int32_t* d_status,
+                         int32_t* d_ref_consumed, uint32_t* d_cigar, const uint64_t* d_cigar_off,
+                         uint32_t* d_n_runs, uint32_t* d_n_windows, uint64_t* d_cells,
+                         void* d_workspace, size_t ws_bytes, const ga_tuning* tuning,
+                         ga_stream_t stream) {
+  ga::AlignParams p{};
+  int rc = fill_params(d_reads, d_read_off, d_read_len, d_refs, d_ref_off, d_ref_len, n_pairs, W,
+                       O, k, d_dist, d_status, d_ref_consumed, d_cigar, d_cigar_off, d_n_runs,
+                       d_n_windows, d_cells, &p);
+  if (rc != GA_OK) return rc;
+  if (n_pairs == 0) return GA_OK;
+  ga::BatchPlan plan{};
+  rc = resolve(W, O, k, tuning, &plan);
+  if (rc != GA_OK) return rc;
+  const ga::WorkspaceLayout L = ga::workspace_layout(n_pairs, plan);
+  if (!d_workspace || ws_bytes < L.total) return GA_ENOSPC;
+  return cuda_fail(ga::launch_batched(p, plan, d_workspace, reinterpret_cast<cudaStream_t>(stream)));
+}
+
+int ga_align_batch(const uint8_t* d_reads, const uint64_t* d_read_off, const uint32_t* d_read_len,
+                   const uint8_t* d_refs, const uint64_t* d_ref_off, const uint32_t* d_ref_len,
+                   uint32_t n_pairs, int W, int O, int k, int32_t* d_dist, int32_t* d_status,
+                   int32_t* d_ref_consumed, uint32_t* d_cigar, const uint64_t* d_cigar_off,
+                   uint32_t* d_n_runs, uint32_t* d_n_windows, uint64_t* d_cells,
+                   void* d_workspace, size_t ws_bytes, ga_stream_t stream) {
+  return ga_align_batch_tuned(d_reads, d_read_off, d_read_len, d_refs, d_ref_off, d_ref_len,
+                              n_pairs, W, O, k, d_dist, d_status, d_ref_consumed, d_cigar,
+                              d_cigar_off, d_n_runs, d_n_windows, d_cells, d_workspace, ws_bytes,
+                              nullptr, stream);
+}
+
+int ga_align_plain(const uint8_t* d_reads, const uint64_t* d_read_off, const uint32_t* d_read_len,
+                   const uint8_t* d_refs, const uint64_t* d_ref_off, const uint32_t* d_ref_len,
+                   uint32_t n_pairs, int W, int O, int k, int32_t* d_dist, int32_t* d_status,
+                   int32_t* d_ref_consumed, uint32_t* d_cigar, const uint64_t* d_cigar_off,
+                   uint32_t* d_n_runs, uint32_t* d_n_windows, uint64_t* d_cells,
+                   ga_stream_t stream) {
+  ga::AlignParams p{};
+  const int rc = fill_params(d_reads, d_read_off, d_read_len, d_refs, d_ref_off, d_ref_len,
+                             n_pairs, W, O, k, d_dist, d_status, d_ref_consumed, d_cigar,
+                             d_cigar_off, d_n_runs, d_n_windows, d_cells, &p);
+  if (rc != GA_OK) return rc;
+  if (n_pairs > 0x7fffffffu) return GA_EINVAL;  // one block per pair
+  return cuda_fail(ga::launch_plain(p, reinterpret_cast<cudaStream_t>(stream)));
+}
+
+}  // extern "C"

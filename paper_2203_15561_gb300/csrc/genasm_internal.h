@@ -1,0 +1,76 @@
+// Internal launch interface between the C ABI (genasm_capi.cu) and the
+// kernels (genasm_align.cu, genasm_aux.cu). Not part of the public ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace ga {
+
+struct AlignParams {
+  const uint8_t* reads;
+  const uint64_t* read_off;
+  const uint32_t* read_len;
+  const uint8_t* refs;
+  const uint64_t* ref_off;
+  const uint32_t* ref_len;
+  uint32_t n_pairs;
+  int W, O, kmax;  // kmax = min(k, W): no window needs rows above W
+  int32_t* dist;
+  int32_t* status;
+  int32_t* ref_consumed;
+  uint32_t* cigar;
+  const uint64_t* cigar_off;
+  uint32_t* n_runs;
+  uint32_t* n_windows;  // optional
+  uint64_t* cells;      // optional
+};
+
+// Resolved tuning of the batched kernel.
+struct BatchPlan {
+  int lanes_per_pair;   // G
+  int pairs_per_block;  // groups per block
+  int table_entries;    // 64-bit table entries per group kept in shared memory
+  int lpt;              // longest-first hand-out
+  int blocks;           // persistent grid size
+  size_t smem_bytes;    // dynamic shared memory per block
+};
+
+// Workspace layout of the batched kernel (byte offsets).
+struct WorkspaceLayout {
+  size_t queue;   // uint32 counters (256 B)
+  size_t hist;    // uint32[kLptBuckets]
+  size_t order;   // uint32[n_pairs]
+  size_t spill;   // uint64[groups][kMaxRows * kMaxCols]
+  size_t total;
+};
+
+constexpr int kLptBuckets = 1024;
+
+WorkspaceLayout workspace_layout(uint32_t n_pairs, const BatchPlan& plan);
+
+// Kernel launches issued by the library (process-wide counter).
+uint64_t launch_count();
+void count_launches(uint64_t n);
+
+cudaError_t measure_int_peak(double out[3], cudaStream_t s);
+
+size_t compact_workspace_bytes(uint32_t n_pairs);
+cudaError_t launch_compact(const uint32_t* cigar, const uint64_t* cigar_off, const uint32_t* n_runs,
+                           uint32_t n, uint32_t* out, uint64_t out_cap, uint64_t* out_off, void* ws,
+                           cudaStream_t s);
+
+cudaError_t launch_pack(const uint8_t* ascii, uint64_t n, uint8_t* packed, uint32_t* n_invalid,
+                        cudaStream_t s);
+cudaError_t launch_plain(const AlignParams& p, cudaStream_t s);
+cudaError_t launch_batched(const AlignParams& p, const BatchPlan& plan, void* ws, cudaStream_t s);
+
+// Default tuning for (W, O, k) on the current device; fills G / pairs per
+// block / table entries / lpt. Returns cudaSuccess or the device query error.
+cudaError_t default_tuning(int W, int O, int k, int* G, int* ppb, int* table_entries, int* lpt);
+cudaError_t resolve_plan(int W, int O, int k, int G, int ppb, int table_entries, int lpt,
+                         BatchPlan* plan);
+
+}  // namespace ga

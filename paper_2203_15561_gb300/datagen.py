@@ -268,19 +268,30 @@ def make_pair(config: int, pair_id: int, seed: int | None = None) -> tuple[np.nd
     raise ValueError(f"no pair generator for workload {config}")
 
 
+def _make_chunk(args):
+    config, ids, seed = args
+    return [make_pair(config, int(p), seed) for p in ids]
+
+
 def make_batch(config: int, pair_ids: Sequence[int] | None = None, n_pairs: int | None = None,
-               seed: int | None = None) -> Batch:
+               seed: int | None = None, workers: int = 0) -> Batch:
     """Pairs of workload ``config``. By default all of its pairs; ``pair_ids``
-    selects a subset, ``n_pairs`` the first n."""
+    selects a subset, ``n_pairs`` the first n. ``workers`` > 1 draws the pairs
+    in that many spawned processes (the result does not depend on it)."""
     if pair_ids is None:
         n = CONFIG_N_PAIRS[config] if n_pairs is None else n_pairs
         pair_ids = range(n)
-    reads, refs = [], []
-    for p in pair_ids:
-        r, f = make_pair(config, int(p), seed)
-        reads.append(r)
-        refs.append(f)
-    return _assemble(reads, refs, list(pair_ids), CONFIG_NAMES[config])
+    ids = [int(p) for p in pair_ids]
+    if workers > 1 and len(ids) >= 4 * workers:
+        import concurrent.futures as cf
+        import multiprocessing as mp
+        step = (len(ids) + 4 * workers - 1) // (4 * workers)
+        chunks = [(config, ids[x:x + step], seed) for x in range(0, len(ids), step)]
+        with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+            pairs = [pr for part in ex.map(_make_chunk, chunks) for pr in part]
+    else:
+        pairs = _make_chunk((config, ids, seed))
+    return _assemble([r for r, _ in pairs], [f for _, f in pairs], ids, CONFIG_NAMES[config])
 
 
 @dataclasses.dataclass

@@ -1,0 +1,160 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Integer work: every output must be identical (distance, status, reference
+bases consumed, CIGAR runs, windows and DP-entry counts).
+"""
+from __future__ import annotations
+
+import random
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2203_15561_gb300 import datagen
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2203_15561_gb300 as ga  # noqa: E402
+from paper_2203_15561_gb300.pipeline import DeviceBatch  # noqa: E402
+
+
+def assert_same(batch, got, ref, label=""):
+    n = batch.n_pairs
+    for name in ("status", "dist", "ref_consumed", "n_runs"):
+        a = np.asarray(getattr(got, name)).astype(np.int64)
+        b = np.asarray(getattr(ref, name)).astype(np.int64)
+        bad = np.nonzero(a != b)[0]
+        assert bad.size == 0, f"{label} {name} differs at pairs {bad[:8]}: gpu {a[bad[:8]]} oracle {b[bad[:8]]}"
+    ok = np.asarray(ref.status) == 0
+    np.testing.assert_array_equal(np.asarray(got.n_windows)[ok], np.asarray(ref.n_windows)[ok])
+    np.testing.assert_array_equal(np.asarray(got.cells)[ok], np.asarray(ref.cells)[ok])
+    for p in range(n):
+        if not np.array_equal(got.runs(p), ref.runs(p)):
+            raise AssertionError(f"{label} pair {p}: cigar gpu {got.cigar_str(p)[:200]} oracle {ref.cigar_str(p)[:200]}")
+
+
+def run_gpu(batch, kernel="batched", W=64, O=24, k=64, tuning=None):
+    db = DeviceBatch(batch, W=W, O=O, k=k)
+    db.run(kernel=kernel, tuning=tuning)
+    return db.results()
+
+
+def edge_pairs(seed=0, n_random=300):
+    rnd = random.Random(seed)
+    rs = lambda L: "".join(rnd.choice("ACGT") for _ in range(L))
+    pairs = [("", ""), ("", "ACGT"), ("A", ""), ("ACGT" * 16, ""), ("A", "A"), ("A", "C"),
+             ("ACGT" * 16, "ACGT" * 16), ("ACGT" * 40, "ACGT" * 40)]
+    for L in (1, 2, 31, 32, 33, 40, 41, 63, 64, 65, 103, 104, 105, 127, 128, 129, 300):
+        s = rs(L)
+        pairs.append((s, s))
+        pairs.append((s, rs(L)))
+        pairs.append((s, s[: max(0, L - 7)]))
+        pairs.append((s[: max(1, L - 5)], s + rs(20)))
+    for _ in range(n_random):
+        m, n = rnd.randint(1, 400), rnd.randint(0, 450)
+        pairs.append((rs(m), rs(n)))
+    return pairs
+
+
+@pytest.mark.parametrize("kernel", ["plain", "batched"])
+def test_workload1_full(kernel):
+    b = datagen.make_batch(1)
+    assert_same(b, run_gpu(b, kernel), oracle.align(b), f"w1/{kernel}")
+
+
+@pytest.mark.parametrize("kernel", ["plain", "batched"])
+def test_edge_cases(kernel):
+    b = datagen.from_pairs(edge_pairs())
+    assert_same(b, run_gpu(b, kernel), oracle.align(b), f"edge/{kernel}")
+
+
+@pytest.mark.parametrize("W,O", [(64, 0), (64, 63), (32, 8), (17, 5), (1, 0), (2, 1), (40, 24)])
+def test_window_geometry(W, O):
+    b = datagen.from_pairs(edge_pairs(seed=W * 100 + O, n_random=120))
+    ref = oracle.align(b, W=W, O=O, k=64)
+    for kernel in ("plain", "batched"):
+        assert_same(b, run_gpu(b, kernel, W=W, O=O), ref, f"W{W}O{O}/{kernel}")
+
+
+@pytest.mark.parametrize("k", [0, 1, 5, 20, 33])
+def test_error_cap(k):
+    b = datagen.from_pairs(edge_pairs(seed=k, n_random=150))
+    ref = oracle.align(b, k=k)
+    assert (ref.status == oracle.STATUS_EXCEEDS_K).any()
+    for kernel in ("plain", "batched"):
+        assert_same(b, run_gpu(b, kernel, k=k), ref, f"k{k}/{kernel}")
+
+
+@pytest.mark.parametrize("G,ppb,rows", [(32, 1, 1), (32, 8, 2), (16, 4, 20), (8, 8, 40), (8, 2, 65),
+                                        (16, 16, 8), (32, 2, 65)])
+def test_tunings_identical(G, ppb, rows):
+    b = datagen.make_batch(4, pair_ids=range(40))
+    ref = oracle.align(b)
+    t = ga.ga_tuning(G, ppb, rows, 1)
+    assert_same(b, run_gpu(b, "batched", tuning=t), ref, f"G{G}/ppb{ppb}/rows{rows}")
+
+
+@pytest.mark.parametrize("config,ids", [(2, range(0, 24)), (3, range(100, 130)), (4, range(1000, 1060))])
+def test_long_workload_samples(config, ids):
+    b = datagen.make_batch(config, pair_ids=list(ids))
+    ref = oracle.align(b)
+    for kernel in ("plain", "batched"):
+        assert_same(b, run_gpu(b, kernel), ref, f"w{config}/{kernel}")
+
+
+def test_pack_matches_oracle():
+    rng = np.random.default_rng(0)
+    for n in (0, 1, 3, 4, 15, 16, 17, 1000, 4096 + 7):
+        a = rng.choice(np.frombuffer(b"ACGTacgtNn-", dtype=np.uint8), size=n)
+        want, bad = oracle.pack(a)
+        for off in (0, 1):  # aligned and unaligned source
+            buf = torch.zeros(n + 16, dtype=torch.uint8, device="cuda")
+            buf[off:off + n] = torch.from_numpy(a).cuda()
+            out = torch.zeros(max(1, (n + 3) // 4), dtype=torch.uint8, device="cuda")
+            cnt = torch.zeros(1, dtype=torch.int32, device="cuda")
+            ga.ga_pack_2bit(buf.data_ptr() + off, n, out, cnt)
+            torch.cuda.synchronize()
+            np.testing.assert_array_equal(out.cpu().numpy()[: (n + 3) // 4], want[: (n + 3) // 4])
+            assert int(cnt.item()) == bad
+
+
+def test_bad_arguments_rejected():
+    b = datagen.make_batch(1, pair_ids=range(4))
+    db = DeviceBatch(b)
+    for W, O, k in ((0, 0, 1), (65, 0, 1), (64, 64, 1), (64, -1, 1), (64, 24, -1)):
+        with pytest.raises(ga.GenasmError) as e:
+            ga.ga_align_plain(db.reads, db.read_off, db.read_len, db.refs, db.ref_off, db.ref_len, 4,
+                              W, O, k, db.dist, db.status, db.ref_consumed, db.cigar, db.cigar_off,
+                              db.n_runs, None, None)
+        assert e.value.code == ga.GA_EINVAL
+    with pytest.raises(ga.GenasmError) as e:
+        ga.ga_align_batch(db.reads, db.read_off, db.read_len, db.refs, db.ref_off, db.ref_len, 4,
+                          64, 24, 64, db.dist, db.status, db.ref_consumed, db.cigar, db.cigar_off,
+                          db.n_runs, None, None, db.workspace, 16)
+    assert e.value.code == ga.GA_ENOSPC
+    with pytest.raises(ga.GenasmError) as e:
+        ga.ga_align_plain(None, db.read_off, db.read_len, db.refs, db.ref_off, db.ref_len, 4,
+                          64, 24, 64, db.dist, db.status, db.ref_consumed, db.cigar, db.cigar_off,
+                          db.n_runs, None, None)
+    assert e.value.code == ga.GA_EINVAL
+
+
+def test_cigar_capacity_overflow():
+    # Give every pair room for one run only: pairs needing more report CIGAR_FULL.
+    b = datagen.make_batch(1, pair_ids=range(50))
+    ref = oracle.align(b)
+    db = DeviceBatch(b)
+    db.h_cigar_off = np.arange(b.n_pairs + 1, dtype=np.uint64)
+    db.cigar_off = torch.from_numpy(db.h_cigar_off.view(np.int64)).cuda()
+    db.run("batched")
+    got = db.results()
+    for p in range(b.n_pairs):
+        if ref.n_runs[p] <= 1:
+            assert got.status[p] == 0 and got.dist[p] == ref.dist[p]
+        else:
+            assert got.status[p] == ga.GA_PAIR_CIGAR_FULL and got.dist[p] == -1 and got.n_runs[p] == 0
