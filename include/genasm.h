@@ -105,16 +105,21 @@ int ga_workspace_size(uint32_t n_pairs, int W, int O, int k, size_t* bytes_out);
  * Tuning of the batched kernel. ga_align_batch uses the library's defaults
  * (or what ga_autotune stored for this device); ga_align_batch_tuned takes an
  * explicit choice. All fields 0 = default.
- *   lanes_per_pair : lanes that run one pair's DC wavefront (1 error row per
- *                    lane per pass): 8, 16 or 32.
+ *   lanes_per_pair : lanes that run one pair's DC wavefront: 4, 8, 16 or 32.
+ *   rows_per_lane  : error rows each lane updates per wavefront step; the
+ *                    supported (lanes_per_pair, rows_per_lane) pairs are
+ *                    (4,5) (8,3) (8,5) (16,3) (32,1) (32,2).
  *   pairs_per_block: pairs resident per thread block.
- *   table_rows     : error rows of each window's table kept in shared memory;
- *                    rows above spill to the workspace.
+ *   table_rows     : error rows of a window's table kept in shared memory
+ *                    (for windows that are not the last); a window whose
+ *                    solution row does not fit is recomputed into the
+ *                    workspace.
  *   lpt            : 1 = hand out pairs longest read first, -1 = in index
  *                    order (0 = default, longest first).
  */
 typedef struct {
   int lanes_per_pair;
+  int rows_per_lane;
   int pairs_per_block;
   int table_rows;
   int lpt;

@@ -11,85 +11,140 @@
 
 namespace ga {
 
-// One pair, windows in sequence (the window chain of a pair is serial: each
-// window starts where the previous traceback stopped).
-template <int G>
-__device__ __forceinline__ void align_pair(const AlignParams& p, uint32_t pair, int r,
-                                           uint32_t gmask, GroupSmem* gs, uint64_t* tab_smem,
-                                           int tab_entries, uint64_t* spill) {
-  const uint32_t m = p.read_len[pair];
-  const uint32_t n = p.ref_len[pair];
-  const uint8_t* __restrict__ read = p.reads + p.read_off[pair];
-  const uint8_t* __restrict__ ref = p.refs + p.ref_off[pair];
-  const uint64_t c0 = p.cigar_off[pair];
-  const uint64_t capl = p.cigar_off[pair + 1] - c0;
-  RunWriter rw{p.cigar + c0, capl > 0xffffffffull ? 0xffffffffu : static_cast<uint32_t>(capl),
-               0u, 0u, 0u, false};
-  const bool writer = r == 0;
-  const int W = p.W;
-  const int commit = p.W - p.O;
-  uint32_t pos_p = 0, pos_t = 0, edits = 0, windows = 0;
-  uint64_t cells = 0;
-  int32_t status = kPairOk;
+// Per-group pair state, replicated in every lane of the group.
+struct PairState {
+  const uint8_t* read;
+  const uint8_t* ref;
+  RunWriter rw;
+  uint64_t cells;
+  uint32_t pair, m, n, pos_p, pos_t, edits, windows;
+  int32_t status;
+  bool busy;
+};
 
-  while (pos_p < m) {
-    const int wp = static_cast<int>(min(static_cast<uint32_t>(W), m - pos_p));
-    const int wt = static_cast<int>(min(static_cast<uint32_t>(W), n - pos_t));
-    const bool last = pos_p + static_cast<uint32_t>(wp) == m;
-    const int ncols = last ? wt + 1 : min(wt, commit) + 1;
-    build_masks<G>(r, gmask, read, pos_p, wp, ref, pos_t, wt, gs->pmcol);
-    __syncwarp(gmask);
-    const TableRef tab{tab_smem, spill, tab_entries / ncols, ncols};
-    const int dmin = dc_window<G>(r, gmask, wp, wt, p.kmax, gs->pmcol, gs->bridge, tab);
-    if (dmin < 0) {
-      status = kPairExceedsK;
-      break;
-    }
-    int cp = 0, ct = 0;
-    if (!tb_window(wp, wt, dmin, last, commit, gs->pmcol, tab, rw, writer, cp, ct, edits) ||
-        cp + ct == 0) {
-      status = kPairTbStuck;
-      break;
-    }
-    if (rw.full) {
-      status = kPairCigarFull;
-      break;
-    }
-    ++windows;
-    cells += static_cast<uint64_t>(wt) * static_cast<uint64_t>(dmin + 1);
-    pos_p += static_cast<uint32_t>(cp);
-    pos_t += static_cast<uint32_t>(ct);
-    __syncwarp(gmask);
-  }
-  if (status == kPairOk) {
-    rw.flush(writer);
-    if (rw.full) status = kPairCigarFull;
+__device__ __forceinline__ void finish_pair(const AlignParams& p, PairState& st, bool writer) {
+  if (st.status == kPairOk) {
+    st.rw.flush(writer);
+    if (st.rw.full) st.status = kPairCigarFull;
   }
   if (writer) {
-    const bool ok = status == kPairOk;
-    p.dist[pair] = ok ? static_cast<int32_t>(edits) : -1;
-    p.status[pair] = status;
-    p.ref_consumed[pair] = ok ? static_cast<int32_t>(pos_t) : -1;
-    p.n_runs[pair] = ok ? rw.n : 0u;
-    if (p.n_windows) p.n_windows[pair] = windows;
-    if (p.cells) p.cells[pair] = cells;
+    const bool ok = st.status == kPairOk;
+    p.dist[st.pair] = ok ? static_cast<int32_t>(st.edits) : -1;
+    p.status[st.pair] = st.status;
+    p.ref_consumed[st.pair] = ok ? static_cast<int32_t>(st.pos_t) : -1;
+    p.n_runs[st.pair] = ok ? st.rw.n : 0u;
+    if (p.n_windows) p.n_windows[st.pair] = st.windows;
+    if (p.cells) p.cells[st.pair] = st.cells;
   }
-  __syncwarp(gmask);
+  st.busy = false;
+}
+
+__device__ __forceinline__ void begin_pair(const AlignParams& p, uint32_t pair, PairState& st,
+                                           bool writer) {
+  st.pair = pair;
+  st.m = p.read_len[pair];
+  st.n = p.ref_len[pair];
+  st.read = p.reads + p.read_off[pair];
+  st.ref = p.refs + p.ref_off[pair];
+  const uint64_t c0 = p.cigar_off[pair];
+  const uint64_t capl = p.cigar_off[pair + 1] - c0;
+  st.rw = RunWriter{p.cigar + c0, capl > 0xffffffffull ? 0xffffffffu : static_cast<uint32_t>(capl),
+                    0u, 0u, 0u, false};
+  st.cells = 0;
+  st.pos_p = st.pos_t = st.edits = st.windows = 0;
+  st.status = kPairOk;
+  st.busy = true;
+  if (st.m == 0) finish_pair(p, st, writer);  // empty read: nothing to align
+}
+
+// One window for every busy group of the warp (the window chain of a pair is
+// serial: each window starts where the previous traceback stopped).
+template <int G, int K>
+__device__ __forceinline__ void step_window(const AlignParams& p, int r, int gbase, PairState& st,
+                                            GroupSmem* gs, uint64_t* tab_smem, int tab_entries,
+                                            uint64_t* spill) {
+  const bool writer = r == 0;
+  const bool ga = st.busy;
+  const int commit = p.W - p.O;
+  int wp = 1, wt = 0, ncols = 1, S = 2, smem_rows = kMaxRows;
+  bool last = true;
+  if (ga) {
+    wp = static_cast<int>(min(static_cast<uint32_t>(p.W), st.m - st.pos_p));
+    wt = static_cast<int>(min(static_cast<uint32_t>(p.W), st.n - st.pos_t));
+    last = st.pos_p + static_cast<uint32_t>(wp) == st.m;
+    ncols = last ? wt + 1 : min(wt, commit) + 1;
+    S = table_stride(ncols);
+    smem_rows = min(tab_entries / S, kMaxRows);
+  }
+  const uint32_t pm_s = smem_addr(gs->pmcol);
+  const uint32_t bridge_s = smem_addr(gs->bridge);
+  const uint32_t tab_s = smem_addr(tab_smem);
+  build_masks<G>(r, gbase, ga, st.read, st.pos_p, wp, st.ref, st.pos_t, wt, gs->pmcol);
+  __syncwarp();
+  int dmin = dc_window<G, K, false>(r, gbase, ga, wp, wt, p.kmax, ncols, S, smem_rows, pm_s,
+                                    bridge_s, tab_s, nullptr);
+  // Rare: the table of rows 0..d_min does not fit the group's shared memory.
+  // Such a group recomputes the window into its global spill area (callers
+  // without one size the table for all 65 rows).
+  const bool spilled = ga && dmin >= smem_rows;
+  const bool can_spill = spill != nullptr;
+  if (__any_sync(kFull, spilled && can_spill)) {
+    __syncwarp();
+    const int d2 = dc_window<G, K, true>(r, gbase, spilled && can_spill, wp, wt, p.kmax, ncols, S,
+                                         kMaxRows, pm_s, bridge_s, tab_s, spill);
+    if (spilled && can_spill) dmin = d2;
+  }
+  __syncwarp();
+  const bool exceeds = ga && dmin < 0;
+  const bool trace = ga && !exceeds && !(spilled && !can_spill);
+  int cp = 0, ct = 0, cp2 = 0, ct2 = 0;
+  bool ok = tb_window<G, false>(r, gbase, trace && !spilled, wp, wt, dmin, last, commit, ncols, S,
+                                pm_s, tab_s, nullptr, st.rw, writer, cp, ct, st.edits);
+  if (__any_sync(kFull, trace && spilled)) {
+    const bool ok2 = tb_window<G, true>(r, gbase, trace && spilled, wp, wt, dmin, last, commit,
+                                        ncols, S, pm_s, tab_s, spill, st.rw, writer, cp2, ct2,
+                                        st.edits);
+    if (spilled) {
+      ok = ok2;
+      cp = cp2;
+      ct = ct2;
+    }
+  }
+  __syncwarp();
+  if (ga) {
+    if (exceeds) {
+      st.status = kPairExceedsK;
+    } else if (!trace || !ok || cp + ct == 0) {
+      st.status = kPairTbStuck;
+    } else if (st.rw.full) {
+      st.status = kPairCigarFull;
+    } else {
+      ++st.windows;
+      st.cells += static_cast<uint64_t>(wt) * static_cast<uint64_t>(dmin + 1);
+      st.pos_p += static_cast<uint32_t>(cp);
+      st.pos_t += static_cast<uint32_t>(ct);
+    }
+    if (st.status != kPairOk || st.pos_p >= st.m) finish_pair(p, st, writer);
+  }
 }
 
 // ---------------------------------------------------------------------------
-// Plain GPU GenASM: one pair per 32-thread block, the whole worst-case table
-// (65 rows x 65 columns) in shared memory, pairs in index order.
+// Plain GPU GenASM: one pair per 32-thread block (each lane a strip of 2
+// error rows, so one 64-row pass covers any window), the worst-case table
+// (65 rows x 66 entries) in shared memory, pairs in index order.
 // ---------------------------------------------------------------------------
 
-constexpr int kPlainTableEntries = kMaxRows * kMaxCols;
+constexpr int kPlainTableEntries = kMaxRows * kMaxStride;
 constexpr size_t kPlainSmem = sizeof(GroupSmem) + sizeof(uint64_t) * kPlainTableEntries;
 
 __global__ void __launch_bounds__(32) align_plain_kernel(const AlignParams p) {
   extern __shared__ __align__(16) uint64_t smem[];
   GroupSmem* gs = reinterpret_cast<GroupSmem*>(smem);
   uint64_t* table = smem + sizeof(GroupSmem) / sizeof(uint64_t);
-  align_pair<32>(p, blockIdx.x, threadIdx.x, 0xffffffffu, gs, table, kPlainTableEntries, nullptr);
+  const int r = threadIdx.x;
+  PairState st;
+  begin_pair(p, blockIdx.x, st, r == 0);
+  while (st.busy) step_window<32, 2>(p, r, 0, st, gs, table, kPlainTableEntries, nullptr);
 }
 
 cudaError_t launch_plain(const AlignParams& p, cudaStream_t s) {
@@ -100,38 +155,49 @@ cudaError_t launch_plain(const AlignParams& p, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------------------
-// Batched: persistent blocks of `pairs_per_block` groups of G lanes. Each
-// group pulls pairs from a device counter; with LPT the counter indexes a
-// longest-read-first permutation built by a counting sort.
+// Batched: persistent blocks of `pairs_per_block` groups of G lanes (each
+// lane a strip of K error rows). Each group pulls pairs from a device
+// counter; with LPT the counter indexes a longest-read-first permutation
+// built by a counting sort.
 // ---------------------------------------------------------------------------
 
 struct BatchArgs {
   uint32_t* queue;
   const uint32_t* order;  // nullptr: index order
-  uint64_t* spill;        // [groups][kMaxRows * kMaxCols]
+  uint64_t* spill;        // [groups][kMaxRows * kMaxStride]
   int table_entries;
 };
 
-template <int G>
-__global__ void align_batched_kernel(const AlignParams p, const BatchArgs a) {
+constexpr int kSpillEntries = kMaxRows * kMaxStride;
+
+template <int G, int K>
+__global__ void __launch_bounds__(256, 1) align_batched_kernel(const AlignParams p, const BatchArgs a) {
   extern __shared__ __align__(16) uint64_t smem[];
   const int lane = threadIdx.x & 31;
   const int group_in_block = threadIdx.x / G;
   const int r = lane % G;
-  const uint32_t gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane - r));
+  const int gbase = lane - r;
   const size_t group_words = sizeof(GroupSmem) / sizeof(uint64_t) + a.table_entries;
   uint64_t* base = smem + group_in_block * group_words;
   GroupSmem* gs = reinterpret_cast<GroupSmem*>(base);
   uint64_t* table = base + sizeof(GroupSmem) / sizeof(uint64_t);
   const size_t group_id = static_cast<size_t>(blockIdx.x) * (blockDim.x / G) + group_in_block;
-  uint64_t* spill = a.spill + group_id * (kMaxRows * kMaxCols);
+  uint64_t* spill = a.spill + group_id * kSpillEntries;
+  PairState st;
+  st.busy = false;
+  bool drained = false;
   for (;;) {
-    uint32_t idx = 0;
-    if (r == 0) idx = atomicAdd(a.queue, 1u);
-    idx = __shfl_sync(gmask, idx, lane - r);
-    if (idx >= p.n_pairs) break;
-    const uint32_t pair = a.order ? a.order[idx] : idx;
-    align_pair<G>(p, pair, r, gmask, gs, table, a.table_entries, spill);
+    // Groups without a pair take the next one from the queue.
+    const bool want = !st.busy && !drained;
+    uint32_t idx = 0xffffffffu;
+    if (want && r == 0) idx = atomicAdd(a.queue, 1u);
+    idx = __shfl_sync(kFull, idx, gbase);
+    if (want) {
+      if (idx < p.n_pairs) begin_pair(p, a.order ? a.order[idx] : idx, st, r == 0);
+      else drained = true;
+    }
+    if (!__any_sync(kFull, st.busy || !drained)) break;
+    if (__any_sync(kFull, st.busy)) step_window<G, K>(p, r, gbase, st, gs, table, a.table_entries, spill);
   }
 }
 
@@ -178,37 +244,61 @@ __global__ void lpt_scatter_kernel(const uint32_t* __restrict__ read_len, uint32
   }
 }
 
-template <int G>
-static cudaError_t set_smem_attr(size_t bytes) {
-  return cudaFuncSetAttribute(align_batched_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              static_cast<int>(bytes));
+// The compiled (G, K) variants of the batched kernel.
+#define GA_BATCH_VARIANTS(X) X(4, 5) X(8, 3) X(8, 5) X(16, 3) X(32, 1) X(32, 2)
+
+bool batch_variant_exists(int G, int K) {
+#define GA_EXISTS(g, k) if (G == g && K == k) return true;
+  GA_BATCH_VARIANTS(GA_EXISTS)
+#undef GA_EXISTS
+  return false;
 }
 
-template <int G>
-static cudaError_t occupancy(int threads, size_t smem, int* blocks_per_sm) {
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, align_batched_kernel<G>,
-                                                       threads, smem);
+static cudaError_t variant_setup(int G, int K, int threads, size_t smem, int* per_sm) {
+#define GA_SETUP(g, k)                                                                          \
+  if (G == g && K == k) {                                                                       \
+    cudaError_t e = cudaFuncSetAttribute(align_batched_kernel<g, k>,                            \
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,           \
+                                         static_cast<int>(smem));                               \
+    if (e != cudaSuccess) return e;                                                             \
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, align_batched_kernel<g, k>,    \
+                                                         threads, smem);                        \
+  }
+  GA_BATCH_VARIANTS(GA_SETUP)
+#undef GA_SETUP
+  return cudaErrorInvalidValue;
 }
 
-cudaError_t default_tuning(int W, int O, int k, int* G, int* ppb, int* table_entries, int* lpt) {
-  (void)W;
-  (void)O;
+static void variant_launch(int G, int K, int blocks, int threads, size_t smem, cudaStream_t s,
+                           const AlignParams& p, const BatchArgs& a) {
+#define GA_LAUNCH(g, k) \
+  if (G == g && K == k) align_batched_kernel<g, k><<<blocks, threads, smem, s>>>(p, a);
+  GA_BATCH_VARIANTS(GA_LAUNCH)
+#undef GA_LAUNCH
+}
+
+cudaError_t default_tuning(int W, int O, int k, int* G, int* K, int* ppb, int* table_entries,
+                           int* lpt) {
   (void)k;
-  *G = 32;
-  *ppb = 4;
-  *table_entries = 36 * 41;
+  *G = 16;
+  *K = 3;
+  *ppb = 2;
+  // Rows 0..37 of a window that is not the last (W-O+1 stored columns).
+  *table_entries = 38 * table_stride(W - O + 1);
   *lpt = 1;
+  (void)W;
   return cudaSuccess;
 }
 
-cudaError_t resolve_plan(int W, int O, int k, int G, int ppb, int table_entries, int lpt,
+cudaError_t resolve_plan(int W, int O, int k, int G, int K, int ppb, int table_entries, int lpt,
                          BatchPlan* plan) {
   (void)W;
   (void)O;
   (void)k;
-  if (G != 8 && G != 16 && G != 32) return cudaErrorInvalidValue;
-  if (ppb < 1 || ppb * G > 1024) return cudaErrorInvalidValue;
-  table_entries = std::max(kMaxCols, std::min(table_entries, kMaxRows * kMaxCols));
+  if (!batch_variant_exists(G, K)) return cudaErrorInvalidValue;
+  if (ppb < 1 || ppb * G > 256 || (ppb * G) % 32 != 0) return cudaErrorInvalidValue;  // whole warps
+  table_entries = std::max(kMaxStride, std::min(table_entries, kMaxRows * kMaxStride));
+  table_entries &= ~1;  // keep every group's area 16-byte aligned
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
@@ -221,23 +311,10 @@ cudaError_t resolve_plan(int W, int O, int k, int G, int ppb, int table_entries,
   if (smem > static_cast<size_t>(smem_optin)) return cudaErrorInvalidValue;
   const int threads = ppb * G;
   int per_sm = 0;
-  switch (G) {
-    case 8:
-      if ((e = set_smem_attr<8>(smem)) != cudaSuccess) return e;
-      e = occupancy<8>(threads, smem, &per_sm);
-      break;
-    case 16:
-      if ((e = set_smem_attr<16>(smem)) != cudaSuccess) return e;
-      e = occupancy<16>(threads, smem, &per_sm);
-      break;
-    default:
-      if ((e = set_smem_attr<32>(smem)) != cudaSuccess) return e;
-      e = occupancy<32>(threads, smem, &per_sm);
-      break;
-  }
-  if (e != cudaSuccess) return e;
+  if ((e = variant_setup(G, K, threads, smem, &per_sm)) != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   plan->lanes_per_pair = G;
+  plan->rows_per_lane = K;
   plan->pairs_per_block = ppb;
   plan->table_entries = table_entries;
   plan->lpt = lpt ? 1 : 0;
@@ -254,7 +331,7 @@ WorkspaceLayout workspace_layout(uint32_t n_pairs, const BatchPlan& plan) {
   L.order = up(L.hist + sizeof(uint32_t) * kLptBuckets);
   L.spill = up(L.order + sizeof(uint32_t) * static_cast<size_t>(n_pairs));
   const size_t groups = static_cast<size_t>(plan.blocks) * plan.pairs_per_block;
-  L.total = up(L.spill + groups * sizeof(uint64_t) * kMaxRows * kMaxCols);
+  L.total = up(L.spill + groups * sizeof(uint64_t) * kSpillEntries);
   return L;
 }
 
@@ -277,17 +354,8 @@ cudaError_t launch_batched(const AlignParams& p, const BatchPlan& plan, void* ws
   BatchArgs a{queue, plan.lpt ? order : nullptr, reinterpret_cast<uint64_t*>(w + L.spill),
               plan.table_entries};
   const int threads = plan.pairs_per_block * plan.lanes_per_pair;
-  switch (plan.lanes_per_pair) {
-    case 8:
-      align_batched_kernel<8><<<plan.blocks, threads, plan.smem_bytes, s>>>(p, a);
-      break;
-    case 16:
-      align_batched_kernel<16><<<plan.blocks, threads, plan.smem_bytes, s>>>(p, a);
-      break;
-    default:
-      align_batched_kernel<32><<<plan.blocks, threads, plan.smem_bytes, s>>>(p, a);
-      break;
-  }
+  variant_launch(plan.lanes_per_pair, plan.rows_per_lane, plan.blocks, threads, plan.smem_bytes, s,
+                 p, a);
   count_launches(1);
   return cudaGetLastError();
 }

@@ -31,6 +31,7 @@ struct AlignParams {
 // Resolved tuning of the batched kernel.
 struct BatchPlan {
   int lanes_per_pair;   // G
+  int rows_per_lane;    // K
   int pairs_per_block;  // groups per block
   int table_entries;    // 64-bit table entries per group kept in shared memory
   int lpt;              // longest-first hand-out
@@ -69,8 +70,10 @@ cudaError_t launch_batched(const AlignParams& p, const BatchPlan& plan, void* ws
 
 // Default tuning for (W, O, k) on the current device; fills G / pairs per
 // block / table entries / lpt. Returns cudaSuccess or the device query error.
-cudaError_t default_tuning(int W, int O, int k, int* G, int* ppb, int* table_entries, int* lpt);
-cudaError_t resolve_plan(int W, int O, int k, int G, int ppb, int table_entries, int lpt,
+cudaError_t default_tuning(int W, int O, int k, int* G, int* K, int* ppb, int* table_entries,
+                           int* lpt);
+bool batch_variant_exists(int G, int K);
+cudaError_t resolve_plan(int W, int O, int k, int G, int K, int ppb, int table_entries, int lpt,
                          BatchPlan* plan);
 
 }  // namespace ga

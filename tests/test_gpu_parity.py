@@ -90,13 +90,24 @@ def test_error_cap(k):
         assert_same(b, run_gpu(b, kernel, k=k), ref, f"k{k}/{kernel}")
 
 
-@pytest.mark.parametrize("G,ppb,rows", [(32, 1, 1), (32, 8, 2), (16, 4, 20), (8, 8, 40), (8, 2, 65),
-                                        (16, 16, 8), (32, 2, 65)])
-def test_tunings_identical(G, ppb, rows):
+TUNINGS = [(4, 5, 8, 38, 1), (4, 5, 8, 1, 1), (8, 3, 4, 20, -1), (8, 5, 4, 65, 1), (8, 5, 8, 2, 1),
+           (16, 3, 4, 30, 1), (32, 1, 2, 36, -1), (32, 2, 1, 65, 1), (32, 2, 3, 10, 1), (16, 3, 2, 3, 1)]
+
+
+@pytest.mark.parametrize("G,K,ppb,rows,lpt", TUNINGS)
+def test_tunings_identical(G, K, ppb, rows, lpt):
     b = datagen.make_batch(4, pair_ids=range(40))
     ref = oracle.align(b)
-    t = ga.ga_tuning(G, ppb, rows, 1)
-    assert_same(b, run_gpu(b, "batched", tuning=t), ref, f"G{G}/ppb{ppb}/rows{rows}")
+    t = ga.ga_tuning(G, K, ppb, rows, lpt)
+    assert_same(b, run_gpu(b, "batched", tuning=t), ref, f"G{G}/K{K}/ppb{ppb}/rows{rows}")
+
+
+@pytest.mark.parametrize("G,K,ppb,rows,lpt", TUNINGS[:4])
+def test_tunings_edge_cases(G, K, ppb, rows, lpt):
+    b = datagen.from_pairs(edge_pairs(seed=G * 10 + K, n_random=100))
+    ref = oracle.align(b, k=40)
+    t = ga.ga_tuning(G, K, ppb, rows, lpt)
+    assert_same(b, run_gpu(b, "batched", k=40, tuning=t), ref, f"edge G{G}/K{K}")
 
 
 @pytest.mark.parametrize("config,ids", [(2, range(0, 24)), (3, range(100, 130)), (4, range(1000, 1060))])
