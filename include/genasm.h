@@ -134,6 +134,37 @@ int ga_workspace_size_tuned(uint32_t n_pairs, int W, int O, int k, const ga_tuni
                             size_t* bytes_out);
 
 /*
+ * ga_align_batch_noalloc - ga_align_batch for callers that cannot allocate
+ * device memory at all, not even a workspace: for example a plugin that only
+ * sees the buffers its host program hands it, a process whose memory budget
+ * is spent, or a latency-critical loop that cannot afford cudaMalloc's
+ * implicit synchronization. The paper has no counterpart; this is a library
+ * convenience.
+ *
+ * Same arguments and outputs as ga_align_batch without the workspace; the
+ * results are identical. It allocates nothing: its scratch (the work-queue
+ * counter, the longest-first histogram and the order of up to
+ * GA_NOALLOC_MAX_PAIRS pairs, about 1 MB) is one static array that every GPU
+ * loading the library holds until the process exits. The first call on a
+ * device looks up that array's device address (cudaGetSymbolAddress with the
+ * device current); make that first call before any stream capture. Every
+ * call shares the array and overwrites what the previous call left there, so
+ * calls whose work overlaps on the GPU (other streams, other host threads)
+ * race: order them on one stream or wait between them. It runs with tables
+ * sized for all 65 error rows in shared memory, so it is slower than
+ * ga_align_batch.
+ * Errors: GA_ENOSPC if n_pairs > GA_NOALLOC_MAX_PAIRS, GA_EINVAL, GA_ECUDA.
+ */
+#define GA_NOALLOC_MAX_PAIRS 262144
+int ga_align_batch_noalloc(const uint8_t* d_reads, const uint64_t* d_read_off,
+                           const uint32_t* d_read_len, const uint8_t* d_refs,
+                           const uint64_t* d_ref_off, const uint32_t* d_ref_len,
+                           uint32_t n_pairs, int W, int O, int k,
+                           int32_t* d_dist, int32_t* d_status, int32_t* d_ref_consumed,
+                           uint32_t* d_cigar, const uint64_t* d_cigar_off, uint32_t* d_n_runs,
+                           uint32_t* d_n_windows, uint64_t* d_cells, ga_stream_t stream);
+
+/*
  * ga_cigar_compact - CIGAR writer, final pass: gathers the runs the alignment
  * wrote at per-pair capacities (d_cigar, d_cigar_off, d_n_runs as given to
  * ga_align_batch) into one dense array. d_out_off (n_pairs + 1 uint64)

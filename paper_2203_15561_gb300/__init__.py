@@ -214,3 +214,23 @@ def ga_align_plain(d_reads, d_read_off, d_read_len, d_refs, d_ref_off, d_ref_len
                     d_dist, d_status, d_ref_consumed, d_cigar, d_cigar_off, d_n_runs, d_n_windows,
                     d_cells)
     return _check(lib().ga_align_plain(*a, _stream(stream)), "ga_align_plain")
+
+
+GA_NOALLOC_MAX_PAIRS = 262144
+
+
+def ga_align_batch_noalloc(d_reads, d_read_off, d_read_len, d_refs, d_ref_off, d_ref_len, n_pairs,
+                           W, O, k, d_dist, d_status, d_ref_consumed, d_cigar, d_cigar_off,
+                           d_n_runs, d_n_windows, d_cells, stream=None) -> int:
+    """ga_align_batch for callers that cannot allocate device memory: no
+    workspace argument; the library's own static scratch (up to
+    GA_NOALLOC_MAX_PAIRS pairs) is used. Calls that overlap on the GPU race."""
+    so = lib()
+    if not getattr(so, "_noalloc_typed", False):
+        so.ga_align_batch_noalloc.restype = _i
+        so.ga_align_batch_noalloc.argtypes = _ALIGN_ARGS + [_vp]
+        so._noalloc_typed = True
+    a = _align_args(d_reads, d_read_off, d_read_len, d_refs, d_ref_off, d_ref_len, n_pairs, W, O, k,
+                    d_dist, d_status, d_ref_consumed, d_cigar, d_cigar_off, d_n_runs, d_n_windows,
+                    d_cells)
+    return _check(so.ga_align_batch_noalloc(*a, _stream(stream)), "ga_align_batch_noalloc")
