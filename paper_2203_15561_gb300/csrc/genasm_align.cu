@@ -76,13 +76,10 @@ __device__ __forceinline__ void step_window(const AlignParams& p, int r, int gba
     S = table_stride(ncols);
     smem_rows = min(tab_entries / S, kMaxRows);
   }
-  const uint32_t pm_s = smem_addr(gs->pmcol);
-  const uint32_t bridge_s = smem_addr(gs->bridge);
-  const uint32_t tab_s = smem_addr(tab_smem);
   build_masks<G>(r, gbase, ga, st.read, st.pos_p, wp, st.ref, st.pos_t, wt, gs->pmcol);
   __syncwarp();
-  int dmin = dc_window<G, K, false>(r, gbase, ga, wp, wt, p.kmax, ncols, S, smem_rows, pm_s,
-                                    bridge_s, tab_s, nullptr);
+  int dmin = dc_window<G, K>(r, gbase, ga, wp, wt, p.kmax, ncols, S, smem_rows, gs->pmcol,
+                             gs->bridge, tab_smem);
   // Rare: the table of rows 0..d_min does not fit the group's shared memory.
   // Such a group recomputes the window into its global spill area (callers
   // without one size the table for all 65 rows).
@@ -90,20 +87,19 @@ __device__ __forceinline__ void step_window(const AlignParams& p, int r, int gba
   const bool can_spill = spill != nullptr;
   if (__any_sync(kFull, spilled && can_spill)) {
     __syncwarp();
-    const int d2 = dc_window<G, K, true>(r, gbase, spilled && can_spill, wp, wt, p.kmax, ncols, S,
-                                         kMaxRows, pm_s, bridge_s, tab_s, spill);
+    const int d2 = dc_window<G, K>(r, gbase, spilled && can_spill, wp, wt, p.kmax, ncols, S,
+                                   kMaxRows, gs->pmcol, gs->bridge, spill);
     if (spilled && can_spill) dmin = d2;
   }
   __syncwarp();
   const bool exceeds = ga && dmin < 0;
   const bool trace = ga && !exceeds && !(spilled && !can_spill);
   int cp = 0, ct = 0, cp2 = 0, ct2 = 0;
-  bool ok = tb_window<G, false>(r, gbase, trace && !spilled, wp, wt, dmin, last, commit, ncols, S,
-                                pm_s, tab_s, nullptr, st.rw, writer, cp, ct, st.edits);
+  bool ok = tb_window<G>(r, gbase, trace && !spilled, wp, wt, dmin, last, commit, ncols, S,
+                         gs->pmcol, tab_smem, st.rw, writer, cp, ct, st.edits);
   if (__any_sync(kFull, trace && spilled)) {
-    const bool ok2 = tb_window<G, true>(r, gbase, trace && spilled, wp, wt, dmin, last, commit,
-                                        ncols, S, pm_s, tab_s, spill, st.rw, writer, cp2, ct2,
-                                        st.edits);
+    const bool ok2 = tb_window<G>(r, gbase, trace && spilled, wp, wt, dmin, last, commit, ncols, S,
+                                  gs->pmcol, spill, st.rw, writer, cp2, ct2, st.edits);
     if (spilled) {
       ok = ok2;
       cp = cp2;

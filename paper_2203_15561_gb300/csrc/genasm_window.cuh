@@ -167,20 +167,19 @@ __device__ __forceinline__ void build_masks(int r, int gbase, bool ga,
 // the solution.
 //
 // Per sub-row k the lane keeps C = R_{i+1}[q] (and C << 1) and
-// UP = R_{i+1}[q-1] (and UP << 1). The table receives rows below `store_rows`
-// at row stride S (entries): in shared memory (tab_s, a shared-window
-// address) or, with SPILL, through the generic pointer tab_g. FIRST marks the
-// pass b = 0, whose row -1 is all ones. Returns d_min, or -1 if it is above
-// kmax (groups with ga == false get -1 too).
-template <int G, int K, bool SPILL, bool FIRST>
+// UP = R_{i+1}[q-1] (and UP << 1). The table `tab` (shared memory, or the
+// global spill area) receives rows below `store_rows` at row stride S.
+// FIRST marks the pass b = 0, whose row -1 is all ones.
+template <int G, int K, bool FIRST>
 __device__ __forceinline__ void dc_pass(int r, int gbase, int b, bool gpass, int wp, int wt,
                                         int kmax, int ncol_store, int S, int store_rows,
-                                        uint32_t pm_s, uint32_t bridge_s, uint32_t tab_s,
-                                        uint64_t* tab_g, int& found) {
+                                        const uint64_t* pmcol, uint64_t* bridge, uint64_t* tab,
+                                        int& found) {
   constexpr int GK = G * K;
   const int q0 = b + r * K;
   uint64_t C[K], CS[K], UP[K], UPS[K], PMR[K];
   int nb[K];  // columns [0, nb) of sub-row k are stored
+  uint32_t row_ok = 0;  // bit k: row q0+k may hold the solution (q <= kmax)
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     const int q = q0 + k;
@@ -191,11 +190,9 @@ __device__ __forceinline__ void dc_pass(int r, int gbase, int b, bool gpass, int
     PMR[k] = ~0ull;
     const bool store_row = gpass && q <= kmax && q < store_rows;
     nb[k] = store_row ? ncol_store : 0;
+    row_ok |= q <= kmax ? (1u << k) : 0u;
     // Column wt of the table holds the initial value of the row.
-    if (store_row && wt < S) {
-      if (SPILL) tab_g[q * S + wt] = C[k];
-      else sts64(tab_s + 8u * (q * S + wt), C[k]);
-    }
+    if (store_row && wt < S) tab[q * S + wt] = C[k];
   }
   const uint64_t lane0_ones = (FIRST && r == 0) ? ~0ull : 0ull;
   const uint32_t row0_fix = (FIRST && r == 0) ? 1u : 0u;
@@ -203,26 +200,30 @@ __device__ __forceinline__ void dc_pass(int r, int gbase, int b, bool gpass, int
   const uint64_t msb_mask = 1ull << (wp - 1);
   const int delta = (K - (wt - 1) % K) % K;
   const int t_last = wt - 1 + GK - 1 + delta;
-  const uint32_t bridge_ok = (r == G - 1 && gpass) ? static_cast<uint32_t>(wt) : 0u;
-  // Table address of sub-row 0 at the current column; sub-row k is at a
-  // fixed offset of k*(S+1) entries from it.
+  const int t_first_done = wt - 1 + delta;  // first step a row can reach column 0
+  const int bridge_n = (r == G - 1 && gpass) ? wt : 0;
+  // i0: column of sub-row 0 at the first step of the block.
   int i0 = wt - 1 + delta + r * K;
-  uint32_t a0 = tab_s + 8u * static_cast<uint32_t>(q0 * S + i0);
+  uint64_t* rowp[K];  // &tab[(q0+k)*S + i0 + k], the cell sub-row k writes at u = 0
+#pragma unroll
+  for (int k = 0; k < K; ++k) rowp[k] = tab + ((q0 + k) * S + i0 + k);
   for (int t0 = 0; __any_sync(kFull, gpass && found < 0 && t0 <= t_last); t0 += K) {
     uint32_t solmask = 0;
+    const bool check = t0 + K - 1 >= t_first_done;
 #pragma unroll
     for (int u = 0; u < K; ++u) {
+      const int iu = i0 - u;  // column of sub-row 0 at this step
       // Row above sub-row 0: lane r-1's last sub-row, one step old.
       uint64_t up0 = __shfl_up_sync(kFull, C[K - 1], 1, G);
       if (FIRST) {
         up0 |= lane0_ones;
       } else {
-        const uint64_t br = lds64(bridge_s + 8u * min(static_cast<uint32_t>(i0), 63u));
-        const uint64_t v0 = static_cast<unsigned>(i0) < static_cast<unsigned>(wt) ? br : init_above;
+        const uint64_t br = bridge[min(static_cast<unsigned>(iu), 63u)];
+        const uint64_t v0 = static_cast<unsigned>(iu) < static_cast<unsigned>(wt) ? br : init_above;
         up0 = r == 0 ? v0 : up0;
       }
       const uint64_t ups0 = shl1(up0, row0_fix);
-      PMR[u] = lds64(pm_s + 8u * min(static_cast<uint32_t>(i0), static_cast<uint32_t>(kPmCols - 1)));
+      PMR[u] = pmcol[min(static_cast<unsigned>(iu), static_cast<unsigned>(kPmCols - 1))];
 #pragma unroll
       for (int k = K - 1; k >= 0; --k) {
         const uint64_t up = k == 0 ? up0 : C[k - 1];
@@ -232,24 +233,22 @@ __device__ __forceinline__ void dc_pass(int r, int gbase, int b, bool gpass, int
         UPS[k] = ups;
         C[k] = nv;
         CS[k] = shl1(nv, 0u);
-        const int i = i0 + k;
-        const bool st = static_cast<unsigned>(i) < static_cast<unsigned>(nb[k]);
-        if (SPILL) {
-          if (st) tab_g[(q0 + k) * S + i] = nv;
-        } else {
-          sts64_if(st, a0 + 8u * static_cast<uint32_t>(k * (S + 1)), nv);
-        }
-        if (k == K - 1)
-          sts64_if(static_cast<unsigned>(i) < bridge_ok, bridge_s + 8u * static_cast<uint32_t>(i), nv);
+        const int i = iu + k;
+        if (static_cast<unsigned>(i) < static_cast<unsigned>(nb[k])) rowp[k][-u] = nv;
+        if (k == K - 1 && static_cast<unsigned>(i) < static_cast<unsigned>(bridge_n)) bridge[i] = nv;
       }
-      // Sub-row u of this lane reaches column 0 at this step iff i0 + u == 0.
-      const bool at0 = i0 + u == 0 && q0 + u <= kmax && !(C[u] & msb_mask);
-      solmask |= at0 ? (1u << u) : 0u;
-      --i0;
-      a0 -= 8u;
+      // Sub-row u of this lane reaches column 0 at this step iff iu + u == 0.
+      if (check) {
+        const bool at0 = iu + u == 0 && ((row_ok >> u) & 1u) && !(C[u] & msb_mask);
+        solmask |= at0 ? (1u << u) : 0u;
+      }
     }
+    i0 -= K;
+#pragma unroll
+    for (int k = 0; k < K; ++k) rowp[k] -= K;
     // Early termination: strips finish in lane order, so the first lane of
-    // the group with a solved row holds the smallest one.
+    // the group with a solved row holds the smallest one. (The votes run for
+    // the whole warp every block: `check` differs between groups.)
     const uint32_t mine = group_bits<G>(__ballot_sync(kFull, solmask != 0u), gbase);
     const int src = mine ? gbase + __ffs(mine) - 1 : (threadIdx.x & 31);
     const int got = __shfl_sync(kFull, q0 + __ffs(solmask) - 1, src);
@@ -257,10 +256,11 @@ __device__ __forceinline__ void dc_pass(int r, int gbase, int b, bool gpass, int
   }
 }
 
-template <int G, int K, bool SPILL>
+// Returns d_min, or -1 if it is above kmax (groups with ga == false get -1).
+template <int G, int K>
 __device__ __forceinline__ int dc_window(int r, int gbase, bool ga, int wp, int wt, int kmax,
-                                         int ncols, int S, int store_rows, uint32_t pm_s,
-                                         uint32_t bridge_s, uint32_t tab_s, uint64_t* tab_g) {
+                                         int ncols, int S, int store_rows, const uint64_t* pmcol,
+                                         uint64_t* bridge, uint64_t* tab) {
   constexpr int GK = G * K;
   constexpr int kSearching = -1, kIdle = -2, kAbove = -3;
   int found = ga ? kSearching : kIdle;
@@ -268,15 +268,15 @@ __device__ __forceinline__ int dc_window(int r, int gbase, bool ga, int wp, int 
   const int ncol_store = min(wt, ncols);
   {
     const bool gpass = found == kSearching;
-    dc_pass<G, K, SPILL, true>(r, gbase, 0, gpass, wp, wt, kmax, ncol_store, S, store_rows, pm_s,
-                               bridge_s, tab_s, tab_g, found);
+    dc_pass<G, K, true>(r, gbase, 0, gpass, wp, wt, kmax, ncol_store, S, store_rows, pmcol, bridge,
+                        tab, found);
     if (gpass && found == kSearching && GK > kmax) found = kAbove;
   }
   for (int b = GK; __any_sync(kFull, found == kSearching && b <= kmax); b += GK) {
     __syncwarp();  // the bridge row of the previous pass is complete
     const bool gpass = found == kSearching && b <= kmax;
-    dc_pass<G, K, SPILL, false>(r, gbase, b, gpass, wp, wt, kmax, ncol_store, S, store_rows, pm_s,
-                                bridge_s, tab_s, tab_g, found);
+    dc_pass<G, K, false>(r, gbase, b, gpass, wp, wt, kmax, ncol_store, S, store_rows, pmcol,
+                         bridge, tab, found);
     if (gpass && found == kSearching && b + GK > kmax) found = kAbove;
   }
   return found >= 0 ? found : -1;
@@ -322,11 +322,12 @@ struct RunWriter {
 // unless it stopped, that lane's edit. Every lane of the warp runs the same
 // iterations; groups that are done only take part in the ballots. Returns
 // false for a group whose walk found no edge (never expected).
-template <int G, bool SPILL>
+template <int G>
 __device__ __forceinline__ bool tb_window(int r, int gbase, bool ga, int wp, int wt, int dmin,
-                                          bool last, int commit, int ncols, int S, uint32_t pm_s,
-                                          uint32_t tab_s, const uint64_t* tab_g, RunWriter& rw,
-                                          bool writer, int& cp_out, int& ct_out, uint32_t& edits) {
+                                          bool last, int commit, int ncols, int S,
+                                          const uint64_t* pmcol, const uint64_t* tab,
+                                          RunWriter& rw, bool writer, int& cp_out, int& ct_out,
+                                          uint32_t& edits) {
   int i = 0, j = wp - 1, d = dmin, cp = 0, ct = 0;
   bool run = ga, ok = true;
   // Columns c and c+1 of a row are read for c <= cmax (always inside the row).
@@ -340,17 +341,10 @@ __device__ __forceinline__ bool tb_window(int r, int gbase, bool ga, int wp, int
     // row that lives in the other (spill or shared) table.
     const int dl = (run && d > 0) ? d : 0;
     const int dm = (run && d > 0) ? d - 1 : 0;
-    uint64_t a, s, in;
-    if (SPILL) {
-      a = tab_g[dl * S + ic + 1];
-      s = tab_g[dm * S + ic + 1];
-      in = tab_g[dm * S + ic];
-    } else {
-      a = lds64(tab_s + 8u * static_cast<uint32_t>(dl * S + ic + 1));
-      s = lds64(tab_s + 8u * static_cast<uint32_t>(dm * S + ic + 1));
-      in = lds64(tab_s + 8u * static_cast<uint32_t>(dm * S + ic));
-    }
-    const uint64_t pm = lds64(pm_s + 8u * static_cast<uint32_t>(min(il, kPmCols - 1)));
+    const uint64_t a = tab[dl * S + ic + 1];
+    uint64_t s = tab[dm * S + ic + 1];
+    uint64_t in = tab[dm * S + ic];
+    const uint64_t pm = pmcol[min(il, kPmCols - 1)];
     const uint64_t none = d > 0 ? 0ull : ~0ull;  // row -1 does not exist
     s |= none;
     in |= none;
