@@ -237,9 +237,12 @@ def run_ours(args):
     cells = int(res.cells.sum())
     windows = int(res.n_windows.sum())
 
-    # ---- batched (the headline) ----
+    # ---- batched (the headline): autotuned, alignment replayed from a CUDA graph ----
+    tuned, tune_ms = db.autotune()
+    g_align = db.graph(pack=False)
     for _ in range(args.warmup):
-        db.run("batched", stats=False)
+        db.pack()
+        g_align.launch()
     torch.cuda.synchronize(dev)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
            torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
@@ -256,7 +259,7 @@ def run_ours(args):
             a.record(stream)
             db.pack()
             b.record(stream)
-            db.align("batched", stats=False)
+            g_align.launch()
             c.record(stream)
         t_end.record(stream)
         torch.cuda.synchronize(dev)
@@ -333,7 +336,11 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": "long-10kb-10000pairs (10 kb PacBio-like reads, 12% error, 5% flanks, seed 2)",
                        "W": W, "O": O, "k": K, "pairs_per_gpu": n, "read_bases_per_gpu": read_bases,
-                       "kernel": "batched (persistent, LPT work queue)",
+                       "kernel": "batched (persistent, LPT work queue, CUDA graph)",
+                       "autotuned": {"lanes_per_pair": tuned.lanes_per_pair,
+                                     "rows_per_lane": tuned.rows_per_lane,
+                                     "pairs_per_block": tuned.pairs_per_block,
+                                     "table_rows": tuned.table_rows, "tune_ms": tune_ms},
                        "l2": "no flush: each step streams 210 MB of ASCII input (> 126 MB L2) and "
                              "writes ~0.5 GB of CIGAR runs, which evicts the previous step's data"},
             "gbases_per_s": gbases,

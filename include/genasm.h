@@ -117,13 +117,68 @@ int ga_workspace_size(uint32_t n_pairs, int W, int O, int k, size_t* bytes_out);
  *   lpt            : 1 = hand out pairs longest read first, -1 = in index
  *                    order (0 = default, longest first).
  */
-typedef struct {
+typedef struct ga_tuning_s {
   int lanes_per_pair;
   int rows_per_lane;
   int pairs_per_block;
   int table_rows;
   int lpt;
 } ga_tuning;
+
+/*
+ * ga_tuning_get / ga_tuning_set - the tuning ga_align_batch and
+ * ga_workspace_size use on the current device for (W, O, k): the one chosen
+ * by ga_autotune or set here, else the library default. ga_tuning_set(NULL)
+ * drops a stored choice. After the default changes, size workspaces again.
+ * Errors: GA_EINVAL (bad W/O/k, NULL out, unsupported tuning), GA_ECUDA.
+ */
+int ga_tuning_get(int W, int O, int k, ga_tuning* out);
+int ga_tuning_set(int W, int O, int k, const ga_tuning* tuning);
+
+/*
+ * ga_autotune - the autotuner of the batched kernel. Runs the current
+ * default once on the caller's sample (with statistics, to estimate the
+ * typical d_min), then times a candidate set of (lanes_per_pair,
+ * rows_per_lane, pairs_per_block, table_rows) with CUDA events, one warm-up
+ * and one timed run each, and stores the fastest as the default for this
+ * device and (W, O, k). Arguments as ga_align_batch (outputs are
+ * overwritten; d_n_windows and d_cells are required); the workspace must hold
+ * ga_autotune_workspace_size(n_pairs, W, O, k) bytes. Synchronous: returns
+ * once every run has finished. *best / *best_ms (either may be NULL) receive
+ * the choice and its time. The paper gives no tuning procedure.
+ * Errors: GA_EINVAL, GA_ENOSPC (no candidate fits the workspace), GA_ECUDA.
+ */
+int ga_autotune(const uint8_t* d_reads, const uint64_t* d_read_off, const uint32_t* d_read_len,
+                const uint8_t* d_refs, const uint64_t* d_ref_off, const uint32_t* d_ref_len,
+                uint32_t n_pairs, int W, int O, int k,
+                int32_t* d_dist, int32_t* d_status, int32_t* d_ref_consumed,
+                uint32_t* d_cigar, const uint64_t* d_cigar_off, uint32_t* d_n_runs,
+                uint32_t* d_n_windows, uint64_t* d_cells,
+                void* d_workspace, size_t ws_bytes, ga_tuning* best, float* best_ms,
+                ga_stream_t stream);
+int ga_autotune_workspace_size(uint32_t n_pairs, int W, int O, int k, size_t* bytes_out);
+
+/*
+ * ga_graph_create / ga_graph_launch / ga_graph_destroy - one whole step of
+ * the hot path captured as a CUDA graph for fixed buffers: 2-bit packing of
+ * d_ascii_reads / d_ascii_refs into d_reads / d_refs (skipped when both ASCII
+ * pointers are NULL), then ga_align_batch_tuned with the given buffers,
+ * workspace and tuning (NULL = the current default). ga_graph_launch replays
+ * it on `stream` (asynchronous); the buffers must stay valid while a graph
+ * may run. Errors: GA_EINVAL, GA_ENOSPC (workspace), GA_ECUDA.
+ */
+typedef struct ga_graph ga_graph;
+int ga_graph_create(const uint8_t* d_ascii_reads, uint64_t n_read_chars,
+                    const uint8_t* d_ascii_refs, uint64_t n_ref_chars,
+                    uint8_t* d_reads, const uint64_t* d_read_off, const uint32_t* d_read_len,
+                    uint8_t* d_refs, const uint64_t* d_ref_off, const uint32_t* d_ref_len,
+                    uint32_t n_pairs, int W, int O, int k,
+                    int32_t* d_dist, int32_t* d_status, int32_t* d_ref_consumed,
+                    uint32_t* d_cigar, const uint64_t* d_cigar_off, uint32_t* d_n_runs,
+                    uint32_t* d_n_windows, uint64_t* d_cells,
+                    void* d_workspace, size_t ws_bytes, const ga_tuning* tuning, ga_graph** out);
+int ga_graph_launch(ga_graph* graph, ga_stream_t stream);
+int ga_graph_destroy(ga_graph* graph);
 
 /*
  * ga_workspace_size_tuned - workspace bytes ga_align_batch_tuned needs with

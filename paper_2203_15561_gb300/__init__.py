@@ -234,3 +234,99 @@ def ga_align_batch_noalloc(d_reads, d_read_off, d_read_len, d_refs, d_ref_off, d
                     d_dist, d_status, d_ref_consumed, d_cigar, d_cigar_off, d_n_runs, d_n_windows,
                     d_cells)
     return _check(so.ga_align_batch_noalloc(*a, _stream(stream)), "ga_align_batch_noalloc")
+
+
+def _typed(name, restype, argtypes):
+    so = lib()
+    f = getattr(so, name)
+    if getattr(f, "_ga_typed", False) is False:
+        f.restype = restype
+        f.argtypes = argtypes
+        f._ga_typed = True
+    return f
+
+
+def ga_tuning_get(W: int, O: int, k: int) -> ga_tuning:
+    out = ga_tuning()
+    f = _typed("ga_tuning_get", _i, [_i, _i, _i, ctypes.POINTER(ga_tuning)])
+    _check(f(W, O, k, ctypes.byref(out)), "ga_tuning_get")
+    return out
+
+
+def ga_tuning_set(W: int, O: int, k: int, tuning=None) -> int:
+    f = _typed("ga_tuning_set", _i, [_i, _i, _i, ctypes.POINTER(ga_tuning)])
+    return _check(f(W, O, k, ctypes.byref(tuning) if tuning is not None else None), "ga_tuning_set")
+
+
+def ga_autotune_workspace_size(n_pairs: int, W: int, O: int, k: int) -> int:
+    out = _sz(0)
+    f = _typed("ga_autotune_workspace_size", _i, [_u32, _i, _i, _i, ctypes.POINTER(_sz)])
+    _check(f(n_pairs, W, O, k, ctypes.byref(out)), "ga_autotune_workspace_size")
+    return int(out.value)
+
+
+def ga_autotune(d_reads, d_read_off, d_read_len, d_refs, d_ref_off, d_ref_len, n_pairs, W, O, k,
+                d_dist, d_status, d_ref_consumed, d_cigar, d_cigar_off, d_n_runs, d_n_windows,
+                d_cells, d_workspace, ws_bytes, stream=None) -> tuple[ga_tuning, float]:
+    """Times candidate tunings on the given sample and stores the fastest as
+    the default for this device and (W, O, k); returns (tuning, ms)."""
+    f = _typed("ga_autotune", _i, _ALIGN_ARGS + [_vp, _sz, ctypes.POINTER(ga_tuning),
+                                                   ctypes.POINTER(ctypes.c_float), _vp])
+    best = ga_tuning()
+    ms = ctypes.c_float(0)
+    a = _align_args(d_reads, d_read_off, d_read_len, d_refs, d_ref_off, d_ref_len, n_pairs, W, O, k,
+                    d_dist, d_status, d_ref_consumed, d_cigar, d_cigar_off, d_n_runs, d_n_windows,
+                    d_cells)
+    _check(f(*a, _ptr(d_workspace), ws_bytes, ctypes.byref(best), ctypes.byref(ms), _stream(stream)),
+           "ga_autotune")
+    return best, float(ms.value)
+
+
+class GraphHandle:
+    """Owns a ga_graph (one captured pack + align step); see ga_graph_create."""
+
+    def __init__(self, handle: int):
+        self.handle = handle
+
+    def launch(self, stream=None):
+        return ga_graph_launch(self, stream)
+
+    def close(self):
+        if self.handle:
+            ga_graph_destroy(self)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def ga_graph_create(d_ascii_reads, n_read_chars, d_ascii_refs, n_ref_chars, d_reads, d_read_off,
+                    d_read_len, d_refs, d_ref_off, d_ref_len, n_pairs, W, O, k, d_dist, d_status,
+                    d_ref_consumed, d_cigar, d_cigar_off, d_n_runs, d_n_windows, d_cells,
+                    d_workspace, ws_bytes, tuning=None) -> GraphHandle:
+    f = _typed("ga_graph_create", _i,
+               [_vp, _u64, _vp, _u64, _vp, _vp, _vp, _vp, _vp, _vp, _u32, _i, _i, _i,
+                _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, ctypes.POINTER(ga_tuning),
+                ctypes.POINTER(_vp)])
+    out = _vp(0)
+    _check(f(_ptr(d_ascii_reads), n_read_chars, _ptr(d_ascii_refs), n_ref_chars, _ptr(d_reads),
+             _ptr(d_read_off), _ptr(d_read_len), _ptr(d_refs), _ptr(d_ref_off), _ptr(d_ref_len),
+             n_pairs, W, O, k, _ptr(d_dist), _ptr(d_status), _ptr(d_ref_consumed), _ptr(d_cigar),
+             _ptr(d_cigar_off), _ptr(d_n_runs), _ptr(d_n_windows), _ptr(d_cells), _ptr(d_workspace),
+             ws_bytes, ctypes.byref(tuning) if tuning is not None else None, ctypes.byref(out)),
+           "ga_graph_create")
+    return GraphHandle(out.value)
+
+
+def ga_graph_launch(graph: GraphHandle, stream=None) -> int:
+    f = _typed("ga_graph_launch", _i, [_vp, _vp])
+    return _check(f(graph.handle, _stream(stream)), "ga_graph_launch")
+
+
+def ga_graph_destroy(graph: GraphHandle) -> int:
+    f = _typed("ga_graph_destroy", _i, [_vp])
+    rc = f(graph.handle)
+    graph.handle = None
+    return _check(rc, "ga_graph_destroy")

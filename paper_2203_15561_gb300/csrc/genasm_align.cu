@@ -6,6 +6,7 @@
 
 #include <cuda_runtime.h>
 
+#include "genasm.h"
 #include "genasm_internal.h"
 #include "genasm_window.cuh"
 
@@ -275,7 +276,15 @@ static void variant_launch(int G, int K, int blocks, int threads, size_t smem, c
 
 cudaError_t default_tuning(int W, int O, int k, int* G, int* K, int* ppb, int* table_entries,
                            int* lpt) {
-  (void)k;
+  ga_tuning t;
+  if (stored_tuning(W, O, k, &t)) {  // chosen by ga_autotune or set by ga_tuning_set
+    *G = t.lanes_per_pair;
+    *K = t.rows_per_lane;
+    *ppb = t.pairs_per_block;
+    *table_entries = t.table_rows * table_stride(W - O + 1);
+    *lpt = t.lpt >= 0 ? 1 : 0;
+    return cudaSuccess;
+  }
   *G = 16;
   *K = 3;
   *ppb = 2;

@@ -22,6 +22,7 @@ std::atomic<uint64_t> g_launches{0};
 
 uint64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
 void count_launches(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+void uncount_launches(uint64_t n) { g_launches.fetch_sub(n, std::memory_order_relaxed); }
 
 __device__ __forceinline__ uint32_t lop3_xor(uint32_t a, uint32_t b, uint32_t c) {
   uint32_t d;

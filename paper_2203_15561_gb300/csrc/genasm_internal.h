@@ -55,6 +55,11 @@ WorkspaceLayout workspace_layout(uint32_t n_pairs, const BatchPlan& plan);
 // Kernel launches issued by the library (process-wide counter).
 uint64_t launch_count();
 void count_launches(uint64_t n);
+void uncount_launches(uint64_t n);  // kernels that were captured into a graph, not run
+
+// Per-device tuning chosen by the autotuner (or set by the caller).
+bool stored_tuning(int W, int O, int k, struct ga_tuning_s* out);
+void store_tuning(int W, int O, int k, const struct ga_tuning_s* t);
 
 cudaError_t measure_int_peak(double out[3], cudaStream_t s);
 

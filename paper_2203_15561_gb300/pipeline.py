@@ -100,6 +100,37 @@ class DeviceBatch:
         self.pack(stream)
         self.align(kernel, tuning, stats, stream)
 
+    def autotune(self, stream=None):
+        """Runs the library's autotuner on this batch (packed first) and makes
+        its choice the default; returns (tuning, ms)."""
+        from . import ga_autotune, ga_autotune_workspace_size
+        need = ga_autotune_workspace_size(self.n, self.W, self.O, self.k)
+        if need > self.ws_bytes:
+            self.workspace = torch.empty(need, dtype=torch.uint8, device=self.device)
+            self.ws_bytes = need
+        self.pack(stream)
+        best, ms = ga_autotune(*self._args(True), self.workspace, self.ws_bytes, stream)
+        need = ga_workspace_size(self.n, self.W, self.O, self.k)
+        if need > self.ws_bytes:
+            self.workspace = torch.empty(need, dtype=torch.uint8, device=self.device)
+            self.ws_bytes = need
+        return best, ms
+
+    def graph(self, tuning=None, stats: bool = False, pack: bool = True):
+        """A CUDA graph of one step (pack + batched align) on this batch's buffers."""
+        from . import ga_graph_create
+        if tuning is not None:
+            need = ga_workspace_size_tuned(self.n, self.W, self.O, self.k, tuning)
+        else:
+            need = ga_workspace_size(self.n, self.W, self.O, self.k)
+        if need > self.ws_bytes:
+            self.workspace = torch.empty(need, dtype=torch.uint8, device=self.device)
+            self.ws_bytes = need
+        a = self._args(stats)
+        return ga_graph_create(self.ascii_reads if pack else None, self.ascii_reads.numel(),
+                               self.ascii_refs if pack else None, self.ascii_refs.numel(),
+                               *a, self.workspace, self.ws_bytes, tuning)
+
     # -- results ------------------------------------------------------------
     def results(self) -> "HostResult":
         torch.cuda.synchronize(self.device)

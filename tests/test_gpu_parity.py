@@ -169,3 +169,30 @@ def test_cigar_capacity_overflow():
             assert got.status[p] == 0 and got.dist[p] == ref.dist[p]
         else:
             assert got.status[p] == ga.GA_PAIR_CIGAR_FULL and got.dist[p] == -1 and got.n_runs[p] == 0
+
+
+def test_autotune_then_default_matches_oracle():
+    b = datagen.make_batch(2, pair_ids=range(0, 48))
+    ref = oracle.align(b)
+    db = DeviceBatch(b)
+    best, ms = db.autotune()
+    assert ms > 0 and ga.ga_tuning_get(64, 24, 64).lanes_per_pair == best.lanes_per_pair
+    db.run("batched")
+    assert_same(b, db.results(), ref, "autotuned")
+    ga.ga_tuning_set(64, 24, 64, None)  # back to the library default
+    t = ga.ga_tuning_get(64, 24, 64)
+    assert (t.lanes_per_pair, t.rows_per_lane) == (16, 3)
+
+
+def test_graph_step_matches_direct_call():
+    b = datagen.make_batch(4, pair_ids=range(300, 340))
+    ref = oracle.align(b)
+    db = DeviceBatch(b)
+    g = db.graph(stats=True)
+    launches = ga.ga_launch_count()
+    for _ in range(2):
+        db.dist.fill_(-5)
+        g.launch()
+        assert_same(b, db.results(), ref, "graph")
+    assert ga.ga_launch_count() - launches == 2 * 6  # 2 pack + 3 LPT + 1 align per replay
+    g.close()
