@@ -220,6 +220,57 @@ int ga_align_batch_noalloc(const uint8_t* d_reads, const uint64_t* d_read_off,
                            uint32_t* d_n_windows, uint64_t* d_cells, ga_stream_t stream);
 
 /*
+ * Alignment server: continuous batching of alignment requests (the paper
+ * aligns one fixed batch of pairs, Sec. II; serving is a library addition).
+ *
+ * ga_server_create allocates, once, at most budget_bytes of device memory on
+ * the current device: arenas for packed sequences and CIGAR runs, per-pair
+ * slots with saved window state, staging buffers. ga_server_submit copies a
+ * request (host ASCII, like the inputs of ga_pack_2bit; any offsets) and
+ * queues it; it returns GA_ENOMEM if the request could never fit the server.
+ * ga_server_step (synchronous) admits queued requests in arrival order while
+ * the budget has room, advances every admitted pair by at most
+ * `step_windows` windows (default 32) with its window state kept on the
+ * device between steps, and completes every request whose pairs are all done
+ * (results copied to host memory, device space freed). Requests that arrive
+ * while others are in flight join at the next step and share its launch.
+ * ga_server_poll hands out completed requests, oldest first (GA_EAGAIN if
+ * none); a result's arrays stay valid until ga_server_release(ticket).
+ * Results are identical to ga_align_batch's for the same pairs. All calls on
+ * one server must come from one host thread at a time.
+ */
+typedef struct ga_server ga_server;
+typedef struct {
+  uint32_t n_pairs;
+  const uint8_t* reads;      /* host ASCII; read p at reads[read_off[p]], read_len[p] bases */
+  const uint64_t* read_off;
+  const uint32_t* read_len;
+  const uint8_t* refs;       /* host ASCII references, same layout */
+  const uint64_t* ref_off;
+  const uint32_t* ref_len;
+  uint64_t tag;              /* returned with the result */
+} ga_request;
+typedef struct {
+  uint64_t ticket, tag;
+  uint32_t n_pairs;
+  const int32_t* dist;          /* n_pairs, -1 unless status is GA_PAIR_OK */
+  const int32_t* status;        /* n_pairs, GA_PAIR_* */
+  const int32_t* ref_consumed;  /* n_pairs */
+  const uint64_t* cigar_off;    /* n_pairs + 1; pair p's runs are cigar[cigar_off[p]..cigar_off[p+1]) */
+  const uint32_t* cigar;        /* runs, len << 4 | op */
+  double submit_ms, admit_ms, done_ms; /* server clock (ms since creation) */
+} ga_result;
+int ga_server_create(size_t budget_bytes, int W, int O, int k, ga_server** out);
+int ga_server_set_step_windows(ga_server* server, uint32_t step_windows);
+int ga_server_submit(ga_server* server, const ga_request* request, uint64_t* ticket);
+int ga_server_step(ga_server* server, uint32_t* n_in_flight);
+int ga_server_poll(ga_server* server, ga_result* out, int max, int* n_out);
+int ga_server_release(ga_server* server, uint64_t ticket);
+int ga_server_pending(ga_server* server, uint32_t* waiting, uint32_t* active_pairs,
+                      uint64_t* device_bytes);
+int ga_server_destroy(ga_server* server);
+
+/*
  * ga_cigar_compact - CIGAR writer, final pass: gathers the runs the alignment
  * wrote at per-pair capacities (d_cigar, d_cigar_off, d_n_runs as given to
  * ga_align_batch) into one dense array. d_out_off (n_pairs + 1 uint64)

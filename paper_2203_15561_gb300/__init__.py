@@ -330,3 +330,73 @@ def ga_graph_destroy(graph: GraphHandle) -> int:
     rc = f(graph.handle)
     graph.handle = None
     return _check(rc, "ga_graph_destroy")
+
+
+class ga_request(ctypes.Structure):
+    _fields_ = [("n_pairs", _u32), ("reads", _vp), ("read_off", _vp), ("read_len", _vp),
+                ("refs", _vp), ("ref_off", _vp), ("ref_len", _vp), ("tag", _u64)]
+
+
+class ga_result(ctypes.Structure):
+    _fields_ = [("ticket", _u64), ("tag", _u64), ("n_pairs", _u32),
+                ("dist", ctypes.POINTER(ctypes.c_int32)), ("status", ctypes.POINTER(ctypes.c_int32)),
+                ("ref_consumed", ctypes.POINTER(ctypes.c_int32)),
+                ("cigar_off", ctypes.POINTER(ctypes.c_uint64)),
+                ("cigar", ctypes.POINTER(ctypes.c_uint32)),
+                ("submit_ms", ctypes.c_double), ("admit_ms", ctypes.c_double),
+                ("done_ms", ctypes.c_double)]
+
+
+def ga_server_create(budget_bytes: int, W: int = 64, O: int = 24, k: int = 64) -> int:
+    f = _typed("ga_server_create", _i, [_sz, _i, _i, _i, ctypes.POINTER(_vp)])
+    out = _vp(0)
+    _check(f(budget_bytes, W, O, k, ctypes.byref(out)), "ga_server_create")
+    return out.value
+
+
+def ga_server_set_step_windows(server: int, step_windows: int) -> int:
+    f = _typed("ga_server_set_step_windows", _i, [_vp, _u32])
+    return _check(f(server, step_windows), "ga_server_set_step_windows")
+
+
+def ga_server_submit(server: int, request: ga_request) -> int:
+    f = _typed("ga_server_submit", _i, [_vp, ctypes.POINTER(ga_request), ctypes.POINTER(_u64)])
+    t = _u64(0)
+    _check(f(server, ctypes.byref(request), ctypes.byref(t)), "ga_server_submit")
+    return int(t.value)
+
+
+def ga_server_step(server: int) -> int:
+    """Runs one server step; returns the number of requests' pairs still in flight."""
+    f = _typed("ga_server_step", _i, [_vp, ctypes.POINTER(_u32)])
+    n = _u32(0)
+    _check(f(server, ctypes.byref(n)), "ga_server_step")
+    return int(n.value)
+
+
+def ga_server_poll(server: int, max_results: int = 256) -> list:
+    f = _typed("ga_server_poll", _i, [_vp, ctypes.POINTER(ga_result), _i, ctypes.POINTER(_i)])
+    buf = (ga_result * max_results)()
+    n = _i(0)
+    rc = f(server, buf, max_results, ctypes.byref(n))
+    if rc not in (GA_OK, GA_EAGAIN):
+        _check(rc, "ga_server_poll")
+    return [buf[q] for q in range(n.value)]
+
+
+def ga_server_release(server: int, ticket: int) -> int:
+    f = _typed("ga_server_release", _i, [_vp, _u64])
+    return _check(f(server, ticket), "ga_server_release")
+
+
+def ga_server_pending(server: int) -> tuple[int, int, int]:
+    f = _typed("ga_server_pending", _i, [_vp, ctypes.POINTER(_u32), ctypes.POINTER(_u32),
+                                          ctypes.POINTER(_u64)])
+    w, a, b = _u32(0), _u32(0), _u64(0)
+    _check(f(server, ctypes.byref(w), ctypes.byref(a), ctypes.byref(b)), "ga_server_pending")
+    return int(w.value), int(a.value), int(b.value)
+
+
+def ga_server_destroy(server: int) -> int:
+    f = _typed("ga_server_destroy", _i, [_vp])
+    return _check(f(server), "ga_server_destroy")

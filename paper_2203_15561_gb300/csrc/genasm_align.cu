@@ -48,7 +48,7 @@ __device__ __forceinline__ void begin_pair(const AlignParams& p, uint32_t pair, 
   st.read = p.reads + p.read_off[pair];
   st.ref = p.refs + p.ref_off[pair];
   const uint64_t c0 = p.cigar_off[pair];
-  const uint64_t capl = p.cigar_off[pair + 1] - c0;
+  const uint64_t capl = p.cigar_cap ? p.cigar_cap[pair] : p.cigar_off[pair + 1] - c0;
   st.rw = RunWriter{p.cigar + c0, capl > 0xffffffffull ? 0xffffffffu : static_cast<uint32_t>(capl),
                     0u, 0u, 0u, false};
   st.cells = 0;
@@ -363,6 +363,119 @@ cudaError_t launch_batched(const AlignParams& p, const BatchPlan& plan, void* ws
                  p, a);
   count_launches(1);
   return cudaGetLastError();
+}
+
+}  // namespace ga
+
+// ---------------------------------------------------------------------------
+// Serving step: resumable alignment. Every pair in the active list advances by
+// at most `max_windows` windows; its window state (positions, edit count,
+// statistics and the open CIGAR run) is kept in device memory between steps,
+// so pairs admitted at different times share one launch.
+// ---------------------------------------------------------------------------
+
+namespace ga {
+
+__device__ __forceinline__ void resume_pair(const AlignParams& p, uint32_t slot,
+                                            const SlotState& s, PairState& st, bool writer) {
+  begin_pair(p, slot, st, writer);  // a fresh slot (all zero) starts here
+  if (!st.busy) return;             // empty read: already finished
+  st.pos_p = s.pos_p;
+  st.pos_t = s.pos_t;
+  st.edits = s.edits;
+  st.windows = s.windows;
+  st.cells = s.cells;
+  st.rw.n = s.runs;
+  st.rw.op = s.run_op;
+  st.rw.len = s.run_len;
+}
+
+__device__ __forceinline__ void save_pair(const PairState& st, SlotState& s) {
+  s.pos_p = st.pos_p;
+  s.pos_t = st.pos_t;
+  s.edits = st.edits;
+  s.windows = st.windows;
+  s.cells = st.cells;
+  s.runs = st.rw.n;
+  s.run_op = st.rw.op;
+  s.run_len = st.rw.len;
+}
+
+template <int G, int K>
+__global__ void __launch_bounds__(256, 1) align_step_kernel(const AlignParams p, const StepArgs a) {
+  extern __shared__ __align__(16) uint64_t smem[];
+  const int lane = threadIdx.x & 31;
+  const int group_in_block = threadIdx.x / G;
+  const int r = lane % G;
+  const int gbase = lane - r;
+  const size_t group_words = sizeof(GroupSmem) / sizeof(uint64_t) + a.table_entries;
+  uint64_t* base = smem + group_in_block * group_words;
+  GroupSmem* gs = reinterpret_cast<GroupSmem*>(base);
+  uint64_t* table = base + sizeof(GroupSmem) / sizeof(uint64_t);
+  const size_t group_id = static_cast<size_t>(blockIdx.x) * (blockDim.x / G) + group_in_block;
+  uint64_t* spill = a.spill + group_id * kSpillEntries;
+  PairState st;
+  st.busy = false;
+  bool drained = false;
+  uint32_t slot = 0, budget = 0;
+  for (;;) {
+    const bool want = !st.busy && !drained;
+    uint32_t idx = 0xffffffffu;
+    if (want && r == 0) idx = atomicAdd(&a.counters[0], 1u);
+    idx = __shfl_sync(kFull, idx, gbase);
+    bool finished = false;
+    if (want) {
+      if (idx < a.n_active) {
+        slot = a.active[idx];
+        resume_pair(p, slot, a.state[slot], st, r == 0);
+        budget = a.max_windows;
+        finished = !st.busy;
+      } else {
+        drained = true;
+      }
+    }
+    if (!__any_sync(kFull, st.busy || !drained || finished)) break;
+    const bool was_busy = st.busy;
+    if (__any_sync(kFull, st.busy)) step_window<G, K>(p, r, gbase, st, gs, table, a.table_entries, spill);
+    if (was_busy) {
+      if (!st.busy) {
+        finished = true;
+      } else if (--budget == 0) {
+        if (r == 0) save_pair(st, a.state[slot]);
+        st.busy = false;  // resumes at the next step
+      }
+    }
+    if (finished && r == 0) a.done[atomicAdd(&a.counters[1], 1u)] = slot;
+  }
+}
+
+#define GA_STEP_VARIANTS(X) X(8, 5) X(16, 3) X(32, 2)
+
+cudaError_t launch_step(const AlignParams& p, const BatchPlan& plan, const StepArgs& a,
+                        cudaStream_t s) {
+  if (a.n_active == 0) return cudaSuccess;
+  const int threads = plan.pairs_per_block * plan.lanes_per_pair;
+  cudaError_t e = cudaErrorInvalidValue;
+#define GA_STEP_LAUNCH(g, k)                                                                      \
+  if (plan.lanes_per_pair == g && plan.rows_per_lane == k) {                                      \
+    e = cudaFuncSetAttribute(align_step_kernel<g, k>,                                             \
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,                         \
+                             static_cast<int>(plan.smem_bytes));                                  \
+    if (e != cudaSuccess) return e;                                                               \
+    align_step_kernel<g, k><<<plan.blocks, threads, plan.smem_bytes, s>>>(p, a);                  \
+    e = cudaGetLastError();                                                                       \
+  }
+  GA_STEP_VARIANTS(GA_STEP_LAUNCH)
+#undef GA_STEP_LAUNCH
+  if (e == cudaSuccess) count_launches(1);
+  return e;
+}
+
+bool step_variant_exists(int G, int K) {
+#define GA_STEP_EXISTS(g, k) if (G == g && K == k) return true;
+  GA_STEP_VARIANTS(GA_STEP_EXISTS)
+#undef GA_STEP_EXISTS
+  return false;
 }
 
 }  // namespace ga

@@ -26,6 +26,7 @@ struct AlignParams {
   uint32_t* n_runs;
   uint32_t* n_windows;  // optional
   uint64_t* cells;      // optional
+  const uint32_t* cigar_cap;  // optional per-pair CIGAR capacity (else cigar_off[p+1] - cigar_off[p])
 };
 
 // Resolved tuning of the batched kernel.
@@ -49,6 +50,28 @@ struct WorkspaceLayout {
 };
 
 constexpr int kLptBuckets = 1024;
+
+// Saved window state of one pair between serving steps (all zero = fresh).
+struct SlotState {
+  uint32_t pos_p, pos_t, edits, windows;
+  uint64_t cells;
+  uint32_t runs, run_op, run_len, pad;
+};
+
+struct StepArgs {
+  const uint32_t* active;  // slots to advance this step
+  uint32_t n_active;
+  uint32_t* counters;      // [0] work counter, [1] finished count (both zeroed per step)
+  SlotState* state;        // per slot
+  uint32_t* done;          // slots that finished this step
+  uint64_t* spill;         // [groups][65 * 66]
+  int table_entries;
+  uint32_t max_windows;
+};
+
+cudaError_t launch_step(const AlignParams& p, const BatchPlan& plan, const StepArgs& a,
+                        cudaStream_t s);
+bool step_variant_exists(int G, int K);
 
 WorkspaceLayout workspace_layout(uint32_t n_pairs, const BatchPlan& plan);
 

@@ -1,0 +1,613 @@
+// Alignment server: continuous batching of alignment requests on one GPU.
+//
+// A request (1..n pairs, host ASCII) is copied at submission and waits until
+// the device-memory budget has room for it: its packed sequences, its CIGAR
+// capacity (read+ref+1 runs per pair) and one slot per pair, all carved from
+// arenas allocated once at creation. Each ga_server_step
+//   1. admits waiting requests in arrival order while they fit: H2D of their
+//      ASCII through a pinned staging buffer, 2-bit packing into the arena,
+//      per-slot metadata, zeroed window state;
+//   2. launches the resumable step kernel over every admitted, unfinished
+//      pair: each advances by at most `max_windows` windows and keeps its
+//      window state (positions, edit count, open CIGAR run) on the device;
+//   3. reads back which pairs finished, and for every request whose pairs
+//      are all done gathers the CIGAR runs into one buffer, copies distances,
+//      statuses and runs to host memory and frees the request's device space.
+// Requests admitted at different steps therefore share launches and overlap
+// on the device, and a finished request's memory is reused at the next step.
+// Every wait is a host-side stream synchronization; no kernel waits on
+// another.
+#include <algorithm>
+#include <chrono>
+#include <cstdlib>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "genasm.h"
+#include "genasm_internal.h"
+#include "genasm_window.cuh"
+
+namespace {
+
+// First-fit allocator of [0, capacity) in units, with coalescing on release.
+class RangeAlloc {
+ public:
+  explicit RangeAlloc(uint64_t cap = 0) : cap_(cap) {
+    if (cap) free_[0] = cap;
+  }
+  bool alloc(uint64_t n, uint64_t* off) {
+    if (n == 0) {
+      *off = 0;
+      return true;
+    }
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second >= n) {
+        const uint64_t o = it->first, rest = it->second - n;
+        free_.erase(it);
+        if (rest) free_[o + n] = rest;
+        *off = o;
+        return true;
+      }
+    }
+    return false;
+  }
+  void release(uint64_t off, uint64_t n) {
+    if (n == 0) return;
+    auto next = free_.lower_bound(off);
+    if (next != free_.end() && off + n == next->first) {
+      n += next->second;
+      next = free_.erase(next);
+    }
+    if (next != free_.begin()) {
+      auto prev = std::prev(next);
+      if (prev->first + prev->second == off) {
+        prev->second += n;
+        return;
+      }
+    }
+    free_[off] = n;
+  }
+  uint64_t capacity() const { return cap_; }
+
+ private:
+  uint64_t cap_;
+  std::map<uint64_t, uint64_t> free_;
+};
+
+struct Request {
+  uint64_t ticket = 0, tag = 0;
+  uint32_t n = 0;
+  std::vector<uint8_t> ascii;  // every sequence 4-aligned: reads then references
+  std::vector<uint64_t> read_at, ref_at;  // ASCII offsets inside `ascii`
+  std::vector<uint32_t> read_len, ref_len;
+  uint64_t runs = 0;            // CIGAR capacity: sum of read + ref + 1
+  uint64_t seq_off = 0, cig_off = 0, slot0 = 0;
+  uint32_t done = 0;
+  double t_submit = 0, t_admit = 0;
+};
+
+struct Result {
+  ga_result pub{};
+  std::vector<int32_t> dist, status, ref_consumed;
+  std::vector<uint64_t> cigar_off;
+  std::vector<uint32_t> cigar;
+};
+
+__global__ void gather_list_kernel(const uint32_t* __restrict__ src, const uint64_t* __restrict__ list,
+                                   uint32_t n, uint32_t* __restrict__ dst) {
+  // list: per pair (src offset, dst offset, count) as three uint64.
+  const uint32_t lane = threadIdx.x & 31;
+  const uint64_t warps = (static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5;
+  for (uint64_t p = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; p < n;
+       p += warps) {
+    const uint64_t s = list[3 * p], d = list[3 * p + 1], c = list[3 * p + 2];
+    for (uint64_t x = lane; x < c; x += 32) dst[d + x] = src[s + x];
+  }
+}
+
+double now_ms(std::chrono::steady_clock::time_point t0) {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
+
+}  // namespace
+
+struct ga_server {
+  int W = 64, O = 24, k = 64, device = 0;
+  uint32_t max_windows = 32;
+  ga::BatchPlan plan{};
+  cudaStream_t stream = nullptr;
+  std::chrono::steady_clock::time_point t0;
+  // device arenas
+  uint8_t* d_seq = nullptr;      // packed sequences
+  uint32_t* d_cigar = nullptr;   // per-pair CIGAR runs
+  uint8_t* d_ascii = nullptr;    // staging for packing
+  uint64_t ascii_cap = 0;
+  // per-slot arrays
+  uint32_t max_slots = 0;
+  uint64_t *d_read_off = nullptr, *d_ref_off = nullptr, *d_cigar_off = nullptr, *d_cells = nullptr;
+  uint32_t *d_read_len = nullptr, *d_ref_len = nullptr, *d_cigar_cap = nullptr;
+  int32_t *d_dist = nullptr, *d_status = nullptr, *d_ref_consumed = nullptr;
+  uint32_t *d_n_runs = nullptr, *d_n_windows = nullptr;
+  ga::SlotState* d_state = nullptr;
+  uint32_t *d_active = nullptr, *d_done = nullptr, *d_counters = nullptr;
+  uint64_t* d_spill = nullptr;
+  uint64_t* d_list = nullptr;    // gather list (3 x uint64 per pair)
+  uint32_t* d_out = nullptr;     // gathered runs of finished requests
+  uint64_t out_cap = 0;
+  // pinned host staging
+  uint8_t* h_ascii = nullptr;
+  uint64_t* h_meta64 = nullptr;  // 3 arrays of max_slots uint64 (read_off, ref_off, cigar_off)
+  uint32_t* h_meta32 = nullptr;  // 3 arrays of max_slots uint32 (read_len, ref_len, cigar_cap)
+  uint32_t *h_active = nullptr, *h_done = nullptr, *h_counters = nullptr;
+  uint64_t* h_list = nullptr;
+  uint32_t* h_out = nullptr;
+  int32_t* h_small = nullptr;    // 4 arrays of max_slots (dist, status, ref_consumed, n_runs)
+  // bookkeeping
+  RangeAlloc seq_alloc, cig_alloc, slot_alloc;
+  std::deque<Request*> pending;
+  std::vector<Request*> slot_owner;  // per slot
+  std::vector<uint32_t> active;
+  std::deque<Result*> ready;
+  std::map<uint64_t, Result*> handed_out;
+  uint64_t next_ticket = 1;
+  uint64_t bytes_total = 0;
+};
+
+namespace {
+
+template <typename T>
+cudaError_t dev_alloc(ga_server* s, T** p, uint64_t count) {
+  const uint64_t bytes = std::max<uint64_t>(count, 1) * sizeof(T);
+  s->bytes_total += bytes;
+  return cudaMalloc(reinterpret_cast<void**>(p), bytes);
+}
+
+void server_free(ga_server* s) {
+  cudaFree(s->d_seq);
+  cudaFree(s->d_cigar);
+  cudaFree(s->d_ascii);
+  cudaFree(s->d_read_off);
+  cudaFree(s->d_ref_off);
+  cudaFree(s->d_cigar_off);
+  cudaFree(s->d_cells);
+  cudaFree(s->d_read_len);
+  cudaFree(s->d_ref_len);
+  cudaFree(s->d_cigar_cap);
+  cudaFree(s->d_dist);
+  cudaFree(s->d_status);
+  cudaFree(s->d_ref_consumed);
+  cudaFree(s->d_n_runs);
+  cudaFree(s->d_n_windows);
+  cudaFree(s->d_state);
+  cudaFree(s->d_active);
+  cudaFree(s->d_done);
+  cudaFree(s->d_counters);
+  cudaFree(s->d_spill);
+  cudaFree(s->d_list);
+  cudaFree(s->d_out);
+  cudaFreeHost(s->h_ascii);
+  cudaFreeHost(s->h_meta64);
+  cudaFreeHost(s->h_meta32);
+  cudaFreeHost(s->h_active);
+  cudaFreeHost(s->h_done);
+  cudaFreeHost(s->h_counters);
+  cudaFreeHost(s->h_list);
+  cudaFreeHost(s->h_out);
+  cudaFreeHost(s->h_small);
+  if (s->stream) cudaStreamDestroy(s->stream);
+  for (Request* r : s->pending) delete r;
+  std::vector<Request*> owners;  // admitted, unfinished requests
+  for (Request* r : s->slot_owner)
+    if (r) owners.push_back(r);
+  std::sort(owners.begin(), owners.end());
+  owners.erase(std::unique(owners.begin(), owners.end()), owners.end());
+  for (Request* r : owners) delete r;
+  for (Result* r : s->ready) delete r;
+  for (auto& kv : s->handed_out) delete kv.second;
+}
+
+constexpr uint64_t kAsciiStaging = 64ull << 20;  // ASCII bytes admitted per step (at most)
+constexpr uint64_t kOutRuns = 16ull << 20;        // runs gathered per step (at most, 64 MB)
+constexpr uint64_t kListPairs = 1ull << 16;       // pairs harvested per step (at most)
+
+}  // namespace
+
+extern "C" int ga_server_create(size_t budget_bytes, int W, int O, int k, ga_server** out) {
+  if (!out || W < 1 || W > GA_MAX_W || O < 0 || O >= W || k < 0) return GA_EINVAL;
+  ga_server* s = new ga_server();
+  s->W = W;
+  s->O = O;
+  s->k = k;
+  s->t0 = std::chrono::steady_clock::now();
+  cudaError_t e = cudaGetDevice(&s->device);
+  // Step kernel tuning: the stored/default tuning when it has a step variant.
+  ga_tuning t{};
+  int G = 8, K = 5, ppb = 8, rows = 38;
+  if (ga_tuning_get(W, O, k, &t) == GA_OK && ga::step_variant_exists(t.lanes_per_pair, t.rows_per_lane)) {
+    G = t.lanes_per_pair;
+    K = t.rows_per_lane;
+    ppb = t.pairs_per_block;
+    rows = t.table_rows;
+  }
+  if (e == cudaSuccess)
+    e = ga::resolve_plan(W, O, k, G, K, ppb, rows * ga::table_stride(W - O + 1), 1, &s->plan);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+  // Fixed parts first, then the arenas from what is left of the budget.
+  const uint64_t groups = static_cast<uint64_t>(s->plan.blocks) * s->plan.pairs_per_block;
+  const uint64_t spill_bytes = groups * 8ull * ga::kMaxRows * ga::kMaxStride;
+  s->max_slots = static_cast<uint32_t>(std::min<uint64_t>(1u << 20, budget_bytes / 8192 + 64));
+  const uint64_t per_slot = 8 * 4 + 4 * 6 + 4 * 2 + sizeof(ga::SlotState);
+  const uint64_t fixed = spill_bytes + kAsciiStaging + kOutRuns * 4 + kListPairs * 24 +
+                         static_cast<uint64_t>(s->max_slots) * per_slot;
+  if (e == cudaSuccess && budget_bytes < fixed + (64ull << 20)) {
+    server_free(s);
+    delete s;
+    return GA_ENOMEM;
+  }
+  const uint64_t arena = budget_bytes - fixed;
+  const uint64_t seq_bytes = arena / 17;                  // 0.25 B per base
+  const uint64_t cig_runs = (arena - seq_bytes) / 4;      // 4 B per run
+  const uint32_t M = s->max_slots;
+  if (e == cudaSuccess) e = dev_alloc(s, &s->d_seq, seq_bytes);
+  if (e == cudaSuccess) e = dev_alloc(s, &s->d_cigar, cig_runs);
+  if (e == cudaSuccess) e = dev_alloc(s, &s->d_ascii, kAsciiStaging);
+  if (e == cudaSuccess) e = dev_alloc(s, &s->d_read_off, M);
+  if (e == cudaSuccess) e = dev_alloc(s, &s->d_ref_off, M);
+  if (e == cudaSuccess) e = dev_alloc(s, &s->d_cigar_off, M);
+  if (e == cudaSuccess) e = dev_alloc(s, &s->d_cells, M);
+  if (e == cudaSuccess) e = dev_alloc(s, &s->d_read_len, M);
+  if (e == cudaSuccess) e = dev_alloc(s, &s->d_ref_len, M);
+  if (e == cudaSuccess) e = dev_alloc(s, &s->d_cigar_cap, M);
+  if (e == cudaSuccess) e = dev_alloc(s, &s->d_dist, M);
+  if (e == cudaSuccess) e = dev_alloc(s, &s->d_status, M);
+  if (e == cudaSuccess) e = dev_alloc(s, &s->d_ref_consumed, M);
+  if (e == cudaSuccess) e = dev_alloc(s, &s->d_n_runs, M);
+  if (e == cudaSuccess) e = dev_alloc(s, &s->d_n_windows, M);
+  if (e == cudaSuccess) e = dev_alloc(s, &s->d_state, M);
+  if (e == cudaSuccess) e = dev_alloc(s, &s->d_active, M);
+  if (e == cudaSuccess) e = dev_alloc(s, &s->d_done, M);
+  if (e == cudaSuccess) e = dev_alloc(s, &s->d_counters, 64);
+  if (e == cudaSuccess) e = dev_alloc(s, &s->d_spill, spill_bytes / 8);
+  if (e == cudaSuccess) e = dev_alloc(s, &s->d_list, 3 * kListPairs);
+  if (e == cudaSuccess) e = dev_alloc(s, &s->d_out, kOutRuns);
+  if (e == cudaSuccess) e = cudaMallocHost(&s->h_ascii, kAsciiStaging);
+  if (e == cudaSuccess) e = cudaMallocHost(&s->h_meta64, 8ull * 3 * M);
+  if (e == cudaSuccess) e = cudaMallocHost(&s->h_meta32, 4ull * 3 * M);
+  if (e == cudaSuccess) e = cudaMallocHost(&s->h_active, 4ull * M);
+  if (e == cudaSuccess) e = cudaMallocHost(&s->h_done, 4ull * M);
+  if (e == cudaSuccess) e = cudaMallocHost(&s->h_counters, 4ull * 64);
+  if (e == cudaSuccess) e = cudaMallocHost(&s->h_list, 24ull * kListPairs);
+  if (e == cudaSuccess) e = cudaMallocHost(&s->h_out, 4ull * kOutRuns);
+  if (e == cudaSuccess) e = cudaMallocHost(&s->h_small, 16ull * M);
+  if (e != cudaSuccess) {
+    server_free(s);
+    delete s;
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? GA_ENOMEM : GA_ECUDA;
+  }
+  s->ascii_cap = kAsciiStaging;
+  s->out_cap = kOutRuns;
+  s->seq_alloc = RangeAlloc(seq_bytes);
+  s->cig_alloc = RangeAlloc(cig_runs);
+  s->slot_alloc = RangeAlloc(M);
+  s->slot_owner.assign(M, nullptr);
+  *out = s;
+  return GA_OK;
+}
+
+extern "C" int ga_server_set_step_windows(ga_server* s, uint32_t max_windows) {
+  if (!s || max_windows == 0) return GA_EINVAL;
+  s->max_windows = max_windows;
+  return GA_OK;
+}
+
+extern "C" int ga_server_submit(ga_server* s, const ga_request* req, uint64_t* ticket) {
+  if (!s || !req || (req->n_pairs > 0 && (!req->reads || !req->read_off || !req->read_len ||
+                                           !req->refs || !req->ref_off || !req->ref_len)))
+    return GA_EINVAL;
+  Request* r = new Request();
+  r->n = req->n_pairs;
+  r->tag = req->tag;
+  uint64_t bytes = 0;
+  for (uint32_t p = 0; p < r->n; ++p) bytes += (req->read_len[p] + 3ull) / 4 * 4 + (req->ref_len[p] + 3ull) / 4 * 4;
+  r->ascii.resize(std::max<uint64_t>(bytes, 4), 'A');
+  r->read_at.resize(r->n);
+  r->ref_at.resize(r->n);
+  r->read_len.assign(req->read_len, req->read_len + r->n);
+  r->ref_len.assign(req->ref_len, req->ref_len + r->n);
+  uint64_t at = 0;
+  for (uint32_t p = 0; p < r->n; ++p) {
+    r->read_at[p] = at;
+    std::memcpy(&r->ascii[at], req->reads + req->read_off[p], req->read_len[p]);
+    at += (req->read_len[p] + 3ull) / 4 * 4;
+    r->ref_at[p] = at;
+    std::memcpy(&r->ascii[at], req->refs + req->ref_off[p], req->ref_len[p]);
+    at += (req->ref_len[p] + 3ull) / 4 * 4;
+    r->runs += static_cast<uint64_t>(req->read_len[p]) + req->ref_len[p] + 1;
+  }
+  // A request that could never fit the server is refused now.
+  if (r->n > s->slot_alloc.capacity() || r->runs > s->cig_alloc.capacity() ||
+      r->ascii.size() / 4 > s->seq_alloc.capacity() || r->ascii.size() > s->ascii_cap ||
+      r->runs > s->out_cap || r->n > kListPairs) {
+    delete r;
+    return GA_ENOMEM;
+  }
+  r->ticket = s->next_ticket++;
+  r->t_submit = now_ms(s->t0);
+  s->pending.push_back(r);
+  if (ticket) *ticket = r->ticket;
+  return GA_OK;
+}
+
+namespace {
+
+// Step 1: admission of waiting requests, in arrival order, while they fit.
+int admit(ga_server* s) {
+  uint64_t staged = 0;
+  std::vector<Request*> batch;
+  while (!s->pending.empty()) {
+    Request* r = s->pending.front();
+    const uint64_t abytes = r->ascii.size();
+    if (staged + abytes > s->ascii_cap) break;
+    uint64_t so = 0, co = 0, sl = 0;
+    if (!s->seq_alloc.alloc(abytes / 4, &so)) break;
+    if (!s->cig_alloc.alloc(r->runs, &co)) {
+      s->seq_alloc.release(so, abytes / 4);
+      break;
+    }
+    if (!s->slot_alloc.alloc(r->n, &sl)) {
+      s->seq_alloc.release(so, abytes / 4);
+      s->cig_alloc.release(co, r->runs);
+      break;
+    }
+    r->seq_off = so;
+    r->cig_off = co;
+    r->slot0 = sl;
+    r->t_admit = now_ms(s->t0);
+    std::memcpy(s->h_ascii + staged, r->ascii.data(), abytes);
+    staged += abytes;
+    batch.push_back(r);
+    s->pending.pop_front();
+  }
+  if (batch.empty()) return GA_OK;
+  cudaStream_t st = s->stream;
+  if (cudaMemcpyAsync(s->d_ascii, s->h_ascii, staged, cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return GA_ECUDA;
+  const uint32_t M = s->max_slots;
+  uint64_t aoff = 0;
+  for (Request* r : batch) {
+    const uint64_t abytes = r->ascii.size();
+    if (ga::launch_pack(s->d_ascii + aoff, abytes, s->d_seq + r->seq_off, nullptr, st) != cudaSuccess)
+      return GA_ECUDA;
+    uint64_t* m64 = s->h_meta64;
+    uint32_t* m32 = s->h_meta32;
+    uint64_t c = r->cig_off;
+    for (uint32_t p = 0; p < r->n; ++p) {
+      const uint64_t slot = r->slot0 + p;
+      m64[slot] = r->seq_off + r->read_at[p] / 4;
+      m64[M + slot] = r->seq_off + r->ref_at[p] / 4;
+      m64[2ull * M + slot] = c;
+      m32[slot] = r->read_len[p];
+      m32[M + slot] = r->ref_len[p];
+      m32[2ull * M + slot] = r->read_len[p] + r->ref_len[p] + 1;
+      c += r->read_len[p] + static_cast<uint64_t>(r->ref_len[p]) + 1;
+      s->slot_owner[slot] = r;
+      s->active.push_back(static_cast<uint32_t>(slot));
+    }
+    const uint64_t a = r->slot0, n = r->n;
+    cudaMemcpyAsync(s->d_read_off + a, m64 + a, 8 * n, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(s->d_ref_off + a, m64 + M + a, 8 * n, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(s->d_cigar_off + a, m64 + 2ull * M + a, 8 * n, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(s->d_read_len + a, m32 + a, 4 * n, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(s->d_ref_len + a, m32 + M + a, 4 * n, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(s->d_cigar_cap + a, m32 + 2ull * M + a, 4 * n, cudaMemcpyHostToDevice, st);
+    if (cudaMemsetAsync(s->d_state + a, 0, sizeof(ga::SlotState) * n, st) != cudaSuccess)
+      return GA_ECUDA;
+    aoff += abytes;
+  }
+  return GA_OK;
+}
+
+// Step 3: results of requests whose pairs are all done.
+int harvest(ga_server* s, const std::vector<Request*>& finished) {
+  if (finished.empty()) return GA_OK;
+  cudaStream_t st = s->stream;
+  const uint32_t M = s->max_slots;
+  int32_t* hs = s->h_small;
+  for (Request* r : finished) {
+    const uint64_t a = r->slot0, n = r->n;
+    cudaMemcpyAsync(hs + a, s->d_dist + a, 4 * n, cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(hs + M + a, s->d_status + a, 4 * n, cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(hs + 2ull * M + a, s->d_ref_consumed + a, 4 * n, cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(hs + 3ull * M + a, s->d_n_runs + a, 4 * n, cudaMemcpyDeviceToHost, st);
+  }
+  if (cudaStreamSynchronize(st) != cudaSuccess) return GA_ECUDA;
+  // One gather of every finished pair's runs, then one copy to the host.
+  uint64_t pairs = 0, total = 0;
+  size_t first = 0;
+  while (first < finished.size()) {
+    size_t last = first;
+    pairs = 0;
+    total = 0;
+    for (; last < finished.size(); ++last) {
+      Request* r = finished[last];
+      uint64_t runs = 0;
+      for (uint32_t p = 0; p < r->n; ++p) runs += static_cast<uint32_t>(hs[3ull * M + r->slot0 + p]);
+      if (last > first && (pairs + r->n > kListPairs || total + runs > s->out_cap)) break;
+      uint64_t c = r->cig_off;
+      for (uint32_t p = 0; p < r->n; ++p) {
+        const uint32_t cnt = static_cast<uint32_t>(hs[3ull * M + r->slot0 + p]);
+        s->h_list[3 * pairs] = c;
+        s->h_list[3 * pairs + 1] = total;
+        s->h_list[3 * pairs + 2] = cnt;
+        c += r->read_len[p] + static_cast<uint64_t>(r->ref_len[p]) + 1;
+        total += cnt;
+        ++pairs;
+      }
+    }
+    if (pairs > 0) {
+      if (cudaMemcpyAsync(s->d_list, s->h_list, 24 * pairs, cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return GA_ECUDA;
+      int sms = 0;
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
+      const uint64_t want = (pairs * 32 + 255) / 256;
+      const int blocks = static_cast<int>(std::max<uint64_t>(1, std::min<uint64_t>(want, 8ull * sms)));
+      gather_list_kernel<<<blocks, 256, 0, st>>>(s->d_cigar, s->d_list, static_cast<uint32_t>(pairs),
+                                                 s->d_out);
+      ga::count_launches(1);
+      if (total > 0 &&
+          cudaMemcpyAsync(s->h_out, s->d_out, 4 * total, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return GA_ECUDA;
+      if (cudaStreamSynchronize(st) != cudaSuccess) return GA_ECUDA;
+    }
+    uint64_t pos = 0;
+    for (size_t q = first; q < last; ++q) {
+      Request* r = finished[q];
+      Result* res = new Result();
+      const uint64_t a = r->slot0, n = r->n;
+      res->dist.assign(hs + a, hs + a + n);
+      res->status.assign(hs + M + a, hs + M + a + n);
+      res->ref_consumed.assign(hs + 2ull * M + a, hs + 2ull * M + a + n);
+      res->cigar_off.resize(n + 1);
+      res->cigar_off[0] = 0;
+      for (uint64_t p = 0; p < n; ++p)
+        res->cigar_off[p + 1] = res->cigar_off[p] + static_cast<uint32_t>(hs[3ull * M + a + p]);
+      res->cigar.assign(s->h_out + pos, s->h_out + pos + res->cigar_off[n]);
+      pos += res->cigar_off[n];
+      res->pub.ticket = r->ticket;
+      res->pub.tag = r->tag;
+      res->pub.n_pairs = r->n;
+      res->pub.dist = res->dist.data();
+      res->pub.status = res->status.data();
+      res->pub.ref_consumed = res->ref_consumed.data();
+      res->pub.cigar_off = res->cigar_off.data();
+      res->pub.cigar = res->cigar.data();
+      res->pub.submit_ms = r->t_submit;
+      res->pub.admit_ms = r->t_admit;
+      res->pub.done_ms = now_ms(s->t0);
+      s->ready.push_back(res);
+      s->seq_alloc.release(r->seq_off, r->ascii.size() / 4);
+      s->cig_alloc.release(r->cig_off, r->runs);
+      s->slot_alloc.release(r->slot0, r->n);
+      for (uint64_t p = 0; p < n; ++p) s->slot_owner[a + p] = nullptr;
+      delete r;
+    }
+    first = last;
+  }
+  return GA_OK;
+}
+
+}  // namespace
+
+extern "C" int ga_server_step(ga_server* s, uint32_t* n_active) {
+  if (!s) return GA_EINVAL;
+  int rc = admit(s);
+  if (rc != GA_OK) return rc;
+  cudaStream_t st = s->stream;
+  std::vector<Request*> finished;
+  // Requests with no pairs finish at admission.
+  if (!s->active.empty()) {
+    const uint32_t na = static_cast<uint32_t>(s->active.size());
+    std::memcpy(s->h_active, s->active.data(), 4ull * na);
+    if (cudaMemcpyAsync(s->d_active, s->h_active, 4ull * na, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemsetAsync(s->d_counters, 0, 8, st) != cudaSuccess)
+      return GA_ECUDA;
+    ga::AlignParams p{};
+    p.reads = s->d_seq;
+    p.read_off = s->d_read_off;
+    p.read_len = s->d_read_len;
+    p.refs = s->d_seq;
+    p.ref_off = s->d_ref_off;
+    p.ref_len = s->d_ref_len;
+    p.n_pairs = s->max_slots;
+    p.W = s->W;
+    p.O = s->O;
+    p.kmax = s->k < s->W ? s->k : s->W;
+    p.dist = s->d_dist;
+    p.status = s->d_status;
+    p.ref_consumed = s->d_ref_consumed;
+    p.cigar = s->d_cigar;
+    p.cigar_off = s->d_cigar_off;
+    p.cigar_cap = s->d_cigar_cap;
+    p.n_runs = s->d_n_runs;
+    p.n_windows = s->d_n_windows;
+    p.cells = s->d_cells;
+    ga::StepArgs a{};
+    a.active = s->d_active;
+    a.n_active = na;
+    a.counters = s->d_counters;
+    a.state = s->d_state;
+    a.done = s->d_done;
+    a.spill = s->d_spill;
+    a.table_entries = s->plan.table_entries;
+    a.max_windows = s->max_windows;
+    if (ga::launch_step(p, s->plan, a, st) != cudaSuccess) return GA_ECUDA;
+    if (cudaMemcpyAsync(s->h_counters, s->d_counters, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return GA_ECUDA;
+    const uint32_t nd = s->h_counters[1];
+    if (nd > 0) {
+      if (cudaMemcpyAsync(s->h_done, s->d_done, 4ull * nd, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+          cudaStreamSynchronize(st) != cudaSuccess)
+        return GA_ECUDA;
+      std::vector<char> gone(s->max_slots, 0);
+      for (uint32_t q = 0; q < nd; ++q) {
+        const uint32_t slot = s->h_done[q];
+        if (slot >= s->max_slots || !s->slot_owner[slot]) return GA_ECUDA;
+        gone[slot] = 1;
+        Request* r = s->slot_owner[slot];
+        if (++r->done == r->n) finished.push_back(r);
+      }
+      size_t w = 0;
+      for (size_t q = 0; q < s->active.size(); ++q)
+        if (!gone[s->active[q]]) s->active[w++] = s->active[q];
+      s->active.resize(w);
+    }
+  }
+  rc = harvest(s, finished);
+  if (n_active) *n_active = static_cast<uint32_t>(s->active.size() + s->pending.size());
+  return rc;
+}
+
+extern "C" int ga_server_poll(ga_server* s, ga_result* out, int max, int* n_out) {
+  if (!s || (!out && max > 0) || !n_out) return GA_EINVAL;
+  int n = 0;
+  while (n < max && !s->ready.empty()) {
+    Result* r = s->ready.front();
+    s->ready.pop_front();
+    out[n++] = r->pub;
+    s->handed_out[r->pub.ticket] = r;
+  }
+  *n_out = n;
+  return n > 0 || max == 0 ? GA_OK : GA_EAGAIN;
+}
+
+extern "C" int ga_server_release(ga_server* s, uint64_t ticket) {
+  if (!s) return GA_EINVAL;
+  auto it = s->handed_out.find(ticket);
+  if (it == s->handed_out.end()) return GA_EINVAL;
+  delete it->second;
+  s->handed_out.erase(it);
+  return GA_OK;
+}
+
+extern "C" int ga_server_pending(ga_server* s, uint32_t* waiting, uint32_t* active_pairs,
+                                 uint64_t* device_bytes) {
+  if (!s) return GA_EINVAL;
+  if (waiting) *waiting = static_cast<uint32_t>(s->pending.size());
+  if (active_pairs) *active_pairs = static_cast<uint32_t>(s->active.size());
+  if (device_bytes) *device_bytes = s->bytes_total;
+  return GA_OK;
+}
+
+extern "C" int ga_server_destroy(ga_server* s) {
+  if (!s) return GA_OK;
+  if (s->stream) cudaStreamSynchronize(s->stream);
+  server_free(s);
+  delete s;
+  return GA_OK;
+}

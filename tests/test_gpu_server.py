@@ -1,0 +1,103 @@
+"""GPU tests of the alignment server (continuous batching): every request's
+result is the same when it runs alone and when it shares steps with others,
+and equals the CPU oracle; requests wait for memory when the budget is tight."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2203_15561_gb300 import datagen
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2203_15561_gb300 as ga  # noqa: E402
+from paper_2203_15561_gb300.serving import Server  # noqa: E402
+
+
+def request_batches(n_requests: int, seed: int = 5):
+    reqs = datagen.make_requests(rate_per_s=2000.0, duration_s=n_requests / 1500.0, seed=seed)[:n_requests]
+    return [datagen.make_batch(4, pair_ids=list(r.pair_ids), seed=seed) for r in reqs]
+
+
+def drain(server, want: int, max_steps: int = 100000):
+    got = {}
+    for _ in range(max_steps):
+        if len(got) >= want:
+            break
+        server.step()
+        for r in server.poll():
+            got[r.tag] = r
+    return got
+
+
+def check_against_oracle(batch, res):
+    ref = oracle.align(batch)
+    np.testing.assert_array_equal(res.dist, ref.dist)
+    np.testing.assert_array_equal(res.status, ref.status)
+    np.testing.assert_array_equal(res.ref_consumed, ref.ref_consumed)
+    for p in range(batch.n_pairs):
+        np.testing.assert_array_equal(res.runs(p), ref.runs(p))
+
+
+def test_same_alone_and_in_the_mix():
+    batches = request_batches(12)
+    # In the mix: staggered submissions so requests join while others run.
+    srv = Server(2 << 30, step_windows=8)
+    got = {}
+    for t, b in enumerate(batches):
+        srv.submit(b, tag=t)
+        srv.step()
+        for r in srv.poll():
+            got[r.tag] = r
+    got.update(drain(srv, len(batches) - len(got)))
+    srv.close()
+    assert len(got) == len(batches)
+    # Alone: one request at a time in a fresh server.
+    for t, b in enumerate(batches):
+        one = Server(2 << 30, step_windows=64)
+        one.submit(b, tag=t)
+        alone = drain(one, 1)[t]
+        one.close()
+        mix = got[t]
+        np.testing.assert_array_equal(alone.dist, mix.dist)
+        np.testing.assert_array_equal(alone.cigar_off, mix.cigar_off)
+        np.testing.assert_array_equal(alone.cigar, mix.cigar)
+        check_against_oracle(b, mix)
+
+
+def test_tight_budget_admits_by_memory():
+    batches = request_batches(6, seed=9)
+    # Just above the server's fixed needs: requests must wait for memory.
+    srv = None
+    for budget in (200 << 20, 256 << 20, 400 << 20):
+        try:
+            srv = Server(budget, step_windows=16)
+            break
+        except ga.GenasmError:
+            continue
+    assert srv is not None
+    tickets = []
+    for t, b in enumerate(batches):
+        try:
+            tickets.append(srv.submit(b, tag=t))
+        except ga.GenasmError as e:  # a request larger than the whole arena
+            assert e.code == ga.GA_ENOMEM
+    got = drain(srv, len(tickets))
+    srv.close()
+    assert len(got) == len(tickets)
+    for t, r in got.items():
+        check_against_oracle(batches[t], r)
+
+
+def test_oversize_request_refused():
+    srv = Server(1 << 30)
+    big = datagen.from_pairs([("A" * 10_000_000, "C" * 10_000_000)])  # more runs than a step can return
+    with pytest.raises(ga.GenasmError) as e:
+        srv.submit(big)
+    assert e.value.code == ga.GA_ENOMEM
+    srv.close()
