@@ -45,6 +45,11 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     ap.add_argument("--workers", type=int, default=0, help="processes for input generation")
+    ap.add_argument("--serve-seconds", type=float, default=10.0,
+                    help="seconds of Poisson arrivals for the serving leg (workload 5 runs 60)")
+    ap.add_argument("--plain-serve-seconds", type=float, default=1.0,
+                    help="seconds of arrivals replayed through the plain per-request launch")
+    ap.add_argument("--no-serve", action="store_true")
     return ap.parse_args()
 
 
@@ -321,6 +326,11 @@ def run_ours(args):
     if not args.no_e2e:
         e2e = run_e2e(args, batch, db, dev, stream, ga, barrier, max_over_ranks, sum_over_ranks)
 
+    # ---- serving: workload 5 through the server, and the plain per-request launch ----
+    serving = None
+    if not args.no_serve and ws == 1:
+        serving = run_serving(args, dev)
+
     # ---- CPU oracle baseline (rank 0, N = 1 only) ----
     cpu = None
     if not args.no_cpu and rank == 0 and ws == 1:
@@ -346,7 +356,8 @@ def run_ours(args):
             "gbases_per_s": gbases,
             "plain": plain,
             "batched_vs_plain": (value / plain["pairs_per_s"]) if plain else None,
-            "p99_latency_ms": None,
+            "p99_latency_ms": serving["served"]["p99_ms"] if serving else None,
+            "serving": serving,
             "bit_exact_repeat": same,
             "roofline": roofline,
             "cpu_baseline": cpu,
@@ -358,6 +369,120 @@ def run_ours(args):
     if ws > 1:
         dist.destroy_process_group()
     return 0
+
+
+def _percentiles(lat_ms):
+    a = np.sort(np.asarray(lat_ms, dtype=np.float64))
+    if a.size == 0:
+        return {"p50_ms": None, "p99_ms": None, "max_ms": None}
+    return {"p50_ms": float(np.percentile(a, 50)), "p99_ms": float(np.percentile(a, 99)),
+            "max_ms": float(a[-1])}
+
+
+def run_serving(args, dev):
+    """Workload 5: open-loop Poisson arrivals at 2,000 requests/s, each 1-64
+    pairs of the workload-4 distribution (seed 5). The pairs come from a pool
+    of distinct pairs (request pair j is pool pair j mod P); every request is
+    copied into the server at submission, so reuse does not share work.
+    Latency = arrival -> result visible on the host."""
+    import ctypes
+    import torch
+    import paper_2203_15561_gb300 as ga
+    from paper_2203_15561_gb300 import datagen
+
+    pool_n = 8192
+    pool = datagen.make_batch(4, pair_ids=range(pool_n), seed=5,
+                              workers=args.workers or min(16, host_cores()))
+    reqs = datagen.make_requests(2000.0, max(args.serve_seconds, args.plain_serve_seconds), seed=5)
+    arrivals = np.array([r.arrival_s for r in reqs])
+    ids = [np.asarray(r.pair_ids, dtype=np.int64) % pool_n for r in reqs]
+    meta = []
+    for q in ids:
+        meta.append([np.ascontiguousarray(pool.read_off[q]), np.ascontiguousarray(pool.read_len[q]),
+                     np.ascontiguousarray(pool.ref_off[q]), np.ascontiguousarray(pool.ref_len[q])])
+    reads_p, refs_p = pool.reads.ctypes.data, pool.refs.ctypes.data
+
+    def request(i):
+        ro, rl, fo, fl = meta[i]
+        return ga.ga_request(len(ro), reads_p, ro.ctypes.data, rl.ctypes.data, refs_p,
+                             fo.ctypes.data, fl.ctypes.data, i)
+
+    # -- served (continuous batching) --
+    free, _ = torch.cuda.mem_get_info(dev)
+    budget = int(min(40 << 30, 0.6 * free))
+    srv = ga.ga_server_create(budget, W, O, K)
+    ga.ga_server_set_step_windows(srv, 48)
+    n_req = int(np.searchsorted(arrivals, args.serve_seconds))
+    lat, pairs, bases, steps = [], 0, 0, 0
+    launches0 = ga.ga_launch_count()
+    t0 = time.perf_counter()
+    nxt, done, inflight = 0, 0, 0
+    f_poll = ga._typed("ga_server_poll", ga._i, [ga._vp, ctypes.POINTER(ga.ga_result), ga._i,
+                                                 ctypes.POINTER(ga._i)])
+    buf = (ga.ga_result * 1024)()
+    nres = ga._i(0)
+    while done < n_req:
+        now = time.perf_counter() - t0
+        while nxt < n_req and arrivals[nxt] <= now:
+            ga.ga_server_submit(srv, request(nxt))
+            nxt += 1
+            inflight += 1
+        if inflight == 0:
+            time.sleep(max(0.0, arrivals[nxt] - (time.perf_counter() - t0)))
+            continue
+        ga.ga_server_step(srv)
+        steps += 1
+        while True:
+            f_poll(srv, buf, 1024, ctypes.byref(nres))
+            if nres.value == 0:
+                break
+            t = time.perf_counter() - t0
+            for q in range(nres.value):
+                r = buf[q]
+                lat.append(1e3 * (t - arrivals[r.tag]))
+                pairs += r.n_pairs
+                bases += int(meta[r.tag][1].sum())
+                ga.ga_server_release(srv, r.ticket)
+            done += nres.value
+            inflight -= nres.value
+    wall = time.perf_counter() - t0
+    server_launches = ga.ga_launch_count() - launches0
+    ga.ga_server_destroy(srv)
+    served = {"requests": n_req, "pairs": pairs, "read_bases": bases, "wall_s": wall,
+              "pairs_per_s": pairs / wall, "gbases_per_s": bases / wall / 1e9, "steps": steps,
+              "step_windows": 48, "budget_bytes": budget, "kernel_launches": server_launches,
+              **_percentiles(lat)}
+
+    # -- plain per-request launch: each request alone, in arrival order --
+    n_plain = int(np.searchsorted(arrivals, args.plain_serve_seconds))
+    lat_p, pairs_p, bases_p = [], 0, 0
+    s = torch.cuda.Stream(dev)
+    t0 = time.perf_counter()
+    for i in range(n_plain):
+        wait = arrivals[i] - (time.perf_counter() - t0)
+        if wait > 0:
+            time.sleep(wait)
+        sub = pool.subset(ids[i])
+        with torch.cuda.stream(s):
+            from paper_2203_15561_gb300.pipeline import DeviceBatch
+            dbq = DeviceBatch(sub, W=W, O=O, k=K, device=str(dev))
+            dbq.run("plain", stats=False, stream=s)
+            h = dbq.dist[:sub.n_pairs].cpu()
+            runs = dbq.cigar.cpu()
+        s.synchronize()
+        lat_p.append(1e3 * ((time.perf_counter() - t0) - arrivals[i]))
+        pairs_p += sub.n_pairs
+        bases_p += sub.read_bases
+        del h, runs, dbq
+    wall_p = time.perf_counter() - t0
+    plain = {"requests": n_plain, "pairs": pairs_p, "wall_s": wall_p,
+             "pairs_per_s": pairs_p / wall_p if wall_p > 0 else None,
+             "gbases_per_s": bases_p / wall_p / 1e9 if wall_p > 0 else None,
+             **_percentiles(lat_p)}
+    offered = sum(len(q) for q in ids[:n_req]) / args.serve_seconds
+    return {"workload": "serving-poisson-2000rps (1-64 workload-4 pairs per request, seed 5, "
+                        f"{args.serve_seconds:g} s of arrivals, pool of {pool_n} distinct pairs)",
+            "offered_pairs_per_s": offered, "served": served, "plain_per_request": plain}
 
 
 def run_e2e(args, batch, db, dev, stream, ga, barrier, max_over_ranks, sum_over_ranks):
