@@ -314,12 +314,17 @@ def run_ours(args):
                 "peak_lop3": peaks[0] / 1e12, "peak_shf": peaks[1] / 1e12,
                 "algorithmic_ops_per_launch": cells * OPS_PER_CELL, "cells_per_launch": cells,
                 "windows_per_launch": windows, "align_ms": align_ms, "pack_ms": pack_ms}
-    prof = ROOT / "profiles" / "align_batched_traffic.json"
+    # DRAM bytes per launch from the committed ncu summary, only while the
+    # kernel sources are the ones those counters were taken from.
+    prof = ROOT / "profiles" / "align_batched_workload2_counters.md"
     if prof.exists():
-        try:
-            roofline["traffic"] = json.loads(prof.read_text()).get("bytes_per_launch")
-        except (ValueError, OSError):
-            pass
+        from paper_2203_15561_gb300.ncu_summary import source_hash
+        fields = dict(l.split(":", 1) for l in prof.read_text().splitlines()
+                      if l.startswith(("source_hash:", "traffic_bytes_per_launch:")))
+        if fields.get("source_hash", "").strip() == source_hash():
+            roofline["traffic"] = int(fields["traffic_bytes_per_launch"]) * n / 10_000
+            roofline["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of a "
+                                          "2,000-pair launch, scaled by pairs")
 
     # ---- end to end through the C ABI with host buffers ----
     e2e = None
