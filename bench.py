@@ -69,7 +69,8 @@ def host_cores() -> int:
 
 def make_inputs(pairs: int, rank: int, workers: int):
     from paper_2203_15561_gb300 import datagen
-    ids = range(rank * pairs, (rank + 1) * pairs)
+    from paper_2203_15561_gb300.multigpu import shard_pair_ids
+    ids = shard_pair_ids(pairs, rank)  # weak scaling: disjoint pairs per rank
     w = workers or min(16, host_cores())
     return datagen.make_batch(WORKLOAD, pair_ids=ids, workers=w)
 
@@ -217,23 +218,9 @@ def run_ours(args):
     db = DeviceBatch(batch, W=W, O=O, k=K, device=str(dev))
     stream = torch.cuda.current_stream(dev)
 
-    def barrier():
-        if ws > 1:
-            dist.barrier()
-
-    def max_over_ranks(x: float) -> float:
-        if ws == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
-    def sum_over_ranks(x: float) -> float:
-        if ws == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        return float(t.item())
+    from paper_2203_15561_gb300.multigpu import Reducer
+    red = Reducer(dev)
+    barrier, max_over_ranks, sum_over_ranks = red.barrier, red.max, red.sum
 
     # DP cells of the run (rows 0..d_min of every window): the algorithmic work.
     db.run("batched", stats=True)
