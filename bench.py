@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--plain-serve-seconds", type=float, default=1.0,
                     help="seconds of arrivals replayed through the plain per-request launch")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--tuning", default="",
+                    help="G,pairs_per_block,table_rows: fixed tuning of the batched kernel instead of the autotuner")
     return ap.parse_args()
 
 
@@ -230,7 +232,13 @@ def run_ours(args):
     windows = int(res.n_windows.sum())
 
     # ---- batched (the headline): autotuned, alignment replayed from a CUDA graph ----
-    tuned, tune_ms = db.autotune()
+    if args.tuning:
+        g_, ppb_, rows_ = (int(v) for v in args.tuning.split(","))
+        ga.ga_tuning_set(W, O, K, ga.ga_tuning(g_, ppb_, rows_, 1))
+        tuned, tune_ms = ga.ga_tuning_get(W, O, K), None
+        db.run("batched")  # sizes the workspace for the fixed tuning
+    else:
+        tuned, tune_ms = db.autotune()
     g_align = db.graph(pack=False)
     for _ in range(args.warmup):
         db.pack()
@@ -339,8 +347,7 @@ def run_ours(args):
             "config": {"workload": "long-10kb-10000pairs (10 kb PacBio-like reads, 12% error, 5% flanks, seed 2)",
                        "W": W, "O": O, "k": K, "pairs_per_gpu": n, "read_bases_per_gpu": read_bases,
                        "kernel": "batched (persistent, LPT work queue, CUDA graph)",
-                       "autotuned": {"lanes_per_pair": tuned.lanes_per_pair,
-                                     "rows_per_lane": tuned.rows_per_lane,
+                       ("tuning" if args.tuning else "autotuned"): {"lanes_per_pair": tuned.lanes_per_pair,
                                      "pairs_per_block": tuned.pairs_per_block,
                                      "table_rows": tuned.table_rows, "tune_ms": tune_ms},
                        "l2": "no flush: each step streams 210 MB of ASCII input (> 126 MB L2) and "

@@ -105,21 +105,22 @@ int ga_workspace_size(uint32_t n_pairs, int W, int O, int k, size_t* bytes_out);
  * Tuning of the batched kernel. ga_align_batch uses the library's defaults
  * (or what ga_autotune stored for this device); ga_align_batch_tuned takes an
  * explicit choice. All fields 0 = default.
- *   lanes_per_pair : lanes that run one pair's DC wavefront: 4, 8, 16 or 32.
- *   rows_per_lane  : error rows each lane updates per wavefront step; the
- *                    supported (lanes_per_pair, rows_per_lane) pairs are
- *                    (4,5) (8,3) (8,5) (16,3) (32,1) (32,2).
+ *   lanes_per_pair : lanes that run one pair's DC wavefront: 4, 8, 16 or 32
+ *                    (each lane owns 64 / lanes_per_pair text columns).
  *   pairs_per_block: pairs resident per thread block.
  *   table_rows     : error rows of a window's table kept in shared memory
  *                    (for windows that are not the last); a window whose
  *                    solution row does not fit is recomputed into the
- *                    workspace.
+ *                    workspace. With O >= 16 such windows keep 32-bit
+ *                    entries (the 32 bits of each cell around the
+ *                    traceback's diagonal; a window whose traceback leaves
+ *                    that band is redone with 64-bit entries in the
+ *                    workspace), otherwise 64-bit entries.
  *   lpt            : 1 = hand out pairs longest read first, -1 = in index
  *                    order (0 = default, longest first).
  */
 typedef struct ga_tuning_s {
   int lanes_per_pair;
-  int rows_per_lane;
   int pairs_per_block;
   int table_rows;
   int lpt;
@@ -139,7 +140,7 @@ int ga_tuning_set(int W, int O, int k, const ga_tuning* tuning);
  * ga_autotune - the autotuner of the batched kernel. Runs the current
  * default once on the caller's sample (with statistics, to estimate the
  * typical d_min), then times a candidate set of (lanes_per_pair,
- * rows_per_lane, pairs_per_block, table_rows) with CUDA events, one warm-up
+ * pairs_per_block, table_rows) with CUDA events, one warm-up
  * and one timed run each, and stores the fastest as the default for this
  * device and (W, O, k). Arguments as ga_align_batch (outputs are
  * overwritten; d_n_windows and d_cells are required); the workspace must hold

@@ -51,7 +51,7 @@ class GenasmError(RuntimeError):
 
 
 class ga_tuning(ctypes.Structure):
-    _fields_ = [("lanes_per_pair", ctypes.c_int), ("rows_per_lane", ctypes.c_int),
+    _fields_ = [("lanes_per_pair", ctypes.c_int),
                 ("pairs_per_block", ctypes.c_int), ("table_rows", ctypes.c_int),
                 ("lpt", ctypes.c_int)]
 

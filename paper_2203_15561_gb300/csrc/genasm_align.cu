@@ -60,51 +60,108 @@ __device__ __forceinline__ void begin_pair(const AlignParams& p, uint32_t pair, 
 
 // One window for every busy group of the warp (the window chain of a pair is
 // serial: each window starts where the previous traceback stopped).
-template <int G, int K>
+//
+// Table formats: a window that is not the last uses a band table in shared
+// memory when the launch enables it (p.band_top >= 0); last windows, and
+// launches without the band, use wide tables. The shared-memory table area
+// holds `tab_entries` 64-bit words of either format. Two rare cases recompute
+// the window with a wide table in the group's global spill area: rows
+// 0..d_min do not fit the shared area, or the traceback's diagonal offset
+// leaves the band (the CIGAR writer is then rolled back to the window start).
+// Callers without a spill area (spill == nullptr) size the shared table for
+// all 65 wide rows and run without the band.
+template <int G>
 __device__ __forceinline__ void step_window(const AlignParams& p, int r, int gbase, PairState& st,
                                             GroupSmem* gs, uint64_t* tab_smem, int tab_entries,
                                             uint64_t* spill) {
   const bool writer = r == 0;
   const bool ga = st.busy;
   const int commit = p.W - p.O;
-  int wp = 1, wt = 0, ncols = 1, S = 2, smem_rows = kMaxRows;
+  const bool can_spill = spill != nullptr;
+  int wp = 1, wt = 0, ncols = 1;
   bool last = true;
   if (ga) {
     wp = static_cast<int>(min(static_cast<uint32_t>(p.W), st.m - st.pos_p));
     wt = static_cast<int>(min(static_cast<uint32_t>(p.W), st.n - st.pos_t));
     last = st.pos_p + static_cast<uint32_t>(wp) == st.m;
     ncols = last ? wt + 1 : min(wt, commit) + 1;
-    S = table_stride(ncols);
-    smem_rows = min(tab_entries / S, kMaxRows);
   }
+  const bool band = ga && !last && p.band_top >= 0 && can_spill;
+  const bool wide = ga && !band;
+  const int Sw = table_stride(ncols);
+  const int Sb = band_stride<G>(ncols);
+  const int smem_rows = min(band ? 2 * tab_entries / Sb : tab_entries / Sw, kMaxRows);
   build_masks<G>(r, gbase, ga, st.read, st.pos_p, wp, st.ref, st.pos_t, wt, gs->pmcol);
   __syncwarp();
-  int dmin = dc_window<G, K>(r, gbase, ga, wp, wt, p.kmax, ncols, S, smem_rows, gs->pmcol,
-                             gs->bridge, tab_smem);
-  // Rare: the table of rows 0..d_min does not fit the group's shared memory.
-  // Such a group recomputes the window into its global spill area (callers
-  // without one size the table for all 65 rows).
+  int dmin = -1;
+  if (__any_sync(kFull, band))
+    dmin = dc_window<G, kFmtBand, true>(r, gbase, band, wp, wt, p.kmax, ncols, Sb, smem_rows,
+                                        p.band_top, gs->pmcol, tab_smem);
+  if (__any_sync(kFull, wide)) {
+    const int d2 = dc_window<G, kFmtWide, true>(r, gbase, wide, wp, wt, p.kmax, ncols, Sw,
+                                                smem_rows, 0, gs->pmcol, tab_smem);
+    if (wide) dmin = d2;
+  }
+  // Rows 0..d_min do not fit the shared table.
   const bool spilled = ga && dmin >= smem_rows;
-  const bool can_spill = spill != nullptr;
   if (__any_sync(kFull, spilled && can_spill)) {
     __syncwarp();
-    const int d2 = dc_window<G, K>(r, gbase, spilled && can_spill, wp, wt, p.kmax, ncols, S,
-                                   kMaxRows, gs->pmcol, gs->bridge, spill);
-    if (spilled && can_spill) dmin = d2;
+    const int d3 = dc_window<G, kFmtWide, false>(r, gbase, spilled && can_spill, wp, wt, p.kmax,
+                                                 ncols, Sw, kMaxRows, 0, gs->pmcol, spill);
+    if (spilled && can_spill) dmin = d3;
   }
   __syncwarp();
   const bool exceeds = ga && dmin < 0;
   const bool trace = ga && !exceeds && !(spilled && !can_spill);
-  int cp = 0, ct = 0, cp2 = 0, ct2 = 0;
-  bool ok = tb_window<G>(r, gbase, trace && !spilled, wp, wt, dmin, last, commit, ncols, S,
-                         gs->pmcol, tab_smem, st.rw, writer, cp, ct, st.edits);
-  if (__any_sync(kFull, trace && spilled)) {
-    const bool ok2 = tb_window<G>(r, gbase, trace && spilled, wp, wt, dmin, last, commit, ncols, S,
-                                  gs->pmcol, spill, st.rw, writer, cp2, ct2, st.edits);
-    if (spilled) {
+  const RunWriter rw0 = st.rw;
+  const uint32_t edits0 = st.edits;
+  int cp = 0, ct = 0;
+  bool ok = true, over = false, unused = false;
+  if (__any_sync(kFull, trace && band && !spilled)) {
+    int c1 = 0, t1 = 0;
+    const bool ok1 = tb_window<G, kFmtBand>(r, gbase, trace && band && !spilled, wp, wt, dmin, last,
+                                            commit, ncols, Sb, p.band_top, gs->pmcol, tab_smem,
+                                            st.rw, writer, c1, t1, st.edits, over);
+    if (band) {
+      ok = ok1;
+      cp = c1;
+      ct = t1;
+    }
+  }
+  // The offset left the band: redo the window with a wide table in the
+  // spill area (band windows always have one).
+  const bool redo = over;
+  if (__any_sync(kFull, redo)) {
+    if (redo) {
+      st.rw = rw0;
+      st.edits = edits0;
+    }
+    __syncwarp();
+    dc_window<G, kFmtWide, false>(r, gbase, redo, wp, wt, p.kmax, ncols, Sw, kMaxRows, 0,
+                                  gs->pmcol, spill);
+    __syncwarp();
+  }
+  if (__any_sync(kFull, trace && wide && !spilled)) {
+    int c2 = 0, t2 = 0;
+    const bool ok2 = tb_window<G, kFmtWide>(r, gbase, trace && wide && !spilled, wp, wt, dmin, last,
+                                            commit, ncols, Sw, 0, gs->pmcol, tab_smem, st.rw,
+                                            writer, c2, t2, st.edits, unused);
+    if (wide && !spilled) {
       ok = ok2;
-      cp = cp2;
-      ct = ct2;
+      cp = c2;
+      ct = t2;
+    }
+  }
+  const bool global_tb = trace && (spilled || redo);
+  if (__any_sync(kFull, global_tb)) {
+    int c3 = 0, t3 = 0;
+    const bool ok3 = tb_window<G, kFmtWide>(r, gbase, global_tb, wp, wt, dmin, last, commit, ncols,
+                                            Sw, 0, gs->pmcol, spill, st.rw, writer, c3, t3,
+                                            st.edits, unused);
+    if (global_tb) {
+      ok = ok3;
+      cp = c3;
+      ct = t3;
     }
   }
   __syncwarp();
@@ -127,8 +184,8 @@ __device__ __forceinline__ void step_window(const AlignParams& p, int r, int gba
 
 // ---------------------------------------------------------------------------
 // Plain GPU GenASM: one pair per 32-thread block (each lane a strip of 2
-// error rows, so one 64-row pass covers any window), the worst-case table
-// (65 rows x 66 entries) in shared memory, pairs in index order.
+// text columns), the worst-case table (65 rows x 66 entries) in shared
+// memory, pairs in index order.
 // ---------------------------------------------------------------------------
 
 constexpr int kPlainTableEntries = kMaxRows * kMaxStride;
@@ -141,19 +198,21 @@ __global__ void __launch_bounds__(32) align_plain_kernel(const AlignParams p) {
   const int r = threadIdx.x;
   PairState st;
   begin_pair(p, blockIdx.x, st, r == 0);
-  while (st.busy) step_window<32, 2>(p, r, 0, st, gs, table, kPlainTableEntries, nullptr);
+  while (st.busy) step_window<32>(p, r, 0, st, gs, table, kPlainTableEntries, nullptr);
 }
 
 cudaError_t launch_plain(const AlignParams& p, cudaStream_t s) {
   if (p.n_pairs == 0) return cudaSuccess;
-  align_plain_kernel<<<p.n_pairs, 32, kPlainSmem, s>>>(p);
+  AlignParams q = p;
+  q.band_top = -1;  // wide tables only (no spill area)
+  align_plain_kernel<<<p.n_pairs, 32, kPlainSmem, s>>>(q);
   count_launches(1);
   return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
 // Batched: persistent blocks of `pairs_per_block` groups of G lanes (each
-// lane a strip of K error rows). Each group pulls pairs from a device
+// lane a strip of 64/G text columns). Each group pulls pairs from a device
 // counter; with LPT the counter indexes a longest-read-first permutation
 // built by a counting sort.
 // ---------------------------------------------------------------------------
@@ -167,7 +226,7 @@ struct BatchArgs {
 
 constexpr int kSpillEntries = kMaxRows * kMaxStride;
 
-template <int G, int K>
+template <int G>
 __global__ void __launch_bounds__(256, 1) align_batched_kernel(const AlignParams p, const BatchArgs a) {
   extern __shared__ __align__(16) uint64_t smem[];
   const int lane = threadIdx.x & 31;
@@ -194,7 +253,7 @@ __global__ void __launch_bounds__(256, 1) align_batched_kernel(const AlignParams
       else drained = true;
     }
     if (!__any_sync(kFull, st.busy || !drained)) break;
-    if (__any_sync(kFull, st.busy)) step_window<G, K>(p, r, gbase, st, gs, table, a.table_entries, spill);
+    if (__any_sync(kFull, st.busy)) step_window<G>(p, r, gbase, st, gs, table, a.table_entries, spill);
   }
 }
 
@@ -241,24 +300,24 @@ __global__ void lpt_scatter_kernel(const uint32_t* __restrict__ read_len, uint32
   }
 }
 
-// The compiled (G, K) variants of the batched kernel.
-#define GA_BATCH_VARIANTS(X) X(4, 5) X(8, 3) X(8, 5) X(16, 3) X(32, 1) X(32, 2)
+// The compiled variants of the batched kernel (lanes per pair G).
+#define GA_BATCH_VARIANTS(X) X(4) X(8) X(16) X(32)
 
-bool batch_variant_exists(int G, int K) {
-#define GA_EXISTS(g, k) if (G == g && K == k) return true;
+bool batch_variant_exists(int G) {
+#define GA_EXISTS(g) if (G == g) return true;
   GA_BATCH_VARIANTS(GA_EXISTS)
 #undef GA_EXISTS
   return false;
 }
 
-static cudaError_t variant_setup(int G, int K, int threads, size_t smem, int* per_sm) {
-#define GA_SETUP(g, k)                                                                          \
-  if (G == g && K == k) {                                                                       \
-    cudaError_t e = cudaFuncSetAttribute(align_batched_kernel<g, k>,                            \
+static cudaError_t variant_setup(int G, int threads, size_t smem, int* per_sm) {
+#define GA_SETUP(g)                                                                             \
+  if (G == g) {                                                                                 \
+    cudaError_t e = cudaFuncSetAttribute(align_batched_kernel<g>,                               \
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,           \
                                          static_cast<int>(smem));                               \
     if (e != cudaSuccess) return e;                                                             \
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, align_batched_kernel<g, k>,    \
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, align_batched_kernel<g>,       \
                                                          threads, smem);                        \
   }
   GA_BATCH_VARIANTS(GA_SETUP)
@@ -266,41 +325,55 @@ static cudaError_t variant_setup(int G, int K, int threads, size_t smem, int* pe
   return cudaErrorInvalidValue;
 }
 
-static void variant_launch(int G, int K, int blocks, int threads, size_t smem, cudaStream_t s,
+static void variant_launch(int G, int blocks, int threads, size_t smem, cudaStream_t s,
                            const AlignParams& p, const BatchArgs& a) {
-#define GA_LAUNCH(g, k) \
-  if (G == g && K == k) align_batched_kernel<g, k><<<blocks, threads, smem, s>>>(p, a);
+#define GA_LAUNCH(g) \
+  if (G == g) align_batched_kernel<g><<<blocks, threads, smem, s>>>(p, a);
   GA_BATCH_VARIANTS(GA_LAUNCH)
 #undef GA_LAUNCH
 }
 
-cudaError_t default_tuning(int W, int O, int k, int* G, int* K, int* ppb, int* table_entries,
-                           int* lpt) {
+int band_top_for(int O) { return O >= 16 ? std::min(22, O - 1) : -1; }
+
+int table_entries_for(int G, int W, int O, int rows, bool band) {
+  const int ncols = W - O + 1;
+  if (!band) return rows * table_stride(ncols);
+  const int C = 64 / G;
+  const int Sb = (ncols + C - 1) / C * C;
+  return (rows * Sb + 1) / 2;
+}
+
+int table_rows_for(int G, int W, int O, int entries, bool band) {
+  const int ncols = W - O + 1;
+  if (!band) return entries / table_stride(ncols);
+  const int C = 64 / G;
+  const int Sb = (ncols + C - 1) / C * C;
+  return 2 * entries / Sb;
+}
+
+cudaError_t default_tuning(int W, int O, int k, int* G, int* ppb, int* table_entries, int* lpt) {
+  const bool band = band_top_for(O) >= 0;
   ga_tuning t;
   if (stored_tuning(W, O, k, &t)) {  // chosen by ga_autotune or set by ga_tuning_set
     *G = t.lanes_per_pair;
-    *K = t.rows_per_lane;
     *ppb = t.pairs_per_block;
-    *table_entries = t.table_rows * table_stride(W - O + 1);
+    *table_entries = table_entries_for(*G, W, O, t.table_rows, band);
     *lpt = t.lpt >= 0 ? 1 : 0;
     return cudaSuccess;
   }
-  *G = 16;
-  *K = 3;
-  *ppb = 2;
-  // Rows 0..37 of a window that is not the last (W-O+1 stored columns).
-  *table_entries = 38 * table_stride(W - O + 1);
+  *G = 8;
+  *ppb = 4;
+  // Rows 0..41 of a window that is not the last (W-O+1 stored columns).
+  *table_entries = table_entries_for(*G, W, O, 42, band);
   *lpt = 1;
-  (void)W;
   return cudaSuccess;
 }
 
-cudaError_t resolve_plan(int W, int O, int k, int G, int K, int ppb, int table_entries, int lpt,
-                         BatchPlan* plan) {
+cudaError_t resolve_plan(int W, int O, int k, int G, int ppb, int table_entries, int lpt,
+                         bool band, BatchPlan* plan) {
   (void)W;
-  (void)O;
   (void)k;
-  if (!batch_variant_exists(G, K)) return cudaErrorInvalidValue;
+  if (!batch_variant_exists(G)) return cudaErrorInvalidValue;
   if (ppb < 1 || ppb * G > 256 || (ppb * G) % 32 != 0) return cudaErrorInvalidValue;  // whole warps
   table_entries = std::max(kMaxStride, std::min(table_entries, kMaxRows * kMaxStride));
   table_entries &= ~1;  // keep every group's area 16-byte aligned
@@ -316,13 +389,13 @@ cudaError_t resolve_plan(int W, int O, int k, int G, int K, int ppb, int table_e
   if (smem > static_cast<size_t>(smem_optin)) return cudaErrorInvalidValue;
   const int threads = ppb * G;
   int per_sm = 0;
-  if ((e = variant_setup(G, K, threads, smem, &per_sm)) != cudaSuccess) return e;
+  if ((e = variant_setup(G, threads, smem, &per_sm)) != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   plan->lanes_per_pair = G;
-  plan->rows_per_lane = K;
   plan->pairs_per_block = ppb;
   plan->table_entries = table_entries;
   plan->lpt = lpt ? 1 : 0;
+  plan->band_top = band ? band_top_for(O) : -1;
   plan->blocks = per_sm * sms;
   plan->smem_bytes = smem;
   return cudaSuccess;
@@ -359,8 +432,9 @@ cudaError_t launch_batched(const AlignParams& p, const BatchPlan& plan, void* ws
   BatchArgs a{queue, plan.lpt ? order : nullptr, reinterpret_cast<uint64_t*>(w + L.spill),
               plan.table_entries};
   const int threads = plan.pairs_per_block * plan.lanes_per_pair;
-  variant_launch(plan.lanes_per_pair, plan.rows_per_lane, plan.blocks, threads, plan.smem_bytes, s,
-                 p, a);
+  AlignParams q = p;
+  q.band_top = plan.band_top;
+  variant_launch(plan.lanes_per_pair, plan.blocks, threads, plan.smem_bytes, s, q, a);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -401,7 +475,7 @@ __device__ __forceinline__ void save_pair(const PairState& st, SlotState& s) {
   s.run_len = st.rw.len;
 }
 
-template <int G, int K>
+template <int G>
 __global__ void __launch_bounds__(256, 1) align_step_kernel(const AlignParams p, const StepArgs a) {
   extern __shared__ __align__(16) uint64_t smem[];
   const int lane = threadIdx.x & 31;
@@ -436,7 +510,7 @@ __global__ void __launch_bounds__(256, 1) align_step_kernel(const AlignParams p,
     }
     if (!__any_sync(kFull, st.busy || !drained || finished)) break;
     const bool was_busy = st.busy;
-    if (__any_sync(kFull, st.busy)) step_window<G, K>(p, r, gbase, st, gs, table, a.table_entries, spill);
+    if (__any_sync(kFull, st.busy)) step_window<G>(p, r, gbase, st, gs, table, a.table_entries, spill);
     if (was_busy) {
       if (!st.busy) {
         finished = true;
@@ -449,20 +523,21 @@ __global__ void __launch_bounds__(256, 1) align_step_kernel(const AlignParams p,
   }
 }
 
-#define GA_STEP_VARIANTS(X) X(8, 5) X(16, 3) X(32, 2)
+#define GA_STEP_VARIANTS(X) X(8) X(16) X(32)
 
 cudaError_t launch_step(const AlignParams& p, const BatchPlan& plan, const StepArgs& a,
                         cudaStream_t s) {
   if (a.n_active == 0) return cudaSuccess;
   const int threads = plan.pairs_per_block * plan.lanes_per_pair;
+  AlignParams q = p;
+  q.band_top = plan.band_top;
   cudaError_t e = cudaErrorInvalidValue;
-#define GA_STEP_LAUNCH(g, k)                                                                      \
-  if (plan.lanes_per_pair == g && plan.rows_per_lane == k) {                                      \
-    e = cudaFuncSetAttribute(align_step_kernel<g, k>,                                             \
-                             cudaFuncAttributeMaxDynamicSharedMemorySize,                         \
+#define GA_STEP_LAUNCH(g)                                                                         \
+  if (plan.lanes_per_pair == g) {                                                                 \
+    e = cudaFuncSetAttribute(align_step_kernel<g>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
                              static_cast<int>(plan.smem_bytes));                                  \
     if (e != cudaSuccess) return e;                                                               \
-    align_step_kernel<g, k><<<plan.blocks, threads, plan.smem_bytes, s>>>(p, a);                  \
+    align_step_kernel<g><<<plan.blocks, threads, plan.smem_bytes, s>>>(q, a);                     \
     e = cudaGetLastError();                                                                       \
   }
   GA_STEP_VARIANTS(GA_STEP_LAUNCH)
@@ -471,8 +546,8 @@ cudaError_t launch_step(const AlignParams& p, const BatchPlan& plan, const StepA
   return e;
 }
 
-bool step_variant_exists(int G, int K) {
-#define GA_STEP_EXISTS(g, k) if (G == g && K == k) return true;
+bool step_variant_exists(int G) {
+#define GA_STEP_EXISTS(g) if (G == g) return true;
   GA_STEP_VARIANTS(GA_STEP_EXISTS)
 #undef GA_STEP_EXISTS
   return false;

@@ -53,20 +53,19 @@ int fill_params(const uint8_t* d_reads, const uint64_t* d_read_off, const uint32
 }
 
 int resolve(int W, int O, int k, const ga_tuning* t, ga::BatchPlan* plan) {
-  int G = 0, K = 0, ppb = 0, entries = 0, lpt = 1;
-  cudaError_t e = ga::default_tuning(W, O, k, &G, &K, &ppb, &entries, &lpt);
+  int G = 0, ppb = 0, entries = 0, lpt = 1;
+  cudaError_t e = ga::default_tuning(W, O, k, &G, &ppb, &entries, &lpt);
   if (e != cudaSuccess) return cuda_fail(e);
   if (t) {
     if (t->lanes_per_pair) G = t->lanes_per_pair;
-    if (t->rows_per_lane) K = t->rows_per_lane;
     if (t->pairs_per_block) ppb = t->pairs_per_block;
-    if (t->table_rows) entries = t->table_rows * ga::table_stride(W - O + 1);
+    if (t->table_rows) entries = ga::table_entries_for(G, W, O, t->table_rows, ga::band_top_for(O) >= 0);
     if (t->lpt) lpt = t->lpt > 0 ? 1 : 0;
-    if (!ga::batch_variant_exists(G, K) || ppb < 1 || ppb * G > 256 || (ppb * G) % 32 != 0 ||
+    if (!ga::batch_variant_exists(G) || ppb < 1 || ppb * G > 256 || (ppb * G) % 32 != 0 ||
         t->table_rows < 0)
       return GA_EINVAL;
   }
-  e = ga::resolve_plan(W, O, k, G, K, ppb, entries, lpt, plan);
+  e = ga::resolve_plan(W, O, k, G, ppb, entries, lpt, true, plan);
   if (e == cudaErrorInvalidValue || e == cudaErrorInvalidConfiguration) {
     cudaGetLastError();
     return GA_EINVAL;

@@ -18,6 +18,7 @@ struct AlignParams {
   const uint32_t* ref_len;
   uint32_t n_pairs;
   int W, O, kmax;  // kmax = min(k, W): no window needs rows above W
+  int band_top;    // band tables for windows that are not the last (-1: wide only); set by the launchers
   int32_t* dist;
   int32_t* status;
   int32_t* ref_consumed;
@@ -31,11 +32,11 @@ struct AlignParams {
 
 // Resolved tuning of the batched kernel.
 struct BatchPlan {
-  int lanes_per_pair;   // G
-  int rows_per_lane;    // K
+  int lanes_per_pair;   // G (each lane owns 64 / G text columns)
   int pairs_per_block;  // groups per block
   int table_entries;    // 64-bit table entries per group kept in shared memory
   int lpt;              // longest-first hand-out
+  int band_top;         // band table offset A, or -1 (wide tables only)
   int blocks;           // persistent grid size
   size_t smem_bytes;    // dynamic shared memory per block
 };
@@ -71,7 +72,7 @@ struct StepArgs {
 
 cudaError_t launch_step(const AlignParams& p, const BatchPlan& plan, const StepArgs& a,
                         cudaStream_t s);
-bool step_variant_exists(int G, int K);
+bool step_variant_exists(int G);
 
 WorkspaceLayout workspace_layout(uint32_t n_pairs, const BatchPlan& plan);
 
@@ -98,10 +99,16 @@ cudaError_t launch_batched(const AlignParams& p, const BatchPlan& plan, void* ws
 
 // Default tuning for (W, O, k) on the current device; fills G / pairs per
 // block / table entries / lpt. Returns cudaSuccess or the device query error.
-cudaError_t default_tuning(int W, int O, int k, int* G, int* K, int* ppb, int* table_entries,
-                           int* lpt);
-bool batch_variant_exists(int G, int K);
-cudaError_t resolve_plan(int W, int O, int k, int G, int K, int ppb, int table_entries, int lpt,
-                         BatchPlan* plan);
+cudaError_t default_tuning(int W, int O, int k, int* G, int* ppb, int* table_entries, int* lpt);
+bool batch_variant_exists(int G);
+cudaError_t resolve_plan(int W, int O, int k, int G, int ppb, int table_entries, int lpt,
+                         bool band, BatchPlan* plan);
+
+// Band tables (32-bit entries around the diagonal) are used for windows that
+// are not the last when O >= 16, with offset A = min(22, O - 1). Table sizes
+// in 64-bit words for `rows` rows of a window that is not the last, and back.
+int band_top_for(int O);
+int table_entries_for(int G, int W, int O, int rows, bool band);
+int table_rows_for(int G, int W, int O, int entries, bool band);
 
 }  // namespace ga

@@ -91,10 +91,12 @@ extern "C" int ga_align_batch_noalloc(const uint8_t* d_reads, const uint64_t* d_
   p.n_windows = d_n_windows;
   p.cells = d_cells;
 
-  // 16 lanes per pair, 3 rows per lane, 2 pairs per block, and a table of
-  // 65 rows x 66 entries per pair: every window fits in shared memory.
+  // 16 lanes per pair, 2 pairs per block, and a wide table of 65 rows x 66
+  // entries per pair: every window fits in shared memory, so the kernel
+  // never needs a spill area (and runs without band tables, whose overflow
+  // would need one).
   ga::BatchPlan plan{};
-  cudaError_t e = ga::resolve_plan(W, O, k, 16, 3, 2, ga::kMaxRows * ga::kMaxStride, 1, &plan);
+  cudaError_t e = ga::resolve_plan(W, O, k, 16, 2, ga::kMaxRows * ga::kMaxStride, 1, false, &plan);
   if (e != cudaSuccess) return GA_ECUDA;
   const ga::WorkspaceLayout L = ga::workspace_layout(n_pairs, plan);
   if (L.order != kOrderOffset || L.order + 4ull * n_pairs > kScratchBytes) return GA_ENOSPC;

@@ -226,15 +226,16 @@ extern "C" int ga_server_create(size_t budget_bytes, int W, int O, int k, ga_ser
   cudaError_t e = cudaGetDevice(&s->device);
   // Step kernel tuning: the stored/default tuning when it has a step variant.
   ga_tuning t{};
-  int G = 8, K = 5, ppb = 8, rows = 38;
-  if (ga_tuning_get(W, O, k, &t) == GA_OK && ga::step_variant_exists(t.lanes_per_pair, t.rows_per_lane)) {
+  int G = 8, ppb = 4, rows = 42;
+  if (ga_tuning_get(W, O, k, &t) == GA_OK && ga::step_variant_exists(t.lanes_per_pair)) {
     G = t.lanes_per_pair;
-    K = t.rows_per_lane;
     ppb = t.pairs_per_block;
     rows = t.table_rows;
   }
   if (e == cudaSuccess)
-    e = ga::resolve_plan(W, O, k, G, K, ppb, rows * ga::table_stride(W - O + 1), 1, &s->plan);
+    e = ga::resolve_plan(W, O, k, G, ppb,
+                         ga::table_entries_for(G, W, O, rows, ga::band_top_for(O) >= 0), 1, true,
+                         &s->plan);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
   // Fixed parts first, then the arenas from what is left of the budget.
   const uint64_t groups = static_cast<uint64_t>(s->plan.blocks) * s->plan.pairs_per_block;

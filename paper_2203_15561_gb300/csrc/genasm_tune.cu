@@ -1,8 +1,7 @@
 // Autotuner and CUDA-graph capture of the batched alignment step.
 //
 // Autotuner: the batched kernel's speed depends on how many lanes work on a
-// pair (G), how many error rows each lane owns (K), how many pairs share a
-// block and how many table rows a window keeps in shared memory (which sets
+// pair (G; each lane owns 64/G text columns), how many pairs share a block and how many table rows a window keeps in shared memory (which sets
 // how many pairs fit on an SM). The best choice depends on the workload's
 // typical d_min. ga_autotune measures a d_min estimate on the caller's sample,
 // times a candidate set on it with CUDA events, and stores the fastest as the
@@ -71,10 +70,9 @@ std::vector<ga_tuning> candidates(int rows) {
   const int lo = std::min(65, std::max(4, rows + 4));
   const int hi = std::min(65, std::max(6, rows + 8));
   std::vector<ga_tuning> c;
-  const int shapes[][3] = {{8, 5, 8}, {8, 5, 4}, {16, 3, 2}, {16, 3, 4}, {32, 2, 1}, {8, 3, 4},
-                           {4, 5, 8}};
+  const int shapes[][2] = {{4, 8}, {4, 16}, {8, 4}, {8, 8}, {16, 2}, {16, 4}, {32, 1}, {32, 2}};
   for (const auto& s : shapes)
-    for (int r : {lo, hi}) c.push_back(ga_tuning{s[0], s[1], s[2], r, 1});
+    for (int r : {lo, hi}) c.push_back(ga_tuning{s[0], s[1], r, 1});
   return c;
 }
 
@@ -83,9 +81,10 @@ std::vector<ga_tuning> candidates(int rows) {
 extern "C" int ga_tuning_get(int W, int O, int k, ga_tuning* out) {
   if (!out || bad_wok(W, O, k)) return GA_EINVAL;
   if (ga::stored_tuning(W, O, k, out)) return GA_OK;
-  int G, K, ppb, entries, lpt;
-  if (ga::default_tuning(W, O, k, &G, &K, &ppb, &entries, &lpt) != cudaSuccess) return GA_ECUDA;
-  *out = ga_tuning{G, K, ppb, entries / ga::table_stride(W - O + 1), lpt ? 1 : -1};
+  int G, ppb, entries, lpt;
+  if (ga::default_tuning(W, O, k, &G, &ppb, &entries, &lpt) != cudaSuccess) return GA_ECUDA;
+  *out = ga_tuning{G, ppb, ga::table_rows_for(G, W, O, entries, ga::band_top_for(O) >= 0),
+                   lpt ? 1 : -1};
   return GA_OK;
 }
 

@@ -10,10 +10,10 @@
 // window T of wt <= 64 bases) a group
 //   1. builds the pattern masks PM[c] (bit j clear iff P[wp-1-j] == c) with
 //      warp ballots, and the per-column mask PM[T[i]] in shared memory;
-//   2. runs the distance calculation (DC) as a wavefront over error rows:
-//      lane r owns a strip of K consecutive rows; row q lags row q-1 by one
-//      text column, so each lane updates K independent cells per step and
-//      receives the row above its strip from lane r-1 with one shuffle;
+//   2. runs the distance calculation (DC) as a wavefront over text columns:
+//      lane c owns 64/G consecutive columns and computes one error row per
+//      step, one row behind lane c+1, whose leftmost cell it receives with
+//      one shuffle;
 //   3. stops at the first row d whose R_0[d] holds the whole pattern
 //      (improvement (2) of Sec. I: no row above d_min is ever needed);
 //   4. stores only R_i[d], the AND of the match/substitution/insertion/deletion
@@ -50,9 +50,9 @@ constexpr uint32_t kFull = 0xffffffffu;
 enum : uint32_t { kOpIns = 1, kOpDel = 2, kOpMatch = 7, kOpSubst = 8, kOpStuck = 15 };
 enum : int32_t { kPairOk = 0, kPairExceedsK = 1, kPairCigarFull = 2, kPairTbStuck = 3 };
 
-// Table row stride for `ncols` stored columns: the smallest even value.
-// With an odd number of rows per lane strip (K) and an even stride, the
-// 64-bit stores of one wavefront step hit distinct bank pairs.
+// Table row stride for `ncols` stored columns: the smallest even value, so
+// that every row starts on a 16-byte boundary and a lane can store two
+// neighbouring columns with one 16-byte store.
 __host__ __device__ __forceinline__ int table_stride(int ncols) { return (ncols + 1) & ~1; }
 
 __device__ __forceinline__ uint64_t init_row(int d, int wp) {
@@ -74,14 +74,60 @@ __device__ __forceinline__ uint64_t shl1(uint64_t x, uint32_t low) {
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
-__device__ __forceinline__ uint64_t lds64(uint32_t a) {
-  uint64_t v;
-  asm volatile("ld.shared.u64 %0, [%1];" : "=l"(v) : "r"(a));
-  return v;
+
+// Predicated table stores: every lane issues the instruction and the
+// predicate masks it, so lanes that store different widths (or nothing) do
+// not diverge. Shared-memory forms take a 32-bit shared address, global ones
+// a generic pointer into global memory.
+__device__ __forceinline__ void st2_if(bool p, uint32_t a, uint64_t x, uint64_t y) {
+  asm volatile(
+      "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %3, 0;\n\t@q st.shared.v2.u64 [%0], {%1, %2};\n\t}"
+      ::"r"(a), "l"(x), "l"(y), "r"(static_cast<uint32_t>(p)) : "memory");
 }
-__device__ __forceinline__ void sts64(uint32_t a, uint64_t v) {
-  asm volatile("st.shared.u64 [%0], %1;" ::"r"(a), "l"(v) : "memory");
+__device__ __forceinline__ void st1_if(bool p, uint32_t a, uint64_t x) {
+  asm volatile(
+      "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q st.shared.u64 [%0], %1;\n\t}"
+      ::"r"(a), "l"(x), "r"(static_cast<uint32_t>(p)) : "memory");
 }
+__device__ __forceinline__ void st2_if(bool p, uint64_t* a, uint64_t x, uint64_t y) {
+  asm volatile(
+      "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %3, 0;\n\t@q st.global.v2.u64 [%0], {%1, %2};\n\t}"
+      ::"l"(a), "l"(x), "l"(y), "r"(static_cast<uint32_t>(p)) : "memory");
+}
+__device__ __forceinline__ void st1_if(bool p, uint64_t* a, uint64_t x) {
+  asm volatile(
+      "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q st.global.u64 [%0], %1;\n\t}"
+      ::"l"(a), "l"(x), "r"(static_cast<uint32_t>(p)) : "memory");
+}
+
+__device__ __forceinline__ void st32x4_if(bool p, uint32_t a, uint32_t x, uint32_t y, uint32_t z,
+                                          uint32_t w) {
+  asm volatile(
+      "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %5, 0;\n\t@q st.shared.v4.u32 [%0], {%1, %2, %3, %4};\n\t}"
+      ::"r"(a), "r"(x), "r"(y), "r"(z), "r"(w), "r"(static_cast<uint32_t>(p)) : "memory");
+}
+__device__ __forceinline__ void st32x2_if(bool p, uint32_t a, uint32_t x, uint32_t y) {
+  asm volatile(
+      "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %3, 0;\n\t@q st.shared.v2.u32 [%0], {%1, %2};\n\t}"
+      ::"r"(a), "r"(x), "r"(y), "r"(static_cast<uint32_t>(p)) : "memory");
+}
+
+// Table addressing: a shared-memory table by 32-bit shared address, the
+// global spill table by pointer.
+template <bool kShared>
+struct TableRef;
+template <>
+struct TableRef<true> {
+  uint32_t base;
+  __device__ explicit TableRef(uint64_t* t) : base(smem_addr(t)) {}
+  __device__ uint32_t at(int entry) const { return base + 8u * static_cast<uint32_t>(entry); }
+};
+template <>
+struct TableRef<false> {
+  uint64_t* base;
+  __device__ explicit TableRef(uint64_t* t) : base(t) {}
+  __device__ uint64_t* at(int entry) const { return base + entry; }
+};
 
 // This group's bits of a full-warp ballot.
 template <int G>
@@ -89,20 +135,13 @@ __device__ __forceinline__ uint32_t group_bits(uint32_t ballot, int gbase) {
   return G == 32 ? ballot : (ballot >> gbase) & ((1u << G) - 1u);
 }
 
-__device__ __forceinline__ void sts64_if(bool p, uint32_t a, uint64_t v) {
-  asm volatile(
-      "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q st.shared.u64 [%0], %1;\n\t}"
-      ::"r"(a), "l"(v), "r"(static_cast<uint32_t>(p)) : "memory");
-}
-
-// Columns of the per-window PM[T[i]] buffer: 0..wt-1 hold the masks, wt..
-// kPmCols-1 hold all ones ("virtual" text columns past the window end).
-constexpr int kPmCols = 136;
+// Columns of the per-window PM[T[i]] buffer: 0..wt-1 hold the masks, wt..63
+// hold all ones ("virtual" text columns past the window end).
+constexpr int kPmCols = kMaxW;
 
 // Shared-memory working set of one group besides its table.
 struct GroupSmem {
   uint64_t pmcol[kPmCols];  // PM[T[i]] for text column i, all ones past wt
-  uint64_t bridge[kMaxW];   // last row of the previous pass, columns 0..wt-1
 };
 
 // Step 1: pattern masks by ballot, then PM[T[i]] per text column. Groups with
@@ -149,137 +188,171 @@ __device__ __forceinline__ void build_masks(int r, int gbase, bool ga,
       const uint64_t v = c == 0 ? pm0 : c == 1 ? pm1 : c == 2 ? pm2 : pm3;
       pmcol[i] = i < wt ? v : ~0ull;
     }
-    for (int i = 64 + r; i < kPmCols; i += G) pmcol[i] = ~0ull;
   }
 }
 
 // Steps 2-4: distance calculation with row early termination.
 //
-// Rows q of the pass starting at b: lane r owns q = b + r*K + k, k < K. The
-// cell (i, q) is computed at step s = (wt-1-i) + (q-b), so each lane updates
-// K cells of one anti-diagonal per step. Cells outside 0 <= i < wt are
-// computed too: past the window end (i >= wt) the all-ones masks keep every
-// row at its initial value R_wt (with PM all ones, (R_wt[q] << 1 | ~0) &
-// (R_wt[q-1] << 1) & (R_wt[q-1] << 1) & R_wt[q-1] = R_wt[q]); before column 0
-// (i < 0) the values are never read. Steps are counted from t = s + delta,
-// delta aligning t with the unrolled loop so that sub-row k of a lane reaches
-// column 0 at an iteration u == k; the lane notes then whether the row holds
-// the solution.
+// Column strips: lane c of the group owns the C = 64/G text columns
+// [c*C, c*C + C) and computes one error row per step, right to left within
+// its strip; lane c+1 runs one row ahead of lane c, so at step t lane c
+// computes row d = t - (G-1-c). The cells of a strip form a chain through
+// the match term (R_i[d] needs R_{i+1}[d]); everything else a cell needs comes
+// from the previous row, which the lane holds in registers:
+//   X_i = (R_{i+1}[d-1] << 1) & (R_i[d-1] << 1) & R_{i+1}[d-1]   (S, I, D)
+//   R_i[d] = ((R_{i+1}[d] << 1) | PM[T[i]]) & X_i                 (M)
+// so each chain link is one shift and one 3-input logic op. The strip's right
+// neighbour R_{c*C+C}[d] is lane c+1's leftmost cell of the row, received by
+// one shuffle; lane G-1's right neighbour is column 64, whose value is the
+// initial column R_wt[d] = ~0 << d. Columns at or past wt use all-ones masks,
+// which keep every row at that initial value ((~0<<q << 1 | ~0) & (~0<<(q-1)
+// << 1) & (~0<<(q-1) << 1) & ~0<<(q-1) = ~0 << q), so the window's real end
+// needs no special case. Bits at and above wp may differ from the
+// recurrence's zeros there (~0 << d instead of 0 once d >= wp); they never
+// reach the bits below wp.
 //
-// Per sub-row k the lane keeps C = R_{i+1}[q] (and C << 1) and
-// UP = R_{i+1}[q-1] (and UP << 1). The table `tab` (shared memory, or the
-// global spill area) receives rows below `store_rows` at row stride S.
-// FIRST marks the pass b = 0, whose row -1 is all ones.
-template <int G, int K, bool FIRST>
-__device__ __forceinline__ void dc_pass(int r, int gbase, int b, bool gpass, int wp, int wt,
-                                        int kmax, int ncol_store, int S, int store_rows,
-                                        const uint64_t* pmcol, uint64_t* bridge, uint64_t* tab,
-                                        int& found) {
-  constexpr int GK = G * K;
-  const int q0 = b + r * K;
-  uint64_t C[K], CS[K], UP[K], UPS[K], PMR[K];
-  int nb[K];  // columns [0, nb) of sub-row k are stored
-  uint32_t row_ok = 0;  // bit k: row q0+k may hold the solution (q <= kmax)
-#pragma unroll
-  for (int k = 0; k < K; ++k) {
-    const int q = q0 + k;
-    C[k] = init_row(q, wp);
-    CS[k] = C[k] << 1;
-    UP[k] = q == 0 ? ~0ull : init_row(q - 1, wp);
-    UPS[k] = q == 0 ? ~0ull : (UP[k] << 1);
-    PMR[k] = ~0ull;
-    const bool store_row = gpass && q <= kmax && q < store_rows;
-    nb[k] = store_row ? ncol_store : 0;
-    row_ok |= q <= kmax ? (1u << k) : 0u;
-    // Column wt of the table holds the initial value of the row.
-    if (store_row && wt < S) tab[q * S + wt] = C[k];
-  }
-  const uint64_t lane0_ones = (FIRST && r == 0) ? ~0ull : 0ull;
-  const uint32_t row0_fix = (FIRST && r == 0) ? 1u : 0u;
-  const uint64_t init_above = FIRST ? ~0ull : init_row(b - 1, wp);
-  const uint64_t msb_mask = 1ull << (wp - 1);
-  const int delta = (K - (wt - 1) % K) % K;
-  const int t_last = wt - 1 + GK - 1 + delta;
-  const int t_first_done = wt - 1 + delta;  // first step a row can reach column 0
-  const int bridge_n = (r == G - 1 && gpass) ? wt : 0;
-  // i0: column of sub-row 0 at the first step of the block.
-  int i0 = wt - 1 + delta + r * K;
-  uint64_t* rowp[K];  // &tab[(q0+k)*S + i0 + k], the cell sub-row k writes at u = 0
-#pragma unroll
-  for (int k = 0; k < K; ++k) rowp[k] = tab + ((q0 + k) * S + i0 + k);
-  for (int t0 = 0; __any_sync(kFull, gpass && found < 0 && t0 <= t_last); t0 += K) {
-    uint32_t solmask = 0;
-    const bool check = t0 + K - 1 >= t_first_done;
-#pragma unroll
-    for (int u = 0; u < K; ++u) {
-      const int iu = i0 - u;  // column of sub-row 0 at this step
-      // Row above sub-row 0: lane r-1's last sub-row, one step old.
-      uint64_t up0 = __shfl_up_sync(kFull, C[K - 1], 1, G);
-      if (FIRST) {
-        up0 |= lane0_ones;
-      } else {
-        const uint64_t br = bridge[min(static_cast<unsigned>(iu), 63u)];
-        const uint64_t v0 = static_cast<unsigned>(iu) < static_cast<unsigned>(wt) ? br : init_above;
-        up0 = r == 0 ? v0 : up0;
-      }
-      const uint64_t ups0 = shl1(up0, row0_fix);
-      PMR[u] = pmcol[min(static_cast<unsigned>(iu), static_cast<unsigned>(kPmCols - 1))];
-#pragma unroll
-      for (int k = K - 1; k >= 0; --k) {
-        const uint64_t up = k == 0 ? up0 : C[k - 1];
-        const uint64_t ups = k == 0 ? ups0 : CS[k - 1];
-        const uint64_t nv = (CS[k] | PMR[(u - k + K) % K]) & ups & UPS[k] & UP[k];
-        UP[k] = up;
-        UPS[k] = ups;
-        C[k] = nv;
-        CS[k] = shl1(nv, 0u);
-        const int i = iu + k;
-        if (static_cast<unsigned>(i) < static_cast<unsigned>(nb[k])) rowp[k][-u] = nv;
-        if (k == K - 1 && static_cast<unsigned>(i) < static_cast<unsigned>(bridge_n)) bridge[i] = nv;
-      }
-      // Sub-row u of this lane reaches column 0 at this step iff iu + u == 0.
-      if (check) {
-        const bool at0 = iu + u == 0 && ((row_ok >> u) & 1u) && !(C[u] & msb_mask);
-        solmask |= at0 ? (1u << u) : 0u;
-      }
-    }
-    i0 -= K;
-#pragma unroll
-    for (int k = 0; k < K; ++k) rowp[k] -= K;
-    // Early termination: strips finish in lane order, so the first lane of
-    // the group with a solved row holds the smallest one. (The votes run for
-    // the whole warp every block: `check` differs between groups.)
-    const uint32_t mine = group_bits<G>(__ballot_sync(kFull, solmask != 0u), gbase);
-    const int src = mine ? gbase + __ffs(mine) - 1 : (threadIdx.x & 31);
-    const int got = __shfl_sync(kFull, q0 + __ffs(solmask) - 1, src);
-    if (gpass && found < 0 && mine) found = got;
-  }
+// Rows below 0 (a lane's first G-1-c steps) are all ones: while d < 0 every
+// shift of the chain brings in a one instead of a zero, so the lane computes
+// all-ones rows from all-ones inputs and enters row 0 with the row -1 state
+// (all ones, which reduces row 0 to the match term) without any reset.
+//
+// Row d is complete when lane 0 has computed it (step d + G - 1); the first
+// such row whose R_0 has bit wp-1 clear is d_min (improvement (2)). Lane 0
+// records it; the group checks for it every kDcUnroll steps, so up to
+// kDcUnroll - 1 further rows may be computed and stored (rows above d_min are
+// never read).
+//
+// The table `tab` (shared memory, or the global spill area) receives rows
+// below `store_rows` at row stride S, columns below `ncols` (improvements (1)
+// and (3)). Two formats:
+//   kFmtWide  : 64-bit entries R_i[d]; column wt holds R_wt[d] for the
+//               traceback (shared memory or the global spill area).
+//   kFmtBand  : 32-bit entries holding bits [e_i, e_i + 31] of R_i[d] with
+//               e_i = wp - 1 - A - i (A = band_top): the bits around the
+//               diagonal that the traceback can read while its offset
+//               (read bases - text bases committed) stays in [A-30, A-1]
+//               (shared memory; windows that are not the last, with
+//               e_i >= 0 for every stored column).
+// Returns d_min, or -1 if it is above kmax (groups with ga == false get -1).
+constexpr int kDcUnroll = 2;
+enum TableFmt { kFmtWide, kFmtBand };
+
+// Row stride (entries) of a band table with `ncols` stored columns: whole
+// strips of C = 64/G columns, so every lane stores its strip with 16-byte
+// (8-byte for C = 2) stores.
+template <int G>
+__host__ __device__ __forceinline__ int band_stride(int ncols) {
+  constexpr int C = 64 / G;
+  return (ncols + C - 1) / C * C;
 }
 
-// Returns d_min, or -1 if it is above kmax (groups with ga == false get -1).
-template <int G, int K>
+template <int G, TableFmt kFmt, bool kShared>
 __device__ __forceinline__ int dc_window(int r, int gbase, bool ga, int wp, int wt, int kmax,
-                                         int ncols, int S, int store_rows, const uint64_t* pmcol,
-                                         uint64_t* bridge, uint64_t* tab) {
-  constexpr int GK = G * K;
-  constexpr int kSearching = -1, kIdle = -2, kAbove = -3;
-  int found = ga ? kSearching : kIdle;
-  if (ga && wt == 0) found = wp <= kmax ? wp : kAbove;  // R_0 = R_wt: d_min = wp
-  const int ncol_store = min(wt, ncols);
-  {
-    const bool gpass = found == kSearching;
-    dc_pass<G, K, true>(r, gbase, 0, gpass, wp, wt, kmax, ncol_store, S, store_rows, pmcol, bridge,
-                        tab, found);
-    if (gpass && found == kSearching && GK > kmax) found = kAbove;
+                                         int ncols, int S, int store_rows, int band_top,
+                                         const uint64_t* pmcol, void* tab) {
+  constexpr int C = 64 / G;
+  static_assert(kFmt == kFmtWide || kShared, "band tables live in shared memory");
+  const int c0 = r * C;
+  uint64_t pm[C];
+#pragma unroll
+  for (int x = 0; x < C; ++x) pm[x] = pmcol[c0 + x];
+  // Row d-1 at the strip's columns and their shifted copies; the same at
+  // column c0+C; this lane's last leftmost cell; lane G-1's R_64[t].
+  uint64_t P[C], PS[C];
+#pragma unroll
+  for (int x = 0; x < C; ++x) {
+    P[x] = ~0ull;
+    PS[x] = ~0ull;
   }
-  for (int b = GK; __any_sync(kFull, found == kSearching && b <= kmax); b += GK) {
-    __syncwarp();  // the bridge row of the previous pass is complete
-    const bool gpass = found == kSearching && b <= kmax;
-    dc_pass<G, K, false>(r, gbase, b, gpass, wp, wt, kmax, ncol_store, S, store_rows, pmcol,
-                         bridge, tab, found);
-    if (gpass && found == kSearching && b + GK > kmax) found = kAbove;
+  uint64_t Pr = ~0ull, PrS = ~0ull, leftmost = ~0ull, initv = ~0ull;
+  // Wide: the strip's stored columns are [c0, c0 + n_store), written in
+  // pairs (a pair may end in the padding column of an odd-width row, which
+  // the even stride provides); lane G-1 also stores column 64 (= R_wt[d])
+  // when the table needs it. Band: a lane whose strip starts inside the
+  // stored columns writes its whole strip (the stride covers whole strips).
+  const int n_store = max(0, min(C, ncols - c0));
+  const bool store64 = kFmt == kFmtWide && r == G - 1 && ncols > 64;
+  const bool band_lane = c0 < ncols;
+  int band_sh[C];
+#pragma unroll
+  for (int x = 0; x < C; ++x) band_sh[x] = max(wp - 1 - band_top - c0 - x, 0);
+  const TableRef<kShared> tref(static_cast<uint64_t*>(tab));
+  const uint64_t msb_mask = 1ull << (wp - 1);
+  const int t_last = kmax + G - 1;  // the step at which lane 0 computes row kmax
+  bool going = ga && wt > 0;        // group-uniform
+  int first = -1;                   // lane 0: first solved row
+  int t = 0;
+  int off = (r - (G - 1)) * S + c0;  // entry offset of (row d, column c0)
+  while (__any_sync(kFull, going)) {
+#pragma unroll
+    for (int u = 0; u < kDcUnroll; ++u) {
+      const int d = t - (G - 1 - r);
+      const uint64_t from_right = __shfl_down_sync(kFull, leftmost, 1, G);
+      const uint64_t right = r == G - 1 ? initv : from_right;  // R_{c0+C}[d]
+      const uint32_t low = d < 0 ? 1u : 0u;
+      // S, I, D terms of the whole strip, from row d-1 only.
+      uint64_t X[C];
+#pragma unroll
+      for (int x = 0; x < C; ++x) {
+        const uint64_t up_r = x == C - 1 ? Pr : P[x + 1];    // R_{i+1}[d-1]
+        const uint64_t up_rs = x == C - 1 ? PrS : PS[x + 1];  // R_{i+1}[d-1] << 1
+        X[x] = up_rs & PS[x] & up_r;
+      }
+      // The match chain, right to left.
+      uint64_t curS = shl1(right, low);
+      PrS = curS;
+      Pr = right;
+#pragma unroll
+      for (int x = C - 1; x >= 0; --x) {
+        const uint64_t nv = (curS | pm[x]) & X[x];
+        curS = shl1(nv, low);
+        P[x] = nv;
+        PS[x] = curS;
+      }
+      leftmost = P[0];
+      initv <<= 1;
+      // Predicated stores, no branches.
+      const bool st_row = going && static_cast<unsigned>(d) < static_cast<unsigned>(store_rows);
+      if constexpr (kFmt == kFmtWide) {
+#pragma unroll
+        for (int x = 0; x < C; x += 2)
+          st2_if(st_row && x < n_store, tref.at(off + x), P[x], P[x + 1]);
+        st1_if(st_row && store64, tref.at(off + 64 - c0), right);
+      } else {
+        uint32_t E[C];
+#pragma unroll
+        for (int x = 0; x < C; ++x) E[x] = static_cast<uint32_t>(P[x] >> band_sh[x]);
+        const uint32_t a = tref.base + 4u * static_cast<uint32_t>(off);
+        if constexpr (C == 2) {
+          st32x2_if(st_row && band_lane, a, E[0], E[C - 1]);
+        } else {
+#pragma unroll
+          for (int x = 0; x + 3 < C; x += 4)
+            st32x4_if(st_row && band_lane, a + 4u * x, E[x], E[x + 1], E[x + 2], E[x + 3]);
+        }
+      }
+      if (first < 0 && static_cast<unsigned>(d) <= static_cast<unsigned>(kmax) &&
+          !(P[0] & msb_mask))
+        first = d;
+      ++t;
+      off += S;
+    }
+    // Lane 0 decides for its group: stop once a row is solved or row kmax
+    // has been computed. (Every lane takes part in the shuffle.)
+    const bool more = first < 0 && t <= t_last;
+    const bool group_more = __shfl_sync(kFull, more ? 1u : 0u, gbase) != 0u;
+    going = going && group_more;
   }
-  return found >= 0 ? found : -1;
+  int found = __shfl_sync(kFull, first, gbase);
+  if (ga && wt == 0) found = wp <= kmax ? wp : -1;  // R_0 = R_wt: d_min = wp
+  return ga ? found : -1;
+}
+
+// Predicated 32-bit global store (see st2_if).
+__device__ __forceinline__ void stg32_if(bool p, uint32_t* a, uint32_t v) {
+  asm volatile(
+      "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q st.global.u32 [%0], %1;\n\t}"
+      ::"l"(a), "r"(v), "r"(static_cast<uint32_t>(p)) : "memory");
 }
 
 // Appends traceback ops to the pair's CIGAR as merged runs; the lane with
@@ -297,7 +370,7 @@ struct RunWriter {
     const bool merge = len > 0 && o == op;
     const bool emit = take && len > 0 && !merge;
     const bool room = n < cap;
-    if (emit && room && writer) out[n] = (len << 4) | op;
+    stg32_if(emit && room && writer, out + n, (len << 4) | op);
     n += (emit && room) ? 1u : 0u;
     full = full || (emit && !room);
     len = take ? (merge ? len + count : count) : len;
@@ -316,67 +389,107 @@ struct RunWriter {
   }
 };
 
+// Traceback decisions of one lane, as a 3-bit code; the CIGAR op of code c
+// is nibble c of kTbOps (M = 7, X = 8, I = 1, D = 2, none = 15).
+enum : uint32_t { kTbM = 0, kTbS = 1, kTbI = 2, kTbD = 3, kTbStuck = 4 };
+constexpr uint32_t kTbOps = 0xF2187u;
+
 // Step 5. Lane r of a group evaluates the state reached after r further
 // match steps from (i, j, d); the first lane whose state is a stop or whose
 // decision is not a match ends the run. The path then takes the matches and,
-// unless it stopped, that lane's edit. Every lane of the warp runs the same
-// iterations; groups that are done only take part in the ballots. Returns
-// false for a group whose walk found no edge (never expected).
-template <int G>
+// unless it stopped, that lane's edit. The ending lane's decision reaches the
+// group by one shuffle; whether it stopped follows from the group-uniform
+// counters. Every lane of the warp runs the same iterations; groups that are
+// done only take part in the votes. Returns false for a group whose walk
+// found no edge (never expected).
+//
+// With a band table (kFmtBand) the bits a lane tests sit at k-1, k and k+1
+// of its entries, k = A - (cp - ct), the same for every lane of the group
+// (the lanes look ahead along one diagonal). A group whose offset leaves the
+// band stops before the iteration that would need it and sets `over`; its
+// caller redoes the window with a wide table.
+template <int G, TableFmt kFmt>
 __device__ __forceinline__ bool tb_window(int r, int gbase, bool ga, int wp, int wt, int dmin,
-                                          bool last, int commit, int ncols, int S,
-                                          const uint64_t* pmcol, const uint64_t* tab,
+                                          bool last, int commit, int ncols, int S, int band_top,
+                                          const uint64_t* pmcol, const void* tab,
                                           RunWriter& rw, bool writer, int& cp_out, int& ct_out,
-                                          uint32_t& edits) {
+                                          uint32_t& edits, bool& over) {
   int i = 0, j = wp - 1, d = dmin, cp = 0, ct = 0;
   bool run = ga, ok = true;
+  // Offset of row d in the table; groups that are not tracing here use row
+  // 0 (their d may be -1 or a row that lives in the other table).
+  int rowd = run ? dmin * S : 0;
   // Columns c and c+1 of a row are read for c <= cmax (always inside the row).
   const int cmax = ncols >= 2 ? ncols - 2 : 0;
   while (__any_sync(kFull, run)) {
+    int kb = 0;
+    if constexpr (kFmt == kFmtBand) {
+      kb = band_top - (cp - ct);
+      const bool in_band = kb >= 1 && kb <= 30;
+      over = over || (run && !in_band);
+      run = run && in_band;
+      kb = min(max(kb, 1), 30);
+    }
     const int il = i + r;
     const int jl = j - r;
     const bool stop = last ? jl < 0 : (cp + r >= commit || ct + r >= commit);
     const int ic = min(il, cmax);
-    // Groups that are not tracing here read row 0: their d may be -1 or a
-    // row that lives in the other (spill or shared) table.
-    const int dl = (run && d > 0) ? d : 0;
-    const int dm = (run && d > 0) ? d - 1 : 0;
-    const uint64_t a = tab[dl * S + ic + 1];
-    uint64_t s = tab[dm * S + ic + 1];
-    uint64_t in = tab[dm * S + ic];
+    const int rowm = max(rowd - S, 0);  // row d-1 (row 0 stands in when d = 0)
     const uint64_t pm = pmcol[min(il, kPmCols - 1)];
-    const uint64_t none = d > 0 ? 0ull : ~0ull;  // row -1 does not exist
-    s |= none;
-    in |= none;
-    const int jc = jl > 0 ? jl : 0;
-    // bit j of (x << 1) is bit j-1 of x, and 0 (active) for j = 0.
-    const bool m_ok = !(((pm | (a << 1)) >> jc) & 1ull);
-    const bool s_ok = !(((s << 1) >> jc) & 1ull);
-    const bool i_ok = !(((in << 1) >> jc) & 1ull);
-    const bool d_ok = !((s >> jc) & 1ull);
-    uint32_t op = m_ok ? kOpMatch : s_ok ? kOpSubst : i_ok ? kOpIns : d_ok ? kOpDel : kOpStuck;
+    // Bit j of (x << 1) is bit j-1 of x, and 0 (active) for j = 0.
+    const uint64_t bit = 1ull << (jl > 0 ? jl : 0);
+    const uint64_t below = bit >> 1;
+    bool m_ok, s_ok, i_ok, d_ok;
+    if constexpr (kFmt == kFmtWide) {
+      const uint64_t* tw = static_cast<const uint64_t*>(tab);
+      const uint64_t a = tw[rowd + ic + 1];
+      const uint64_t none = d > 0 ? 0ull : ~0ull;  // row -1 does not exist
+      const uint64_t s = tw[rowm + ic + 1] | none;
+      const uint64_t in = tw[rowm + ic] | none;
+      m_ok = ((pm & bit) | (a & below)) == 0ull;
+      s_ok = (s & below) == 0ull;
+      i_ok = (in & below) == 0ull;
+      d_ok = (s & bit) == 0ull;
+    } else {
+      // Band entries: bit j-1 of column i+1, bit j of column i+1 and bit
+      // j-1 of column i sit at kb, kb+1 and kb-1.
+      const uint32_t* tn = static_cast<const uint32_t*>(tab);
+      const uint32_t mk = 1u << kb;
+      const uint32_t a = tn[rowd + ic + 1];
+      const uint32_t none = d > 0 ? 0u : ~0u;
+      const uint32_t s = tn[rowm + ic + 1] | none;
+      const uint32_t in = tn[rowm + ic] | none;
+      m_ok = (pm & bit) == 0ull && (a & mk) == 0u;
+      s_ok = (s & mk) == 0u;
+      i_ok = (in & (mk >> 1)) == 0u;
+      d_ok = (s & (mk << 1)) == 0u;
+    }
+    uint32_t code = m_ok ? kTbM : s_ok ? kTbS : i_ok ? kTbI : d_ok ? kTbD : kTbStuck;
     // Text used up (il == wt): only an insertion leaves the column (R_wt[d]
     // bit j is clear iff j < d, so d >= 1 whenever the walk is consistent).
-    op = il == wt ? (d > 0 ? kOpIns : kOpStuck) : op;
-    op = il > wt ? kOpStuck : op;
-    const uint32_t ends =
-        group_bits<G>(__ballot_sync(kFull, !run || stop || op != kOpMatch), gbase);
-    const int L = ends ? __ffs(ends) - 1 : G;  // match steps taken this iteration
-    const int src = gbase + (L < G ? L : 0);
-    const uint32_t eop = __shfl_sync(kFull, op, src);
-    const bool estop = __shfl_sync(kFull, stop ? 1u : 0u, src) != 0u;
-    const bool ended = L < G;
-    const bool edit = run && ended && !estop && eop != kOpStuck;
-    ok = ok && !(run && ended && !estop && eop == kOpStuck);
+    code = il == wt ? (d > 0 ? kTbI : kTbStuck) : code;
+    code = il > wt ? kTbStuck : code;
+    const uint32_t ends = group_bits<G>(__ballot_sync(kFull, !run || stop || code != kTbM), gbase);
+    const bool ended = ends != 0u;
+    const int L = ended ? __ffs(ends) - 1 : G;  // match steps taken this iteration
+    const int Ls = ended ? L : 0;
+    const uint32_t ecode = __shfl_sync(kFull, code, gbase + Ls);  // the ending lane's decision
+    const bool estop = last ? j - L < 0 : (cp + L >= commit || ct + L >= commit);
+    const bool edit = run && ended && !estop && ecode != kTbStuck;
+    ok = ok && !(run && ended && !estop && ecode == kTbStuck);
+    const uint32_t eop = (kTbOps >> (4u * ecode)) & 15u;
     rw.push(run, kOpMatch, static_cast<uint32_t>(L), writer);
     rw.push(edit, eop, 1u, writer);
     const int Lr = run ? L : 0;
     const int e = edit ? 1 : 0;
-    i += Lr + (e & (eop != kOpIns));
-    j -= Lr + (e & (eop != kOpDel));
+    const int e_t = e & (ecode != kTbI);  // the edit consumes a text (reference) base
+    const int e_p = e & (ecode != kTbD);  // the edit consumes a pattern (read) base
+    i += Lr + e_t;
+    j -= Lr + e_p;
     d -= e;
-    cp += Lr + (e & (eop != kOpDel));
-    ct += Lr + (e & (eop != kOpIns));
+    rowd -= edit ? S : 0;
+    cp += Lr + e_p;
+    ct += Lr + e_t;
     edits += e;
     run = run && (!ended || edit);
   }

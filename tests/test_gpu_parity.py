@@ -73,12 +73,71 @@ def test_edge_cases(kernel):
     assert_same(b, run_gpu(b, kernel), oracle.align(b), f"edge/{kernel}")
 
 
-@pytest.mark.parametrize("W,O", [(64, 0), (64, 63), (32, 8), (17, 5), (1, 0), (2, 1), (40, 24)])
+@pytest.mark.parametrize("W,O", [(64, 0), (64, 63), (32, 8), (17, 5), (1, 0), (2, 1), (40, 24), (64, 16),
+                                 (48, 20)])
 def test_window_geometry(W, O):
     b = datagen.from_pairs(edge_pairs(seed=W * 100 + O, n_random=120))
     ref = oracle.align(b, W=W, O=O, k=64)
     for kernel in ("plain", "batched"):
         assert_same(b, run_gpu(b, kernel, W=W, O=O), ref, f"W{W}O{O}/{kernel}")
+
+
+def band_overflow_windows(batch, ref, W=64, O=24):
+    """Windows (not the last) whose traceback offset (read minus reference
+    bases committed) leaves [A-30, A-1], A = min(22, O-1): the windows the
+    batched kernel must redo with a wide table. Replayed from the oracle's
+    CIGARs with the windowing rule (a window commits until W-O read or
+    reference bases are used; the last window is the one holding the read's
+    end)."""
+    A = min(22, O - 1)
+    commit = W - O
+    n = 0
+    for q in range(batch.n_pairs):
+        if int(ref.status[q]) != 0:
+            continue
+        m = int(batch.read_len[q])
+        pos_p = cp = ct = 0
+        out = False
+        for w in ref.runs(q):
+            length, op = int(w) >> 4, int(w) & 15
+            for _ in range(length):
+                if m - pos_p <= W:  # the last window: no band
+                    break
+                out = out or not (A - 30 <= cp - ct <= A - 1)
+                cp += op in (7, 8, 1)
+                ct += op in (7, 8, 2)
+                if cp == commit or ct == commit:
+                    n += out
+                    pos_p += cp
+                    cp = ct = 0
+                    out = False
+    return n
+
+
+def indel_pairs(seed, n=60):
+    """Reads with one long insertion or deletion (9-40 bases) inside a window
+    that is not the last, plus a few substitutions."""
+    rnd = random.Random(seed)
+    rs = lambda L: "".join(rnd.choice("ACGT") for _ in range(L))
+    pairs = []
+    for q in range(n):
+        ref = rs(rnd.choice([300, 500, 800]))
+        g = rnd.choice([9, 12, 16, 20, 22, 25, 30, 40])
+        at = rnd.randrange(40, len(ref) - 150)
+        read = ref[:at] + rs(g) + ref[at:] if q % 2 == 0 else ref[:at] + ref[at + g:]
+        read = list(read)
+        for _ in range(len(read) // 50):
+            read[rnd.randrange(len(read))] = rnd.choice("ACGT")
+        pairs.append(("".join(read), ref))
+    return pairs
+
+
+def test_band_overflow_redo():
+    b = datagen.from_pairs(indel_pairs(seed=11))
+    ref = oracle.align(b)
+    assert band_overflow_windows(b, ref) >= 5, "the inputs should leave the band in some windows"
+    for kernel in ("batched", "plain"):
+        assert_same(b, run_gpu(b, kernel), ref, f"indels/{kernel}")
 
 
 @pytest.mark.parametrize("k", [0, 1, 5, 20, 33])
@@ -90,24 +149,25 @@ def test_error_cap(k):
         assert_same(b, run_gpu(b, kernel, k=k), ref, f"k{k}/{kernel}")
 
 
-TUNINGS = [(4, 5, 8, 38, 1), (4, 5, 8, 1, 1), (8, 3, 4, 20, -1), (8, 5, 4, 65, 1), (8, 5, 8, 2, 1),
-           (16, 3, 4, 30, 1), (32, 1, 2, 36, -1), (32, 2, 1, 65, 1), (32, 2, 3, 10, 1), (16, 3, 2, 3, 1)]
+TUNINGS = [(4, 8, 38, 1), (4, 8, 1, 1), (8, 4, 20, -1), (8, 4, 65, 1), (16, 4, 30, 1),
+           (32, 2, 36, -1), (8, 8, 2, 1), (32, 1, 65, 1), (32, 3, 10, 1), (16, 2, 3, 1),
+           (4, 16, 40, 1), (16, 16, 12, 1)]
 
 
-@pytest.mark.parametrize("G,K,ppb,rows,lpt", TUNINGS)
-def test_tunings_identical(G, K, ppb, rows, lpt):
+@pytest.mark.parametrize("G,ppb,rows,lpt", TUNINGS)
+def test_tunings_identical(G, ppb, rows, lpt):
     b = datagen.make_batch(4, pair_ids=range(40))
     ref = oracle.align(b)
-    t = ga.ga_tuning(G, K, ppb, rows, lpt)
-    assert_same(b, run_gpu(b, "batched", tuning=t), ref, f"G{G}/K{K}/ppb{ppb}/rows{rows}")
+    t = ga.ga_tuning(G, ppb, rows, lpt)
+    assert_same(b, run_gpu(b, "batched", tuning=t), ref, f"G{G}/ppb{ppb}/rows{rows}")
 
 
-@pytest.mark.parametrize("G,K,ppb,rows,lpt", TUNINGS[:4])
-def test_tunings_edge_cases(G, K, ppb, rows, lpt):
-    b = datagen.from_pairs(edge_pairs(seed=G * 10 + K, n_random=100))
+@pytest.mark.parametrize("G,ppb,rows,lpt", TUNINGS[:6])
+def test_tunings_edge_cases(G, ppb, rows, lpt):
+    b = datagen.from_pairs(edge_pairs(seed=G * 10 + ppb, n_random=100))
     ref = oracle.align(b, k=40)
-    t = ga.ga_tuning(G, K, ppb, rows, lpt)
-    assert_same(b, run_gpu(b, "batched", k=40, tuning=t), ref, f"edge G{G}/K{K}")
+    t = ga.ga_tuning(G, ppb, rows, lpt)
+    assert_same(b, run_gpu(b, "batched", k=40, tuning=t), ref, f"edge G{G}/ppb{ppb}/rows{rows}")
 
 
 @pytest.mark.parametrize("config,ids", [(2, range(0, 24)), (3, range(100, 130)), (4, range(1000, 1060))])
@@ -181,7 +241,7 @@ def test_autotune_then_default_matches_oracle():
     assert_same(b, db.results(), ref, "autotuned")
     ga.ga_tuning_set(64, 24, 64, None)  # back to the library default
     t = ga.ga_tuning_get(64, 24, 64)
-    assert (t.lanes_per_pair, t.rows_per_lane) == (16, 3)
+    assert (t.lanes_per_pair, t.pairs_per_block, t.table_rows) == (8, 4, 42)
 
 
 def test_graph_step_matches_direct_call():
