@@ -89,7 +89,7 @@ __device__ __forceinline__ void step_window(const AlignParams& p, int r, int gba
   const bool band = ga && !last && p.band_top >= 0 && can_spill;
   const bool wide = ga && !band;
   const int Sw = table_stride(ncols);
-  const int Sb = band_stride<G>(ncols);
+  const int Sb = band_stride(G, ncols);
   const int smem_rows = min(band ? 2 * tab_entries / Sb : tab_entries / Sw, kMaxRows);
   build_masks<G>(r, gbase, ga, st.read, st.pos_p, wp, st.ref, st.pos_t, wt, gs->pmcol);
   __syncwarp();
@@ -337,18 +337,12 @@ int band_top_for(int O) { return O >= 16 ? std::min(22, O - 1) : -1; }
 
 int table_entries_for(int G, int W, int O, int rows, bool band) {
   const int ncols = W - O + 1;
-  if (!band) return rows * table_stride(ncols);
-  const int C = 64 / G;
-  const int Sb = (ncols + C - 1) / C * C;
-  return (rows * Sb + 1) / 2;
+  return band ? (rows * band_stride(G, ncols) + 1) / 2 : rows * table_stride(ncols);
 }
 
 int table_rows_for(int G, int W, int O, int entries, bool band) {
   const int ncols = W - O + 1;
-  if (!band) return entries / table_stride(ncols);
-  const int C = 64 / G;
-  const int Sb = (ncols + C - 1) / C * C;
-  return 2 * entries / Sb;
+  return band ? 2 * entries / band_stride(G, ncols) : entries / table_stride(ncols);
 }
 
 cudaError_t default_tuning(int W, int O, int k, int* G, int* ppb, int* table_entries, int* lpt) {

@@ -238,12 +238,11 @@ constexpr int kDcUnroll = 2;
 enum TableFmt { kFmtWide, kFmtBand };
 
 // Row stride (entries) of a band table with `ncols` stored columns: whole
-// strips of C = 64/G columns, so every lane stores its strip with 16-byte
-// (8-byte for C = 2) stores.
-template <int G>
-__host__ __device__ __forceinline__ int band_stride(int ncols) {
-  constexpr int C = 64 / G;
-  return (ncols + C - 1) / C * C;
+// 16-byte chunks of 4 entries (8-byte chunks of 2 when a strip has C = 2
+// columns), each written by one store.
+__host__ __device__ __forceinline__ int band_stride(int G, int ncols) {
+  const int q = G == 32 ? 2 : 4;
+  return (ncols + q - 1) / q * q;
 }
 
 template <int G, TableFmt kFmt, bool kShared>
@@ -268,11 +267,11 @@ __device__ __forceinline__ int dc_window(int r, int gbase, bool ga, int wp, int 
   // Wide: the strip's stored columns are [c0, c0 + n_store), written in
   // pairs (a pair may end in the padding column of an odd-width row, which
   // the even stride provides); lane G-1 also stores column 64 (= R_wt[d])
-  // when the table needs it. Band: a lane whose strip starts inside the
-  // stored columns writes its whole strip (the stride covers whole strips).
+  // when the table needs it. Band: every chunk of the strip that starts
+  // inside the stored columns is written whole (the stride covers whole
+  // chunks).
   const int n_store = max(0, min(C, ncols - c0));
   const bool store64 = kFmt == kFmtWide && r == G - 1 && ncols > 64;
-  const bool band_lane = c0 < ncols;
   int band_sh[C];
 #pragma unroll
   for (int x = 0; x < C; ++x) band_sh[x] = max(wp - 1 - band_top - c0 - x, 0);
@@ -324,11 +323,11 @@ __device__ __forceinline__ int dc_window(int r, int gbase, bool ga, int wp, int 
         for (int x = 0; x < C; ++x) E[x] = static_cast<uint32_t>(P[x] >> band_sh[x]);
         const uint32_t a = tref.base + 4u * static_cast<uint32_t>(off);
         if constexpr (C == 2) {
-          st32x2_if(st_row && band_lane, a, E[0], E[C - 1]);
+          st32x2_if(st_row && n_store > 0, a, E[0], E[C - 1]);
         } else {
 #pragma unroll
           for (int x = 0; x + 3 < C; x += 4)
-            st32x4_if(st_row && band_lane, a + 4u * x, E[x], E[x + 1], E[x + 2], E[x + 3]);
+            st32x4_if(st_row && x < n_store, a + 4u * x, E[x], E[x + 1], E[x + 2], E[x + 3]);
         }
       }
       if (first < 0 && static_cast<unsigned>(d) <= static_cast<unsigned>(kmax) &&
