@@ -102,9 +102,13 @@ __device__ __forceinline__ void step_window(const AlignParams& p, int r, int gba
                                                 smem_rows, 0, gs->pmcol, tab_smem);
     if (wide) dmin = d2;
   }
-  // Rows 0..d_min do not fit the shared table.
+  // Rows 0..d_min do not fit the shared table. (A band pass replaced the
+  // 64-bit masks, so they are rebuilt first.)
   const bool spilled = ga && dmin >= smem_rows;
   if (__any_sync(kFull, spilled && can_spill)) {
+    __syncwarp();
+    build_masks<G>(r, gbase, spilled && can_spill, st.read, st.pos_p, wp, st.ref, st.pos_t, wt,
+                   gs->pmcol);
     __syncwarp();
     const int d3 = dc_window<G, kFmtWide, false>(r, gbase, spilled && can_spill, wp, wt, p.kmax,
                                                  ncols, Sw, kMaxRows, 0, gs->pmcol, spill);
@@ -136,6 +140,8 @@ __device__ __forceinline__ void step_window(const AlignParams& p, int r, int gba
       st.rw = rw0;
       st.edits = edits0;
     }
+    __syncwarp();
+    build_masks<G>(r, gbase, redo, st.read, st.pos_p, wp, st.ref, st.pos_t, wt, gs->pmcol);
     __syncwarp();
     dc_window<G, kFmtWide, false>(r, gbase, redo, wp, wt, p.kmax, ncols, Sw, kMaxRows, 0,
                                   gs->pmcol, spill);

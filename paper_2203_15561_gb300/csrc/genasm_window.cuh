@@ -234,7 +234,7 @@ __device__ __forceinline__ void build_masks(int r, int gbase, bool ga,
 //               (shared memory; windows that are not the last, with
 //               e_i >= 0 for every stored column).
 // Returns d_min, or -1 if it is above kmax (groups with ga == false get -1).
-constexpr int kDcUnroll = 2;
+constexpr int kDcUnroll = 4;
 enum TableFmt { kFmtWide, kFmtBand };
 
 // Row stride (entries) of a band table with `ncols` stored columns: whole
@@ -248,7 +248,7 @@ __host__ __device__ __forceinline__ int band_stride(int G, int ncols) {
 template <int G, TableFmt kFmt, bool kShared>
 __device__ __forceinline__ int dc_window(int r, int gbase, bool ga, int wp, int wt, int kmax,
                                          int ncols, int S, int store_rows, int band_top,
-                                         const uint64_t* pmcol, void* tab) {
+                                         uint64_t* pmcol, void* tab) {
   constexpr int C = 64 / G;
   static_assert(kFmt == kFmtWide || kShared, "band tables live in shared memory");
   const int c0 = r * C;
@@ -275,6 +275,23 @@ __device__ __forceinline__ int dc_window(int r, int gbase, bool ga, int wp, int 
   int band_sh[C];
 #pragma unroll
   for (int x = 0; x < C; ++x) band_sh[x] = max(wp - 1 - band_top - c0 - x, 0);
+  if constexpr (kFmt == kFmtBand) {
+    // The traceback of a band window tests PM[T[i]] in band coordinates
+    // too; they replace the 64-bit masks, which this window no longer needs
+    // (a window redone with a wide table rebuilds them).
+    __syncwarp();
+    uint32_t pb[C];
+#pragma unroll
+    for (int x = 0; x < C; ++x) pb[x] = static_cast<uint32_t>(pm[x] >> band_sh[x]);
+    const uint32_t pa = smem_addr(pmcol) + 4u * static_cast<uint32_t>(c0);
+    if constexpr (C == 2) {
+      st32x2_if(ga, pa, pb[0], pb[1]);
+    } else {
+#pragma unroll
+      for (int x = 0; x + 3 < C; x += 4) st32x4_if(ga, pa + 4u * x, pb[x], pb[x + 1], pb[x + 2], pb[x + 3]);
+    }
+    __syncwarp();
+  }
   const TableRef<kShared> tref(static_cast<uint64_t*>(tab));
   const uint64_t msb_mask = 1ull << (wp - 1);
   const int t_last = kmax + G - 1;  // the step at which lane 0 computes row kmax
@@ -375,6 +392,27 @@ struct RunWriter {
     len = take ? (merge ? len + count : count) : len;
     op = take ? o : op;
   }
+  // Appends L matches (when take_m) and then, when `edit`, one op `eop`:
+  // the two pushes of a traceback iteration in one step.
+  __device__ __forceinline__ void append(bool take_m, uint32_t L, bool edit, uint32_t eop,
+                                         bool writer) {
+    const bool tm = take_m && L > 0;
+    const bool e1 = tm && len > 0 && op != kOpMatch;  // close the open run
+    const uint32_t w1 = (len << 4) | op;
+    const uint32_t op1 = tm ? kOpMatch : op;
+    const uint32_t len1 = tm ? (op == kOpMatch ? len + L : L) : len;
+    const bool e2 = edit && len1 > 0 && op1 != eop;
+    const uint32_t w2 = (len1 << 4) | op1;
+    op = edit ? eop : op1;
+    len = edit ? (len1 > 0 && op1 == eop ? len1 + 1 : 1u) : len1;
+    const bool r1 = n < cap;
+    stg32_if(e1 && r1 && writer, out + n, w1);
+    const uint32_t n1 = n + ((e1 && r1) ? 1u : 0u);
+    const bool r2 = n1 < cap;
+    stg32_if(e2 && r2 && writer, out + n1, w2);
+    n = n1 + ((e2 && r2) ? 1u : 0u);
+    full = full || (e1 && !r1) || (e2 && !r2);
+  }
   __device__ __forceinline__ void flush(bool writer) {
     if (len > 0) {
       if (n < cap) {
@@ -413,7 +451,8 @@ __device__ __forceinline__ bool tb_window(int r, int gbase, bool ga, int wp, int
                                           const uint64_t* pmcol, const void* tab,
                                           RunWriter& rw, bool writer, int& cp_out, int& ct_out,
                                           uint32_t& edits, bool& over) {
-  int i = 0, j = wp - 1, d = dmin, cp = 0, ct = 0;
+  // The walk is at text column ct and pattern bit wp-1-cp.
+  int d = dmin, cp = 0, ct = 0;
   bool run = ga, ok = true;
   // Offset of row d in the table; groups that are not tracing here use row
   // 0 (their d may be -1 or a row that lives in the other table).
@@ -424,41 +463,44 @@ __device__ __forceinline__ bool tb_window(int r, int gbase, bool ga, int wp, int
     int kb = 0;
     if constexpr (kFmt == kFmtBand) {
       kb = band_top - (cp - ct);
-      const bool in_band = kb >= 1 && kb <= 30;
+      const bool in_band = static_cast<unsigned>(kb - 1) <= 29u;
       over = over || (run && !in_band);
       run = run && in_band;
-      kb = min(max(kb, 1), 30);
+      kb &= 31;
     }
-    const int il = i + r;
-    const int jl = j - r;
-    const bool stop = last ? jl < 0 : (cp + r >= commit || ct + r >= commit);
+    // Lanes r >= lim look at or past the stop point (group-uniform).
+    const int lim = last ? wp - cp : min(commit - cp, commit - ct);
+    const bool stop = r >= lim;
+    const int il = ct + r;
     const int ic = min(il, cmax);
     const int rowm = max(rowd - S, 0);  // row d-1 (row 0 stands in when d = 0)
-    const uint64_t pm = pmcol[min(il, kPmCols - 1)];
-    // Bit j of (x << 1) is bit j-1 of x, and 0 (active) for j = 0.
-    const uint64_t bit = 1ull << (jl > 0 ? jl : 0);
-    const uint64_t below = bit >> 1;
     bool m_ok, s_ok, i_ok, d_ok;
     if constexpr (kFmt == kFmtWide) {
+      const int jl = wp - 1 - cp - r;
       const uint64_t* tw = static_cast<const uint64_t*>(tab);
+      const uint64_t pm = pmcol[min(il, kPmCols - 1)];
       const uint64_t a = tw[rowd + ic + 1];
       const uint64_t none = d > 0 ? 0ull : ~0ull;  // row -1 does not exist
       const uint64_t s = tw[rowm + ic + 1] | none;
       const uint64_t in = tw[rowm + ic] | none;
+      // Bit j of (x << 1) is bit j-1 of x, and 0 (active) for j = 0.
+      const uint64_t bit = 1ull << (jl > 0 ? jl : 0);
+      const uint64_t below = bit >> 1;
       m_ok = ((pm & bit) | (a & below)) == 0ull;
       s_ok = (s & below) == 0ull;
       i_ok = (in & below) == 0ull;
       d_ok = (s & bit) == 0ull;
     } else {
-      // Band entries: bit j-1 of column i+1, bit j of column i+1 and bit
-      // j-1 of column i sit at kb, kb+1 and kb-1.
+      // Band entries: bit j of PM[T[i]], bit j-1 of column i+1, bit j of
+      // column i+1 and bit j-1 of column i sit at kb, kb, kb+1 and kb-1.
       const uint32_t* tn = static_cast<const uint32_t*>(tab);
+      const uint32_t pmv = reinterpret_cast<const uint32_t*>(pmcol)[min(il, kPmCols - 1)];
       const uint32_t mk = 1u << kb;
       const uint32_t a = tn[rowd + ic + 1];
       const uint32_t none = d > 0 ? 0u : ~0u;
       const uint32_t s = tn[rowm + ic + 1] | none;
       const uint32_t in = tn[rowm + ic] | none;
-      m_ok = (pm & bit) == 0ull && (a & mk) == 0u;
+      m_ok = ((pmv | a) & mk) == 0u;
       s_ok = (s & mk) == 0u;
       i_ok = (in & (mk >> 1)) == 0u;
       d_ok = (s & (mk << 1)) == 0u;
@@ -471,24 +513,18 @@ __device__ __forceinline__ bool tb_window(int r, int gbase, bool ga, int wp, int
     const uint32_t ends = group_bits<G>(__ballot_sync(kFull, !run || stop || code != kTbM), gbase);
     const bool ended = ends != 0u;
     const int L = ended ? __ffs(ends) - 1 : G;  // match steps taken this iteration
-    const int Ls = ended ? L : 0;
-    const uint32_t ecode = __shfl_sync(kFull, code, gbase + Ls);  // the ending lane's decision
-    const bool estop = last ? j - L < 0 : (cp + L >= commit || ct + L >= commit);
-    const bool edit = run && ended && !estop && ecode != kTbStuck;
-    ok = ok && !(run && ended && !estop && ecode == kTbStuck);
-    const uint32_t eop = (kTbOps >> (4u * ecode)) & 15u;
-    rw.push(run, kOpMatch, static_cast<uint32_t>(L), writer);
-    rw.push(edit, eop, 1u, writer);
+    // The decision of the lane that ends the run.
+    const uint32_t ecode = __shfl_sync(kFull, code, gbase + (ended ? L : 0));
+    const bool live = run && ended && L < lim;  // the iteration ends in an edit decision
+    const bool edit = live && ecode != kTbStuck;
+    ok = ok && !(live && ecode == kTbStuck);
+    rw.append(run, static_cast<uint32_t>(L), edit, (kTbOps >> (4u * ecode)) & 15u, writer);
     const int Lr = run ? L : 0;
     const int e = edit ? 1 : 0;
-    const int e_t = e & (ecode != kTbI);  // the edit consumes a text (reference) base
-    const int e_p = e & (ecode != kTbD);  // the edit consumes a pattern (read) base
-    i += Lr + e_t;
-    j -= Lr + e_p;
     d -= e;
     rowd -= edit ? S : 0;
-    cp += Lr + e_p;
-    ct += Lr + e_t;
+    cp += Lr + (e & (ecode != kTbD));  // the edit consumes a pattern (read) base
+    ct += Lr + (e & (ecode != kTbI));  // the edit consumes a text (reference) base
     edits += e;
     run = run && (!ended || edit);
   }
