@@ -90,16 +90,21 @@ __device__ __forceinline__ void step_window(const AlignParams& p, int r, int gba
   const bool wide = ga && !band;
   const int Sw = table_stride(ncols);
   const int Sb = band_stride(G, ncols);
-  const int smem_rows = min(band ? 2 * tab_entries / Sb : tab_entries / Sw, kMaxRows);
-  build_masks<G>(r, gbase, ga, st.read, st.pos_p, wp, st.ref, st.pos_t, wt, gs->pmcol);
+  // The last kPmCols words of the area hold the 64-bit PM columns: a wide
+  // table stays clear of them, a band table may overwrite them once its DC
+  // has loaded them.
+  uint64_t* pmcol = tab_smem + (tab_entries - kPmCols);
+  const int smem_rows =
+      min(band ? 2 * tab_entries / Sb : (tab_entries - kPmCols) / Sw, kMaxRows);
+  build_masks<G>(r, gbase, ga, st.read, st.pos_p, wp, st.ref, st.pos_t, wt, pmcol);
   __syncwarp();
   int dmin = -1;
   if (__any_sync(kFull, band))
     dmin = dc_window<G, kFmtBand, true>(r, gbase, band, wp, wt, p.kmax, ncols, Sb, smem_rows,
-                                        p.band_top, gs->pmcol, tab_smem);
+                                        p.band_top, pmcol, gs->pmb, tab_smem);
   if (__any_sync(kFull, wide)) {
     const int d2 = dc_window<G, kFmtWide, true>(r, gbase, wide, wp, wt, p.kmax, ncols, Sw,
-                                                smem_rows, 0, gs->pmcol, tab_smem);
+                                                smem_rows, 0, pmcol, gs->pmb, tab_smem);
     if (wide) dmin = d2;
   }
   // Rows 0..d_min do not fit the shared table. (A band pass replaced the
@@ -108,10 +113,10 @@ __device__ __forceinline__ void step_window(const AlignParams& p, int r, int gba
   if (__any_sync(kFull, spilled && can_spill)) {
     __syncwarp();
     build_masks<G>(r, gbase, spilled && can_spill, st.read, st.pos_p, wp, st.ref, st.pos_t, wt,
-                   gs->pmcol);
+                   pmcol);
     __syncwarp();
     const int d3 = dc_window<G, kFmtWide, false>(r, gbase, spilled && can_spill, wp, wt, p.kmax,
-                                                 ncols, Sw, kMaxRows, 0, gs->pmcol, spill);
+                                                 ncols, Sw, kMaxRows, 0, pmcol, gs->pmb, spill);
     if (spilled && can_spill) dmin = d3;
   }
   __syncwarp();
@@ -124,7 +129,7 @@ __device__ __forceinline__ void step_window(const AlignParams& p, int r, int gba
   if (__any_sync(kFull, trace && band && !spilled)) {
     int c1 = 0, t1 = 0;
     const bool ok1 = tb_window<G, kFmtBand>(r, gbase, trace && band && !spilled, wp, wt, dmin, last,
-                                            commit, ncols, Sb, p.band_top, gs->pmcol, tab_smem,
+                                            commit, ncols, Sb, p.band_top, pmcol, gs->pmb, tab_smem,
                                             st.rw, writer, c1, t1, st.edits, over);
     if (band) {
       ok = ok1;
@@ -141,16 +146,16 @@ __device__ __forceinline__ void step_window(const AlignParams& p, int r, int gba
       st.edits = edits0;
     }
     __syncwarp();
-    build_masks<G>(r, gbase, redo, st.read, st.pos_p, wp, st.ref, st.pos_t, wt, gs->pmcol);
+    build_masks<G>(r, gbase, redo, st.read, st.pos_p, wp, st.ref, st.pos_t, wt, pmcol);
     __syncwarp();
     dc_window<G, kFmtWide, false>(r, gbase, redo, wp, wt, p.kmax, ncols, Sw, kMaxRows, 0,
-                                  gs->pmcol, spill);
+                                  pmcol, gs->pmb, spill);
     __syncwarp();
   }
   if (__any_sync(kFull, trace && wide && !spilled)) {
     int c2 = 0, t2 = 0;
     const bool ok2 = tb_window<G, kFmtWide>(r, gbase, trace && wide && !spilled, wp, wt, dmin, last,
-                                            commit, ncols, Sw, 0, gs->pmcol, tab_smem, st.rw,
+                                            commit, ncols, Sw, 0, pmcol, gs->pmb, tab_smem, st.rw,
                                             writer, c2, t2, st.edits, unused);
     if (wide && !spilled) {
       ok = ok2;
@@ -162,7 +167,7 @@ __device__ __forceinline__ void step_window(const AlignParams& p, int r, int gba
   if (__any_sync(kFull, global_tb)) {
     int c3 = 0, t3 = 0;
     const bool ok3 = tb_window<G, kFmtWide>(r, gbase, global_tb, wp, wt, dmin, last, commit, ncols,
-                                            Sw, 0, gs->pmcol, spill, st.rw, writer, c3, t3,
+                                            Sw, 0, pmcol, gs->pmb, spill, st.rw, writer, c3, t3,
                                             st.edits, unused);
     if (global_tb) {
       ok = ok3;
@@ -194,7 +199,7 @@ __device__ __forceinline__ void step_window(const AlignParams& p, int r, int gba
 // memory, pairs in index order.
 // ---------------------------------------------------------------------------
 
-constexpr int kPlainTableEntries = kMaxRows * kMaxStride;
+constexpr int kPlainTableEntries = kMaxRows * kMaxStride + kPmCols;
 constexpr size_t kPlainSmem = sizeof(GroupSmem) + sizeof(uint64_t) * kPlainTableEntries;
 
 __global__ void __launch_bounds__(32) align_plain_kernel(const AlignParams p) {
@@ -343,12 +348,13 @@ int band_top_for(int O) { return O >= 16 ? std::min(22, O - 1) : -1; }
 
 int table_entries_for(int G, int W, int O, int rows, bool band) {
   const int ncols = W - O + 1;
-  return band ? (rows * band_stride(G, ncols) + 1) / 2 : rows * table_stride(ncols);
+  return band ? std::max((rows * band_stride(G, ncols) + 1) / 2, kPmCols)
+              : rows * table_stride(ncols) + kPmCols;
 }
 
 int table_rows_for(int G, int W, int O, int entries, bool band) {
   const int ncols = W - O + 1;
-  return band ? 2 * entries / band_stride(G, ncols) : entries / table_stride(ncols);
+  return band ? 2 * entries / band_stride(G, ncols) : (entries - kPmCols) / table_stride(ncols);
 }
 
 cudaError_t default_tuning(int W, int O, int k, int* G, int* ppb, int* table_entries, int* lpt) {
@@ -362,9 +368,9 @@ cudaError_t default_tuning(int W, int O, int k, int* G, int* ppb, int* table_ent
     return cudaSuccess;
   }
   *G = 8;
-  *ppb = 4;
-  // Rows 0..41 of a window that is not the last (W-O+1 stored columns).
-  *table_entries = table_entries_for(*G, W, O, 42, band);
+  *ppb = 8;
+  // Rows 0..38 of a window that is not the last (W-O+1 stored columns).
+  *table_entries = table_entries_for(*G, W, O, 39, band);
   *lpt = 1;
   return cudaSuccess;
 }
@@ -375,7 +381,9 @@ cudaError_t resolve_plan(int W, int O, int k, int G, int ppb, int table_entries,
   (void)k;
   if (!batch_variant_exists(G)) return cudaErrorInvalidValue;
   if (ppb < 1 || ppb * G > 256 || (ppb * G) % 32 != 0) return cudaErrorInvalidValue;  // whole warps
-  table_entries = std::max(kMaxStride, std::min(table_entries, kMaxRows * kMaxStride));
+  // The area holds the table rows and the 64 words of 64-bit PM columns.
+  table_entries =
+      std::max(kMaxStride + kPmCols, std::min(table_entries, kMaxRows * kMaxStride + kPmCols));
   table_entries &= ~1;  // keep every group's area 16-byte aligned
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);

@@ -96,7 +96,8 @@ extern "C" int ga_align_batch_noalloc(const uint8_t* d_reads, const uint64_t* d_
   // never needs a spill area (and runs without band tables, whose overflow
   // would need one).
   ga::BatchPlan plan{};
-  cudaError_t e = ga::resolve_plan(W, O, k, 16, 2, ga::kMaxRows * ga::kMaxStride, 1, false, &plan);
+  cudaError_t e = ga::resolve_plan(W, O, k, 16, 2, ga::kMaxRows * ga::kMaxStride + ga::kPmCols, 1,
+                                   false, &plan);
   if (e != cudaSuccess) return GA_ECUDA;
   const ga::WorkspaceLayout L = ga::workspace_layout(n_pairs, plan);
   if (L.order != kOrderOffset || L.order + 4ull * n_pairs > kScratchBytes) return GA_ENOSPC;

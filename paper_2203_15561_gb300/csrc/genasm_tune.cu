@@ -67,7 +67,7 @@ int bad_wok(int W, int O, int k) { return W < 1 || W > GA_MAX_W || O < 0 || O >=
 
 // Candidate tunings for a workload whose windows keep about `rows` rows.
 std::vector<ga_tuning> candidates(int rows) {
-  const int lo = std::min(65, std::max(4, rows + 4));
+  const int lo = std::min(65, std::max(4, rows + 5));
   const int hi = std::min(65, std::max(6, rows + 8));
   std::vector<ga_tuning> c;
   const int shapes[][2] = {{4, 8}, {4, 16}, {8, 4}, {8, 8}, {16, 2}, {16, 4}, {32, 1}, {32, 2}};

@@ -136,12 +136,15 @@ __device__ __forceinline__ uint32_t group_bits(uint32_t ballot, int gbase) {
 }
 
 // Columns of the per-window PM[T[i]] buffer: 0..wt-1 hold the masks, wt..63
-// hold all ones ("virtual" text columns past the window end).
+// hold all ones ("virtual" text columns past the window end). The 64-bit
+// buffer (pmcol) lives in the last kPmCols words of the group's table area:
+// a band window needs it only until its DC has loaded it into registers, a
+// wide window keeps it out of its table rows.
 constexpr int kPmCols = kMaxW;
 
-// Shared-memory working set of one group besides its table.
+// Shared-memory working set of one group besides its table area.
 struct GroupSmem {
-  uint64_t pmcol[kPmCols];  // PM[T[i]] for text column i, all ones past wt
+  uint32_t pmb[kPmCols];  // band windows: PM[T[i]] in band coordinates
 };
 
 // Step 1: pattern masks by ballot, then PM[T[i]] per text column. Groups with
@@ -248,7 +251,7 @@ __host__ __device__ __forceinline__ int band_stride(int G, int ncols) {
 template <int G, TableFmt kFmt, bool kShared>
 __device__ __forceinline__ int dc_window(int r, int gbase, bool ga, int wp, int wt, int kmax,
                                          int ncols, int S, int store_rows, int band_top,
-                                         uint64_t* pmcol, void* tab) {
+                                         const uint64_t* pmcol, uint32_t* pmb, void* tab) {
   constexpr int C = 64 / G;
   static_assert(kFmt == kFmtWide || kShared, "band tables live in shared memory");
   const int c0 = r * C;
@@ -277,13 +280,13 @@ __device__ __forceinline__ int dc_window(int r, int gbase, bool ga, int wp, int 
   for (int x = 0; x < C; ++x) band_sh[x] = max(wp - 1 - band_top - c0 - x, 0);
   if constexpr (kFmt == kFmtBand) {
     // The traceback of a band window tests PM[T[i]] in band coordinates
-    // too; they replace the 64-bit masks, which this window no longer needs
-    // (a window redone with a wide table rebuilds them).
+    // too. After this the 64-bit masks are dead: the band rows may overwrite
+    // them (a window redone with a wide table rebuilds them).
     __syncwarp();
     uint32_t pb[C];
 #pragma unroll
     for (int x = 0; x < C; ++x) pb[x] = static_cast<uint32_t>(pm[x] >> band_sh[x]);
-    const uint32_t pa = smem_addr(pmcol) + 4u * static_cast<uint32_t>(c0);
+    const uint32_t pa = smem_addr(pmb) + 4u * static_cast<uint32_t>(c0);
     if constexpr (C == 2) {
       st32x2_if(ga, pa, pb[0], pb[1]);
     } else {
@@ -448,7 +451,8 @@ constexpr uint32_t kTbOps = 0xF2187u;
 template <int G, TableFmt kFmt>
 __device__ __forceinline__ bool tb_window(int r, int gbase, bool ga, int wp, int wt, int dmin,
                                           bool last, int commit, int ncols, int S, int band_top,
-                                          const uint64_t* pmcol, const void* tab,
+                                          const uint64_t* pmcol, const uint32_t* pmb,
+                                          const void* tab,
                                           RunWriter& rw, bool writer, int& cp_out, int& ct_out,
                                           uint32_t& edits, bool& over) {
   // The walk is at text column ct and pattern bit wp-1-cp.
@@ -494,7 +498,7 @@ __device__ __forceinline__ bool tb_window(int r, int gbase, bool ga, int wp, int
       // Band entries: bit j of PM[T[i]], bit j-1 of column i+1, bit j of
       // column i+1 and bit j-1 of column i sit at kb, kb, kb+1 and kb-1.
       const uint32_t* tn = static_cast<const uint32_t*>(tab);
-      const uint32_t pmv = reinterpret_cast<const uint32_t*>(pmcol)[min(il, kPmCols - 1)];
+      const uint32_t pmv = pmb[min(il, kPmCols - 1)];
       const uint32_t mk = 1u << kb;
       const uint32_t a = tn[rowd + ic + 1];
       const uint32_t none = d > 0 ? 0u : ~0u;

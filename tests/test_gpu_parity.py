@@ -241,7 +241,7 @@ def test_autotune_then_default_matches_oracle():
     assert_same(b, db.results(), ref, "autotuned")
     ga.ga_tuning_set(64, 24, 64, None)  # back to the library default
     t = ga.ga_tuning_get(64, 24, 64)
-    assert (t.lanes_per_pair, t.pairs_per_block, t.table_rows) == (8, 4, 42)
+    assert (t.lanes_per_pair, t.pairs_per_block, t.table_rows) == (8, 8, 39)
 
 
 def test_graph_step_matches_direct_call():
