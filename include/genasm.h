@@ -313,6 +313,10 @@ int ga_measure_int_peak(double out[3], ga_stream_t stream);
  *
  * Inputs (device): d_reads/d_refs packed bases; d_read_off/d_ref_off byte
  * offsets (uint64, n_pairs); d_read_len/d_ref_len lengths in bases (uint32).
+ * The kernels read the packed buffers in aligned 4-byte words: the words
+ * holding a sequence's first and last bytes are read whole, so those bytes'
+ * neighbours must lie in mapped device memory (always true inside one
+ * device allocation, whose start is at least 256-byte aligned).
  * Outputs (device, n_pairs each): d_dist edit distance (-1 unless status OK);
  * d_status GA_PAIR_*; d_ref_consumed reference bases the alignment spans
  * (-1 on failure); d_n_runs CIGAR runs written. d_cigar receives pair p's

@@ -21,6 +21,9 @@ struct PairState {
   uint32_t pair, m, n, pos_p, pos_t, edits, windows;
   int32_t status;
   bool busy;
+  bool a_valid;          // blocks ra/ta hold this window's bases
+  SeqBlock ra, ta;       // read / reference blocks of this window
+  SeqBlock rb, tb;       // the next window's blocks (loading)
 };
 
 __device__ __forceinline__ void finish_pair(const AlignParams& p, PairState& st, bool writer) {
@@ -55,6 +58,7 @@ __device__ __forceinline__ void begin_pair(const AlignParams& p, uint32_t pair, 
   st.pos_p = st.pos_t = st.edits = st.windows = 0;
   st.status = kPairOk;
   st.busy = true;
+  st.a_valid = false;
   if (st.m == 0) finish_pair(p, st, writer);  // empty read: nothing to align
 }
 
@@ -96,27 +100,57 @@ __device__ __forceinline__ void step_window(const AlignParams& p, int r, int gba
   uint64_t* pmcol = tab_smem + (tab_entries - kPmCols);
   const int smem_rows =
       min(band ? 2 * tab_entries / Sb : (tab_entries - kPmCols) / Sw, kMaxRows);
-  build_masks<G>(r, gbase, ga, st.read, st.pos_p, wp, st.ref, st.pos_t, wt, pmcol);
+  uint64_t pm[64 / G];  // this lane's PM[T[i]] columns
+  if constexpr (G <= 8) {
+    // This window's bases: from the blocks loaded one window ago, or loaded
+    // now (first window of a pair, or a window past its block).
+    constexpr uint32_t kBlockBits = 32u * kPfWords;
+    const bool need_a =
+        ga && (!st.a_valid || st.ra.o0 + 2u * (st.pos_p - st.ra.pos) + 2u * wp > kBlockBits ||
+               st.ta.o0 + 2u * (st.pos_t - st.ta.pos) + 2u * wt > kBlockBits);
+    if (__any_sync(kFull, need_a)) {
+      SeqBlock nr, nt;
+      load_block<G>(need_a, r, st.read, st.m, st.pos_p, nr);
+      load_block<G>(need_a, r, st.ref, st.n, st.pos_t, nt);
+      if (need_a) {
+        st.ra = nr;
+        st.ta = nt;
+      }
+    }
+    // The next window starts within W-O bases: its blocks start loading now.
+    load_block<G>(ga && !last, r, st.read, st.m, st.pos_p, st.rb);
+    load_block<G>(ga && !last, r, st.ref, st.n, st.pos_t, st.tb);
+    uint32_t Pw[4], Tw[4];
+    block_window<G>(gbase, st.ra, st.pos_p, Pw);
+    block_window<G>(gbase, st.ta, st.pos_t, Tw);
+    window_masks<G>(r, wp, wt, Pw, Tw, pm);
+    store_pmcol<G>(wide, r, pm, pmcol);  // a wide traceback reads them from shared memory
+  } else {
+    build_masks<G>(r, gbase, ga, st.read, st.pos_p, wp, st.ref, st.pos_t, wt, pmcol);
+    __syncwarp();
+#pragma unroll
+    for (int x = 0; x < 64 / G; ++x) pm[x] = pmcol[r * (64 / G) + x];
+  }
   __syncwarp();
   int dmin = -1;
   if (__any_sync(kFull, band))
     dmin = dc_window<G, kFmtBand, true>(r, gbase, band, wp, wt, p.kmax, ncols, Sb, smem_rows,
-                                        p.band_top, pmcol, gs->pmb, tab_smem);
+                                        p.band_top, pm, gs->pmb, tab_smem);
   if (__any_sync(kFull, wide)) {
     const int d2 = dc_window<G, kFmtWide, true>(r, gbase, wide, wp, wt, p.kmax, ncols, Sw,
-                                                smem_rows, 0, pmcol, gs->pmb, tab_smem);
+                                                smem_rows, 0, pm, gs->pmb, tab_smem);
     if (wide) dmin = d2;
   }
-  // Rows 0..d_min do not fit the shared table. (A band pass replaced the
-  // 64-bit masks, so they are rebuilt first.)
+  // Rows 0..d_min do not fit the shared table. (A band table may have
+  // overwritten the 64-bit masks, which the wide traceback reads: store them
+  // again.)
   const bool spilled = ga && dmin >= smem_rows;
   if (__any_sync(kFull, spilled && can_spill)) {
     __syncwarp();
-    build_masks<G>(r, gbase, spilled && can_spill, st.read, st.pos_p, wp, st.ref, st.pos_t, wt,
-                   pmcol);
+    store_pmcol<G>(spilled && can_spill, r, pm, pmcol);
     __syncwarp();
     const int d3 = dc_window<G, kFmtWide, false>(r, gbase, spilled && can_spill, wp, wt, p.kmax,
-                                                 ncols, Sw, kMaxRows, 0, pmcol, gs->pmb, spill);
+                                                 ncols, Sw, kMaxRows, 0, pm, gs->pmb, spill);
     if (spilled && can_spill) dmin = d3;
   }
   __syncwarp();
@@ -146,10 +180,10 @@ __device__ __forceinline__ void step_window(const AlignParams& p, int r, int gba
       st.edits = edits0;
     }
     __syncwarp();
-    build_masks<G>(r, gbase, redo, st.read, st.pos_p, wp, st.ref, st.pos_t, wt, pmcol);
+    store_pmcol<G>(redo, r, pm, pmcol);
     __syncwarp();
-    dc_window<G, kFmtWide, false>(r, gbase, redo, wp, wt, p.kmax, ncols, Sw, kMaxRows, 0,
-                                  pmcol, gs->pmb, spill);
+    dc_window<G, kFmtWide, false>(r, gbase, redo, wp, wt, p.kmax, ncols, Sw, kMaxRows, 0, pm,
+                                  gs->pmb, spill);
     __syncwarp();
   }
   if (__any_sync(kFull, trace && wide && !spilled)) {
@@ -188,6 +222,12 @@ __device__ __forceinline__ void step_window(const AlignParams& p, int r, int gba
       st.cells += static_cast<uint64_t>(wt) * static_cast<uint64_t>(dmin + 1);
       st.pos_p += static_cast<uint32_t>(cp);
       st.pos_t += static_cast<uint32_t>(ct);
+    }
+    if constexpr (G <= 8) {
+      // The blocks loaded during this window hold the next window's bases.
+      st.ra = st.rb;
+      st.ta = st.tb;
+      st.a_valid = !last;
     }
     if (st.status != kPairOk || st.pos_p >= st.m) finish_pair(p, st, writer);
   }

@@ -8,8 +8,9 @@
 //
 // Per window (pattern = read window P of wp <= 64 bases, text = reference
 // window T of wt <= 64 bases) a group
-//   1. builds the pattern masks PM[c] (bit j clear iff P[wp-1-j] == c) with
-//      warp ballots, and the per-column mask PM[T[i]] in shared memory;
+//   1. builds the pattern masks PM[c] (bit j clear iff P[wp-1-j] == c) from
+//      the window's bases, prefetched into registers one window ahead, and
+//      each lane's columns PM[T[i]] in registers;
 //   2. runs the distance calculation (DC) as a wavefront over text columns:
 //      lane c owns 64/G consecutive columns and computes one error row per
 //      step, one row behind lane c+1, whose leftmost cell it receives with
@@ -147,8 +148,121 @@ struct GroupSmem {
   uint32_t pmb[kPmCols];  // band windows: PM[T[i]] in band coordinates
 };
 
-// Step 1: pattern masks by ballot, then PM[T[i]] per text column. Groups with
-// ga == false take part in the ballots only.
+// Step 1: the window's bases, pattern masks and PM[T[i]] columns.
+//
+// Bases come from 8-word blocks of the packed sequences held across the
+// group's lanes (word w in lane w % G, slot w / G). A block is loaded at a
+// window's (word-aligned) start and serves that window and the next one:
+// a window advances at most W-O bases, so the next window's 64 bases lie in
+// the same 128-base block for W-O <= 49. The group loads the block for the
+// next window while the current one runs, so its latency is hidden; the
+// first window of a pair (or one past its block) loads its block directly.
+constexpr int kPfWords = 8;
+
+struct SeqBlock {
+  uint32_t w[2];  // this lane's words of the block (slot 1 only when G < 8)
+  uint32_t pos;   // the base position the block was loaded at
+  uint32_t o0;    // bit offset of that base in word 0
+};
+
+// Loads the block holding bases pos.. of `seq` (len bases) for groups with
+// go set. Only words that hold a base of the sequence are read.
+template <int G>
+__device__ __forceinline__ void load_block(bool go, int r, const uint8_t* seq, uint32_t len,
+                                           uint32_t pos, SeqBlock& b) {
+  const uintptr_t a = reinterpret_cast<uintptr_t>(seq) + (pos >> 2);
+  const uint32_t* wa = reinterpret_cast<const uint32_t*>(a & ~static_cast<uintptr_t>(3));
+  const uint32_t o0 = 8u * static_cast<uint32_t>(a & 3u) + 2u * (pos & 3u);
+  const uint64_t lim = o0 + 2ull * (len > pos ? len - pos : 0u);  // first bit past the sequence
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    const int wi = r + s * G;
+    const bool v = go && (s == 0 || G < kPfWords) && wi < kPfWords &&
+                   32ull * static_cast<uint64_t>(wi) < lim;
+    b.w[s] = v ? __ldg(wa + wi) : 0u;
+  }
+  b.pos = pos;
+  b.o0 = o0;
+}
+
+// The 64 bases starting at `pos` (inside block b) as 4 words, base pos+u at
+// bits 2u%32.. of word u/16; every lane of the group receives them.
+template <int G>
+__device__ __forceinline__ void block_window(int gbase, const SeqBlock& b, uint32_t pos,
+                                             uint32_t (&out)[4]) {
+  const uint32_t o = b.o0 + 2u * (pos - b.pos);
+  const int k0 = static_cast<int>(min(o >> 5, static_cast<uint32_t>(kPfWords - 1)));
+  const uint32_t sh = o & 31u;
+  uint32_t x[5];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    const int wi = min(k0 + k, kPfWords - 1);
+    const uint32_t mine = (G < kPfWords && wi >= G) ? b.w[1] : b.w[0];
+    x[k] = __shfl_sync(kFull, mine, gbase + (wi & (G - 1)));
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) out[k] = __funnelshift_r(x[k], x[k + 1], sh);
+}
+
+// Bits 0, 2, ..., 30 of x, packed into bits 0..15.
+__device__ __forceinline__ uint32_t even_bits16(uint32_t x) {
+  x &= 0x55555555u;
+  x = (x | (x >> 1)) & 0x33333333u;
+  x = (x | (x >> 2)) & 0x0F0F0F0Fu;
+  x = (x | (x >> 4)) & 0x00FF00FFu;
+  return __byte_perm(x, 0u, 0x4420);
+}
+
+__device__ __forceinline__ uint64_t rev64(uint64_t x) {
+  return (static_cast<uint64_t>(__brev(static_cast<uint32_t>(x))) << 32) |
+         __brev(static_cast<uint32_t>(x >> 32));
+}
+
+// Pattern masks PM[c] (bit j clear iff P[wp-1-j] == c), from the pattern
+// window's 2-bit codes split into their low and high bit planes, and this
+// lane's columns PM[T[c0 + x]] (all ones at c0 + x >= wt).
+template <int G>
+__device__ __forceinline__ void window_masks(int r, int wp, int wt, const uint32_t (&P)[4],
+                                             const uint32_t (&T)[4], uint64_t (&pm)[64 / G]) {
+  constexpr int C = 64 / G;
+  uint32_t l16[4], h16[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    l16[k] = even_bits16(P[k]);
+    h16[k] = even_bits16(P[k] >> 1);
+  }
+  // Bit u of Lu / Hu: low / high code bit of pattern base u.
+  const uint64_t Lu = (static_cast<uint64_t>(__byte_perm(l16[2], l16[3], 0x5410)) << 32) |
+                      __byte_perm(l16[0], l16[1], 0x5410);
+  const uint64_t Hu = (static_cast<uint64_t>(__byte_perm(h16[2], h16[3], 0x5410)) << 32) |
+                      __byte_perm(h16[0], h16[1], 0x5410);
+  // Bit j <-> pattern base wp-1-j (bits at and above wp: zero).
+  const uint32_t sh = static_cast<uint32_t>(64 - wp);
+  const uint64_t L = rev64(Lu) >> sh;
+  const uint64_t H = rev64(Hu) >> sh;
+  const uint64_t pm0 = L | H;     // clear where code 0 (A)
+  const uint64_t pm1 = ~L | H;    // clear where code 1 (C)
+  const uint64_t pm2 = L | ~H;    // clear where code 2 (G)
+  const uint64_t pm3 = ~(L & H);  // clear where code 3 (T)
+  const int c0 = r * C;
+  const int wi = (2 * c0) >> 5;
+  uint32_t tw = T[0];
+  tw = wi == 1 ? T[1] : tw;
+  tw = wi == 2 ? T[2] : tw;
+  tw = wi == 3 ? T[3] : tw;
+  tw >>= (2 * c0) & 31;
+#pragma unroll
+  for (int x = 0; x < C; ++x) {
+    const uint32_t c = (tw >> (2 * x)) & 3u;
+    const uint64_t v = c == 0 ? pm0 : c == 1 ? pm1 : c == 2 ? pm2 : pm3;
+    pm[x] = c0 + x < wt ? v : ~0ull;
+  }
+}
+
+// Step 1 for wide groups (G >= 16, where a pattern mask takes at most 8
+// ballots): pattern masks by warp ballots over bases loaded directly, then
+// PM[T[i]] per text column into the 64-bit buffer. Groups with ga == false
+// take part in the ballots only.
 template <int G>
 __device__ __forceinline__ void build_masks(int r, int gbase, bool ga,
                                             const uint8_t* __restrict__ read, uint32_t pos_p,
@@ -192,6 +306,16 @@ __device__ __forceinline__ void build_masks(int r, int gbase, bool ga,
       pmcol[i] = i < wt ? v : ~0ull;
     }
   }
+}
+
+// This lane's PM[T[i]] columns into the 64-bit buffer (groups with go).
+template <int G>
+__device__ __forceinline__ void store_pmcol(bool go, int r, const uint64_t (&pm)[64 / G],
+                                            uint64_t* pmcol) {
+  constexpr int C = 64 / G;
+  const uint32_t a = smem_addr(pmcol + r * C);
+#pragma unroll
+  for (int x = 0; x < C; x += 2) st2_if(go, a + 8u * x, pm[x], pm[x + 1]);
 }
 
 // Steps 2-4: distance calculation with row early termination.
@@ -251,13 +375,13 @@ __host__ __device__ __forceinline__ int band_stride(int G, int ncols) {
 template <int G, TableFmt kFmt, bool kShared>
 __device__ __forceinline__ int dc_window(int r, int gbase, bool ga, int wp, int wt, int kmax,
                                          int ncols, int S, int store_rows, int band_top,
-                                         const uint64_t* pmcol, uint32_t* pmb, void* tab) {
+                                         const uint64_t (&pmr)[64 / G], uint32_t* pmb, void* tab) {
   constexpr int C = 64 / G;
   static_assert(kFmt == kFmtWide || kShared, "band tables live in shared memory");
   const int c0 = r * C;
   uint64_t pm[C];
 #pragma unroll
-  for (int x = 0; x < C; ++x) pm[x] = pmcol[c0 + x];
+  for (int x = 0; x < C; ++x) pm[x] = pmr[x];
   // Row d-1 at the strip's columns and their shifted copies; the same at
   // column c0+C; this lane's last leftmost cell; lane G-1's R_64[t].
   uint64_t P[C], PS[C];
