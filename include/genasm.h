@@ -350,6 +350,37 @@ int ga_align_batch_tuned(const uint8_t* d_reads, const uint64_t* d_read_off,
                          ga_stream_t stream);
 
 /*
+ * ga_align_ablation - the ablation of the paper's three improvements to
+ * GenASM (Sec. I, key ideas (1) store only the AND of the four DP vectors,
+ * (2) stop at the first row that holds the solution, (3) store only what the
+ * traceback can reach) on this GPU: the batched alignment with the window
+ * table kept in the workspace (global memory) as
+ *   variant 0: plain GenASM, the four vectors M, S, I, D of every cell of
+ *              rows 0..k and all columns;
+ *   variant 1: only their AND (idea 1);
+ *   variant 2: and only rows 0..d_min (ideas 1, 2);
+ *   variant 3: and only the columns the traceback can reach (ideas 1-3).
+ * ga_align_batch is the further step: only the reachable bits, on chip.
+ * Every variant gives ga_align_batch's outputs exactly (same arguments and
+ * contract, no tuning). d_table_bytes (NULL to skip; n_pairs x 5 uint64,
+ * overwritten) receives per pair the bytes of window table that variants
+ * 0..3 and ga_align_batch (column 4) write, summed over the pair's windows.
+ * Workspace: ga_ablation_workspace_size(n_pairs, W, O, k, variant) bytes
+ * (variant 0 holds 137 KB of table per resident pair).
+ * Errors: GA_EINVAL (also variant outside 0..3), GA_ENOSPC, GA_ECUDA.
+ */
+int ga_ablation_workspace_size(uint32_t n_pairs, int W, int O, int k, int variant,
+                               size_t* bytes_out);
+int ga_align_ablation(const uint8_t* d_reads, const uint64_t* d_read_off,
+                      const uint32_t* d_read_len, const uint8_t* d_refs, const uint64_t* d_ref_off,
+                      const uint32_t* d_ref_len, uint32_t n_pairs, int W, int O, int k,
+                      int32_t* d_dist, int32_t* d_status, int32_t* d_ref_consumed,
+                      uint32_t* d_cigar, const uint64_t* d_cigar_off, uint32_t* d_n_runs,
+                      uint32_t* d_n_windows, uint64_t* d_cells, int variant,
+                      uint64_t* d_table_bytes, void* d_workspace, size_t ws_bytes,
+                      ga_stream_t stream);
+
+/*
  * ga_align_plain - the same alignment as ga_align_batch, computed by the
  * plain GPU GenASM form: one pair per thread block, one launch, pairs in
  * index order, no work queue, no tuning, no workspace. Outputs are identical

@@ -102,6 +102,10 @@ def lib():
             so.ga_align_batch_tuned.argtypes = _ALIGN_ARGS + [_vp, _sz, ctypes.POINTER(ga_tuning), _vp]
             so.ga_align_plain.restype = _i
             so.ga_align_plain.argtypes = _ALIGN_ARGS + [_vp]
+            so.ga_ablation_workspace_size.restype = _i
+            so.ga_ablation_workspace_size.argtypes = [_u32, _i, _i, _i, _i, ctypes.POINTER(_sz)]
+            so.ga_align_ablation.restype = _i
+            so.ga_align_ablation.argtypes = _ALIGN_ARGS + [_i, _vp, _vp, _sz, _vp]
             _lib = so
         return _lib
 
@@ -214,6 +218,24 @@ def ga_align_plain(d_reads, d_read_off, d_read_len, d_refs, d_ref_off, d_ref_len
                     d_dist, d_status, d_ref_consumed, d_cigar, d_cigar_off, d_n_runs, d_n_windows,
                     d_cells)
     return _check(lib().ga_align_plain(*a, _stream(stream)), "ga_align_plain")
+
+
+def ga_ablation_workspace_size(n_pairs: int, W: int, O: int, k: int, variant: int) -> int:
+    out = _sz(0)
+    _check(lib().ga_ablation_workspace_size(n_pairs, W, O, k, variant, ctypes.byref(out)),
+           "ga_ablation_workspace_size")
+    return out.value
+
+
+def ga_align_ablation(d_reads, d_read_off, d_read_len, d_refs, d_ref_off, d_ref_len, n_pairs, W, O,
+                      k, d_dist, d_status, d_ref_consumed, d_cigar, d_cigar_off, d_n_runs,
+                      d_n_windows, d_cells, variant, d_table_bytes, d_workspace, ws_bytes,
+                      stream=None) -> int:
+    a = _align_args(d_reads, d_read_off, d_read_len, d_refs, d_ref_off, d_ref_len, n_pairs, W, O, k,
+                    d_dist, d_status, d_ref_consumed, d_cigar, d_cigar_off, d_n_runs, d_n_windows,
+                    d_cells)
+    return _check(lib().ga_align_ablation(*a, variant, _ptr(d_table_bytes), _ptr(d_workspace),
+                                          ws_bytes, _stream(stream)), "ga_align_ablation")
 
 
 GA_NOALLOC_MAX_PAIRS = 262144

@@ -9,58 +9,9 @@
 #include "genasm.h"
 #include "genasm_internal.h"
 #include "genasm_window.cuh"
+#include "genasm_pair.cuh"
 
 namespace ga {
-
-// Per-group pair state, replicated in every lane of the group.
-struct PairState {
-  const uint8_t* read;
-  const uint8_t* ref;
-  RunWriter rw;
-  uint64_t cells;
-  uint32_t pair, m, n, pos_p, pos_t, edits, windows;
-  int32_t status;
-  bool busy;
-  bool a_valid;          // blocks ra/ta hold this window's bases
-  SeqBlock ra, ta;       // read / reference blocks of this window
-  SeqBlock rb, tb;       // the next window's blocks (loading)
-};
-
-__device__ __forceinline__ void finish_pair(const AlignParams& p, PairState& st, bool writer) {
-  if (st.status == kPairOk) {
-    st.rw.flush(writer);
-    if (st.rw.full) st.status = kPairCigarFull;
-  }
-  if (writer) {
-    const bool ok = st.status == kPairOk;
-    p.dist[st.pair] = ok ? static_cast<int32_t>(st.edits) : -1;
-    p.status[st.pair] = st.status;
-    p.ref_consumed[st.pair] = ok ? static_cast<int32_t>(st.pos_t) : -1;
-    p.n_runs[st.pair] = ok ? st.rw.n : 0u;
-    if (p.n_windows) p.n_windows[st.pair] = st.windows;
-    if (p.cells) p.cells[st.pair] = st.cells;
-  }
-  st.busy = false;
-}
-
-__device__ __forceinline__ void begin_pair(const AlignParams& p, uint32_t pair, PairState& st,
-                                           bool writer) {
-  st.pair = pair;
-  st.m = p.read_len[pair];
-  st.n = p.ref_len[pair];
-  st.read = p.reads + p.read_off[pair];
-  st.ref = p.refs + p.ref_off[pair];
-  const uint64_t c0 = p.cigar_off[pair];
-  const uint64_t capl = p.cigar_cap ? p.cigar_cap[pair] : p.cigar_off[pair + 1] - c0;
-  st.rw = RunWriter{p.cigar + c0, capl > 0xffffffffull ? 0xffffffffu : static_cast<uint32_t>(capl),
-                    0u, 0u, 0u, false};
-  st.cells = 0;
-  st.pos_p = st.pos_t = st.edits = st.windows = 0;
-  st.status = kPairOk;
-  st.busy = true;
-  st.a_valid = false;
-  if (st.m == 0) finish_pair(p, st, writer);  // empty read: nothing to align
-}
 
 // One window for every busy group of the warp (the window chain of a pair is
 // serial: each window starts where the previous traceback stopped).
@@ -449,6 +400,16 @@ cudaError_t resolve_plan(int W, int O, int k, int G, int ppb, int table_entries,
   return cudaSuccess;
 }
 
+cudaError_t launch_lpt_order(const uint32_t* read_len, uint32_t n, uint32_t* hist, uint32_t* order,
+                             cudaStream_t s) {
+  const int blocks = static_cast<int>(std::min<uint32_t>((n + 255) / 256, 1024u));
+  lpt_histogram_kernel<<<blocks, 256, 0, s>>>(read_len, n, hist);
+  lpt_scan_kernel<<<1, kLptBuckets, 0, s>>>(hist);
+  lpt_scatter_kernel<<<blocks, 256, 0, s>>>(read_len, n, hist, order);
+  count_launches(3);
+  return cudaGetLastError();
+}
+
 WorkspaceLayout workspace_layout(uint32_t n_pairs, const BatchPlan& plan) {
   auto up = [](size_t x) { return (x + 255) & ~static_cast<size_t>(255); };
   WorkspaceLayout L{};
@@ -470,13 +431,8 @@ cudaError_t launch_batched(const AlignParams& p, const BatchPlan& plan, void* ws
   uint32_t* order = reinterpret_cast<uint32_t*>(w + L.order);
   cudaError_t e = cudaMemsetAsync(w, 0, L.order, s);  // counters + histogram
   if (e != cudaSuccess) return e;
-  if (plan.lpt) {
-    const int blocks = static_cast<int>(std::min<uint32_t>((p.n_pairs + 255) / 256, 1024u));
-    lpt_histogram_kernel<<<blocks, 256, 0, s>>>(p.read_len, p.n_pairs, hist);
-    lpt_scan_kernel<<<1, kLptBuckets, 0, s>>>(hist);
-    lpt_scatter_kernel<<<blocks, 256, 0, s>>>(p.read_len, p.n_pairs, hist, order);
-    count_launches(3);
-  }
+  if (plan.lpt && (e = launch_lpt_order(p.read_len, p.n_pairs, hist, order, s)) != cudaSuccess)
+    return e;
   BatchArgs a{queue, plan.lpt ? order : nullptr, reinterpret_cast<uint64_t*>(w + L.spill),
               plan.table_entries};
   const int threads = plan.pairs_per_block * plan.lanes_per_pair;

@@ -177,6 +177,36 @@ int ga_align_batch(const uint8_t* d_reads, const uint64_t* d_read_off, const uin
                               nullptr, stream);
 }
 
+int ga_ablation_workspace_size(uint32_t n_pairs, int W, int O, int k, int variant,
+                               size_t* bytes_out) {
+  if (!bytes_out || bad_wok(W, O, k) || variant < 0 || variant > 3) return GA_EINVAL;
+  return cuda_fail(ga::ablation_workspace_bytes(n_pairs, variant, bytes_out));
+}
+
+int ga_align_ablation(const uint8_t* d_reads, const uint64_t* d_read_off,
+                      const uint32_t* d_read_len, const uint8_t* d_refs, const uint64_t* d_ref_off,
+                      const uint32_t* d_ref_len, uint32_t n_pairs, int W, int O, int k,
+                      int32_t* d_dist, int32_t* d_status, int32_t* d_ref_consumed,
+                      uint32_t* d_cigar, const uint64_t* d_cigar_off, uint32_t* d_n_runs,
+                      uint32_t* d_n_windows, uint64_t* d_cells, int variant,
+                      uint64_t* d_table_bytes, void* d_workspace, size_t ws_bytes,
+                      ga_stream_t stream) {
+  if (variant < 0 || variant > 3) return GA_EINVAL;
+  ga::AlignParams p{};
+  const int rc = fill_params(d_reads, d_read_off, d_read_len, d_refs, d_ref_off, d_ref_len,
+                             n_pairs, W, O, k, d_dist, d_status, d_ref_consumed, d_cigar,
+                             d_cigar_off, d_n_runs, d_n_windows, d_cells, &p);
+  if (rc != GA_OK) return rc;
+  if (n_pairs == 0) return GA_OK;
+  p.band_top = -1;
+  size_t need = 0;
+  const cudaError_t e = ga::ablation_workspace_bytes(n_pairs, variant, &need);
+  if (e != cudaSuccess) return cuda_fail(e);
+  if (!d_workspace || ws_bytes < need) return GA_ENOSPC;
+  return cuda_fail(ga::launch_ablation(p, variant, d_table_bytes, d_workspace, ws_bytes,
+                                       reinterpret_cast<cudaStream_t>(stream)));
+}
+
 int ga_align_plain(const uint8_t* d_reads, const uint64_t* d_read_off, const uint32_t* d_read_len,
                    const uint8_t* d_refs, const uint64_t* d_ref_off, const uint32_t* d_ref_len,
                    uint32_t n_pairs, int W, int O, int k, int32_t* d_dist, int32_t* d_status,

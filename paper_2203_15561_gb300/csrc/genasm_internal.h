@@ -76,6 +76,16 @@ bool step_variant_exists(int G);
 
 WorkspaceLayout workspace_layout(uint32_t n_pairs, const BatchPlan& plan);
 
+// Ablation kernels (genasm_ablation.cu): variant 0..3, see ga_align_ablation.
+cudaError_t ablation_workspace_bytes(uint32_t n_pairs, int variant, size_t* bytes);
+cudaError_t launch_ablation(const AlignParams& p, int variant, uint64_t* table_bytes, void* ws,
+                            size_t ws_bytes, cudaStream_t s);
+
+// Longest-read-first order of n pairs (counting sort over kLptBuckets read
+// length buckets): hist must hold kLptBuckets zeroed counters, order n entries.
+cudaError_t launch_lpt_order(const uint32_t* read_len, uint32_t n, uint32_t* hist, uint32_t* order,
+                             cudaStream_t s);
+
 // Kernel launches issued by the library (process-wide counter).
 uint64_t launch_count();
 void count_launches(uint64_t n);

@@ -1,0 +1,63 @@
+// Per-pair state of a group of lanes and its start / finish, shared by the
+// alignment kernels (genasm_align.cu) and the ablation kernels
+// (genasm_ablation.cu).
+#pragma once
+
+#include <cstdint>
+
+#include "genasm_internal.h"
+#include "genasm_window.cuh"
+
+namespace ga {
+
+// Per-group pair state, replicated in every lane of the group.
+struct PairState {
+  const uint8_t* read;
+  const uint8_t* ref;
+  RunWriter rw;
+  uint64_t cells;
+  uint32_t pair, m, n, pos_p, pos_t, edits, windows;
+  int32_t status;
+  bool busy;
+  bool a_valid;          // blocks ra/ta hold this window's bases
+  SeqBlock ra, ta;       // read / reference blocks of this window
+  SeqBlock rb, tb;       // the next window's blocks (loading)
+};
+
+__device__ __forceinline__ void finish_pair(const AlignParams& p, PairState& st, bool writer) {
+  if (st.status == kPairOk) {
+    st.rw.flush(writer);
+    if (st.rw.full) st.status = kPairCigarFull;
+  }
+  if (writer) {
+    const bool ok = st.status == kPairOk;
+    p.dist[st.pair] = ok ? static_cast<int32_t>(st.edits) : -1;
+    p.status[st.pair] = st.status;
+    p.ref_consumed[st.pair] = ok ? static_cast<int32_t>(st.pos_t) : -1;
+    p.n_runs[st.pair] = ok ? st.rw.n : 0u;
+    if (p.n_windows) p.n_windows[st.pair] = st.windows;
+    if (p.cells) p.cells[st.pair] = st.cells;
+  }
+  st.busy = false;
+}
+
+__device__ __forceinline__ void begin_pair(const AlignParams& p, uint32_t pair, PairState& st,
+                                           bool writer) {
+  st.pair = pair;
+  st.m = p.read_len[pair];
+  st.n = p.ref_len[pair];
+  st.read = p.reads + p.read_off[pair];
+  st.ref = p.refs + p.ref_off[pair];
+  const uint64_t c0 = p.cigar_off[pair];
+  const uint64_t capl = p.cigar_cap ? p.cigar_cap[pair] : p.cigar_off[pair + 1] - c0;
+  st.rw = RunWriter{p.cigar + c0, capl > 0xffffffffull ? 0xffffffffu : static_cast<uint32_t>(capl),
+                    0u, 0u, 0u, false};
+  st.cells = 0;
+  st.pos_p = st.pos_t = st.edits = st.windows = 0;
+  st.status = kPairOk;
+  st.busy = true;
+  st.a_valid = false;
+  if (st.m == 0) finish_pair(p, st, writer);  // empty read: nothing to align
+}
+
+}  // namespace ga

@@ -372,11 +372,18 @@ __host__ __device__ __forceinline__ int band_stride(int G, int ncols) {
   return (ncols + q - 1) / q * q;
 }
 
-template <int G, TableFmt kFmt, bool kShared>
+//
+// Two switches serve the ablation of the paper's improvements (defaults: the
+// improved algorithm). kEt = false computes every row up to kmax instead of
+// stopping at d_min (plain GenASM); kFour stores, per cell, the four vectors
+// M, S, I, D of plain GenASM (entry 4*(d*S + i) + {0, 1, 2, 3}; wide, global)
+// instead of their AND.
+template <int G, TableFmt kFmt, bool kShared, bool kEt = true, bool kFour = false>
 __device__ __forceinline__ int dc_window(int r, int gbase, bool ga, int wp, int wt, int kmax,
                                          int ncols, int S, int store_rows, int band_top,
                                          const uint64_t (&pmr)[64 / G], uint32_t* pmb, void* tab) {
   constexpr int C = 64 / G;
+  static_assert(!kFour || (kFmt == kFmtWide && !kShared), "four-vector tables are wide, global");
   static_assert(kFmt == kFmtWide || kShared, "band tables live in shared memory");
   const int c0 = r * C;
   uint64_t pm[C];
@@ -435,11 +442,17 @@ __device__ __forceinline__ int dc_window(int r, int gbase, bool ga, int wp, int 
       const uint32_t low = d < 0 ? 1u : 0u;
       // S, I, D terms of the whole strip, from row d-1 only.
       uint64_t X[C];
+      uint64_t V4[kFour ? 4 * C : 1];  // four-vector tables: M, S, I, D of each cell
 #pragma unroll
       for (int x = 0; x < C; ++x) {
         const uint64_t up_r = x == C - 1 ? Pr : P[x + 1];    // R_{i+1}[d-1]
         const uint64_t up_rs = x == C - 1 ? PrS : PS[x + 1];  // R_{i+1}[d-1] << 1
         X[x] = up_rs & PS[x] & up_r;
+        if constexpr (kFour) {
+          V4[4 * x + 1] = up_rs;  // S
+          V4[4 * x + 2] = PS[x];  // I = R_i[d-1] << 1
+          V4[4 * x + 3] = up_r;   // D
+        }
       }
       // The match chain, right to left.
       uint64_t curS = shl1(right, low);
@@ -447,6 +460,7 @@ __device__ __forceinline__ int dc_window(int r, int gbase, bool ga, int wp, int 
       Pr = right;
 #pragma unroll
       for (int x = C - 1; x >= 0; --x) {
+        if constexpr (kFour) V4[4 * x] = curS | pm[x];  // M
         const uint64_t nv = (curS | pm[x]) & X[x];
         curS = shl1(nv, low);
         P[x] = nv;
@@ -456,7 +470,13 @@ __device__ __forceinline__ int dc_window(int r, int gbase, bool ga, int wp, int 
       initv <<= 1;
       // Predicated stores, no branches.
       const bool st_row = going && static_cast<unsigned>(d) < static_cast<unsigned>(store_rows);
-      if constexpr (kFmt == kFmtWide) {
+      if constexpr (kFour) {
+#pragma unroll
+        for (int x = 0; x < C; ++x) {
+          st2_if(st_row && x < n_store, tref.at(4 * (off + x)), V4[4 * x], V4[4 * x + 1]);
+          st2_if(st_row && x < n_store, tref.at(4 * (off + x) + 2), V4[4 * x + 2], V4[4 * x + 3]);
+        }
+      } else if constexpr (kFmt == kFmtWide) {
 #pragma unroll
         for (int x = 0; x < C; x += 2)
           st2_if(st_row && x < n_store, tref.at(off + x), P[x], P[x + 1]);
@@ -482,7 +502,7 @@ __device__ __forceinline__ int dc_window(int r, int gbase, bool ga, int wp, int 
     }
     // Lane 0 decides for its group: stop once a row is solved or row kmax
     // has been computed. (Every lane takes part in the shuffle.)
-    const bool more = first < 0 && t <= t_last;
+    const bool more = (!kEt || first < 0) && t <= t_last;
     const bool group_more = __shfl_sync(kFull, more ? 1u : 0u, gbase) != 0u;
     going = going && group_more;
   }
@@ -572,7 +592,11 @@ constexpr uint32_t kTbOps = 0xF2187u;
 // (the lanes look ahead along one diagonal). A group whose offset leaves the
 // band stops before the iteration that would need it and sets `over`; its
 // caller redoes the window with a wide table.
-template <int G, TableFmt kFmt>
+//
+// kFour walks a plain GenASM four-vector table (see dc_window): at cell (i,
+// d) the edge is M if bit j of M_i[d] is 0 (i < wt), else S, I, D by bit j of
+// S_i[d], I_i[d], D_i[d] (all ones in row 0).
+template <int G, TableFmt kFmt, bool kFour = false>
 __device__ __forceinline__ bool tb_window(int r, int gbase, bool ga, int wp, int wt, int dmin,
                                           bool last, int commit, int ncols, int S, int band_top,
                                           const uint64_t* pmcol, const uint32_t* pmb,
@@ -603,7 +627,15 @@ __device__ __forceinline__ bool tb_window(int r, int gbase, bool ga, int wp, int
     const int ic = min(il, cmax);
     const int rowm = max(rowd - S, 0);  // row d-1 (row 0 stands in when d = 0)
     bool m_ok, s_ok, i_ok, d_ok;
-    if constexpr (kFmt == kFmtWide) {
+    if constexpr (kFour) {
+      const int jl = wp - 1 - cp - r;
+      const uint64_t* t4 = static_cast<const uint64_t*>(tab) + 4 * (rowd + min(il, ncols - 1));
+      const uint64_t bit = 1ull << (jl > 0 ? jl : 0);
+      m_ok = (t4[0] & bit) == 0ull;
+      s_ok = (t4[1] & bit) == 0ull;
+      i_ok = (t4[2] & bit) == 0ull;
+      d_ok = (t4[3] & bit) == 0ull;
+    } else if constexpr (kFmt == kFmtWide) {
       const int jl = wp - 1 - cp - r;
       const uint64_t* tw = static_cast<const uint64_t*>(tab);
       const uint64_t pm = pmcol[min(il, kPmCols - 1)];

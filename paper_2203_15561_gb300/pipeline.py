@@ -96,6 +96,17 @@ class DeviceBatch:
         else:
             ga_align_batch(*self._args(stats), self.workspace, self.ws_bytes, stream)
 
+    def ablation(self, variant: int, table_bytes=None, stats: bool = True, stream=None):
+        """The alignment by ablation variant 0..3 (see ga_align_ablation) on the
+        packed batch; table_bytes: optional int64 tensor of n x 5."""
+        from . import ga_ablation_workspace_size, ga_align_ablation
+        need = ga_ablation_workspace_size(self.n, self.W, self.O, self.k, variant)
+        ws = getattr(self, "_ablation_ws", None)
+        if ws is None or ws.numel() < need:
+            ws = torch.empty(max(need, 1), dtype=torch.uint8, device=self.device)
+            self._ablation_ws = ws
+        ga_align_ablation(*self._args(stats), variant, table_bytes, ws, ws.numel(), stream)
+
     def run(self, kernel: str = "batched", tuning=None, stats: bool = True, stream=None):
         self.pack(stream)
         self.align(kernel, tuning, stats, stream)

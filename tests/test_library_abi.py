@@ -42,6 +42,10 @@ def test_bad_arguments_rejected_before_any_cuda_call():
     assert L.ga_workspace_size(10, 64, 24, 1, None) == ga.GA_EINVAL
     args = [None] * 6 + [5, 64, 24, 64] + [None] * 8
     assert L.ga_align_plain(*args, None) == ga.GA_EINVAL       # NULL buffers, n_pairs > 0
+    assert L.ga_align_ablation(*args, 0, None, None, 0, None) == ga.GA_EINVAL
+    assert L.ga_align_ablation(*([None] * 6 + [0, 64, 24, 64] + [None] * 8), 4, None, None, 0,
+                               None) == ga.GA_EINVAL          # variant outside 0..3
+    assert L.ga_ablation_workspace_size(10, 64, 24, 64, 7, ctypes.byref(sz)) == ga.GA_EINVAL
     assert L.ga_pack_2bit(None, 16, None, None, None) == ga.GA_EINVAL
     assert L.ga_pack_2bit(None, 0, None, None, None) == ga.GA_OK  # nothing to do
 
