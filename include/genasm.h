@@ -338,6 +338,33 @@ int ga_align_batch(const uint8_t* d_reads, const uint64_t* d_read_off, const uin
                    uint32_t* d_n_windows, uint64_t* d_cells,
                    void* d_workspace, size_t ws_bytes, ga_stream_t stream);
 
+/*
+ * ga_align_batch_order - ga_align_batch with another traceback priority
+ * order. When several edges leave a traceback state, the first possible one
+ * of tb_order is taken. Neither the paper nor GenASM fixes one;
+ * ga_align_batch uses M > S > I > D. tb_order packs the four edge kinds
+ * GA_EDGE_M 0 (match), GA_EDGE_S 1 (substitution), GA_EDGE_I 2 (insertion),
+ * GA_EDGE_D 3 (deletion), two bits each, highest priority in bits 0-1
+ * (GA_TB_ORDER_DEFAULT = 0xE4). Every permutation is valid: any edge the
+ * traceback may take keeps the walk on an alignment of the window, so the
+ * last window's edit count is d_min under every order. Same contract as
+ * ga_align_batch otherwise (stored tuning, workspace).
+ * Errors: GA_EINVAL (also tb_order not a permutation), GA_ENOSPC, GA_ECUDA.
+ */
+#define GA_EDGE_M 0
+#define GA_EDGE_S 1
+#define GA_EDGE_I 2
+#define GA_EDGE_D 3
+#define GA_TB_ORDER_DEFAULT 0xE4
+int ga_align_batch_order(const uint8_t* d_reads, const uint64_t* d_read_off,
+                         const uint32_t* d_read_len, const uint8_t* d_refs,
+                         const uint64_t* d_ref_off, const uint32_t* d_ref_len,
+                         uint32_t n_pairs, int W, int O, int k,
+                         int32_t* d_dist, int32_t* d_status, int32_t* d_ref_consumed,
+                         uint32_t* d_cigar, const uint64_t* d_cigar_off, uint32_t* d_n_runs,
+                         uint32_t* d_n_windows, uint64_t* d_cells, int tb_order,
+                         void* d_workspace, size_t ws_bytes, ga_stream_t stream);
+
 /* ga_align_batch with an explicit tuning (NULL = defaults). Same contract. */
 int ga_align_batch_tuned(const uint8_t* d_reads, const uint64_t* d_read_off,
                          const uint32_t* d_read_len, const uint8_t* d_refs,

@@ -71,7 +71,7 @@ def lib(mutant: int | None = None):
             so.oracle_align_batch.restype = ctypes.c_int
             so.oracle_align_batch.argtypes = [
                 _u8p, _u64p, _u32p, _u8p, _u64p, _u32p, ctypes.c_uint32,
-                ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                 _i32p, _i32p, _i32p, _u32p, _u64p, _u32p, _u32p, _u64p]
             so.oracle_window_dmin.restype = ctypes.c_int
             so.oracle_window_dmin.argtypes = [_u8p, ctypes.c_int, _u8p, ctypes.c_int, ctypes.c_int]
@@ -134,11 +134,23 @@ def cigar_string(runs: np.ndarray) -> str:
     return "".join(f"{int(r) >> 4}{OP_CHARS[int(r) & 15]}" for r in runs)
 
 
+EDGES = "MSID"  # edge kinds of a traceback priority order, codes 0..3
+
+
+def tb_order_code(order: str) -> int:
+    """A traceback priority order ("MSID" = M > S > I > D, the default reading)
+    packed as the C oracle takes it: 2 bits per place, highest priority first."""
+    if sorted(order) != sorted(EDGES):
+        raise ValueError(f"a traceback order is a permutation of {EDGES!r}, got {order!r}")
+    return sum(EDGES.index(e) << (2 * p) for p, e in enumerate(order))
+
+
 def align(batch, W: int = 64, O: int = 24, k: int = 64, variant: str = "unimproved",
-          threads: int = 0, mutant: int | None = None) -> Result:
+          threads: int = 0, mutant: int | None = None, tb_order: str = "MSID") -> Result:
     """Align every pair of a ``datagen.Batch`` (ASCII layout) on host threads.
 
     The oracle packs the ASCII with its own packer, then runs the window driver.
+    ``tb_order`` is the traceback's priority among possible edges.
     """
     reads, bad_r = pack(batch.reads, mutant)
     refs, bad_f = pack(batch.refs, mutant)
@@ -153,7 +165,7 @@ def align(batch, W: int = 64, O: int = 24, k: int = 64, variant: str = "unimprov
     res.threads = lib(mutant).oracle_align_batch(
         _p(reads, _u8p), _p(read_off, _u64p), _p(read_len, _u32p),
         _p(refs, _u8p), _p(ref_off, _u64p), _p(ref_len, _u32p), n,
-        W, O, k, VARIANTS[variant], threads,
+        W, O, k, VARIANTS[variant], tb_order_code(tb_order), threads,
         _p(res.dist, _i32p), _p(res.status, _i32p), _p(res.ref_consumed, _i32p),
         _p(res.cigar, _u32p), _p(res.cigar_off, _u64p), _p(res.n_runs, _u32p),
         _p(res.n_windows, _u32p), _p(res.cells, _u64p))

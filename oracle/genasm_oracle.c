@@ -82,7 +82,8 @@ static uint64_t init_row(int d, int wp) {
 }
 
 int oracle_window_unimproved(const uint8_t* P, int wp, const uint8_t* T, int wt, int last,
-                             int W, int O, int k, oracle_tables* tb, oracle_window_result* res) {
+                             int W, int O, int k, int order, oracle_tables* tb,
+                             oracle_window_result* res) {
   const uint64_t mask = wp_mask(wp);
   uint64_t PM[4];
   for (int c = 0; c < 4; ++c) {
@@ -139,7 +140,9 @@ int oracle_window_unimproved(const uint8_t* P, int wp, const uint8_t* T, int wt,
   if (dmin < 0) return ORACLE_STATUS_EXCEEDS_K;
   res->dmin = dmin;
 
-  /* Traceback from (text 0, whole pattern, d_min), priority M > S > I > D. */
+  /* Traceback from (text 0, whole pattern, d_min): of the edges whose
+   * stored vector has bit j clear, the first one in `order` (the default
+   * reading: M > S > I > D). */
   const int commit = W - O;
   int i = 0, j = wp - 1, d = dmin, cp = 0, ct = 0, n = 0;
 #if GA_ORACLE_MUTANT == 10
@@ -153,21 +156,30 @@ int oracle_window_unimproved(const uint8_t* P, int wp, const uint8_t* T, int wt,
     }
     if (j < 0 || d < 0 || i > wt) return ORACLE_STATUS_TB_STUCK;
     const uint64_t bit = 1ull << j;
+    const unsigned valid = (unsigned)!(tb->Mv[d][i] & bit) << ORACLE_EDGE_M |
+                           (unsigned)!(tb->Sv[d][i] & bit) << ORACLE_EDGE_S |
+                           (unsigned)!(tb->Iv[d][i] & bit) << ORACLE_EDGE_I |
+                           (unsigned)!(tb->Dv[d][i] & bit) << ORACLE_EDGE_D;
     uint8_t op;
-    if (!(tb->Mv[d][i] & bit)) {
-      op = ORACLE_OP_MATCH; ++i; --j; ++cp; ++ct;
-    } else if (!(tb->Sv[d][i] & bit)) {
+    switch (oracle_pick_edge(order, valid)) {
+      case ORACLE_EDGE_M:
+        op = ORACLE_OP_MATCH; ++i; --j; ++cp; ++ct;
+        break;
+      case ORACLE_EDGE_S:
 #if GA_ORACLE_MUTANT == 5
-      op = ORACLE_OP_SUBST; ++i; --j; ++cp; ++ct; /* planted mistake: d not decremented */
+        op = ORACLE_OP_SUBST; ++i; --j; ++cp; ++ct; /* planted mistake: d not decremented */
 #else
-      op = ORACLE_OP_SUBST; ++i; --j; --d; ++cp; ++ct;
+        op = ORACLE_OP_SUBST; ++i; --j; --d; ++cp; ++ct;
 #endif
-    } else if (!(tb->Iv[d][i] & bit)) {
-      op = ORACLE_OP_INS; --j; --d; ++cp;
-    } else if (!(tb->Dv[d][i] & bit)) {
-      op = ORACLE_OP_DEL; ++i; --d; ++ct;
-    } else {
-      return ORACLE_STATUS_TB_STUCK;
+        break;
+      case ORACLE_EDGE_I:
+        op = ORACLE_OP_INS; --j; --d; ++cp;
+        break;
+      case ORACLE_EDGE_D:
+        op = ORACLE_OP_DEL; ++i; --d; ++ct;
+        break;
+      default:
+        return ORACLE_STATUS_TB_STUCK;
     }
     res->ops[n++] = op;
   }
@@ -183,7 +195,7 @@ int oracle_window_dmin(const uint8_t* P, int wp, const uint8_t* T, int wt, int k
   oracle_tables* tb = (oracle_tables*)malloc(sizeof(oracle_tables));
   if (!tb) return -3;
   oracle_window_result res;
-  int st = oracle_window_unimproved(P, wp, T, wt, 1, 64, 0, k, tb, &res);
+  int st = oracle_window_unimproved(P, wp, T, wt, 1, 64, 0, k, ORACLE_ORDER_DEFAULT, tb, &res);
   free(tb);
   return st == ORACLE_STATUS_OK ? res.dmin : -1;
 }
@@ -193,7 +205,7 @@ int oracle_window_dmin(const uint8_t* P, int wp, const uint8_t* T, int wt, int k
 /* ------------------------------------------------------------------------ */
 
 static int align_pair_with(const uint8_t* read, uint32_t m, const uint8_t* ref, uint32_t n,
-                           int W, int O, int k, int variant, oracle_tables* tb,
+                           int W, int O, int k, int variant, int order, oracle_tables* tb,
                            int32_t* dist, int32_t* ref_consumed,
                            uint32_t* cigar, uint32_t cigar_cap, uint32_t* n_runs,
                            uint32_t* n_windows, uint64_t* cells) {
@@ -219,8 +231,9 @@ static int align_pair_with(const uint8_t* read, uint32_t m, const uint8_t* ref, 
     unpack(ref, pos_t, (uint32_t)wt, T);
     oracle_window_result res;
     const int st = variant == ORACLE_IMPROVED
-                       ? oracle_window_improved(P, wp, T, wt, last, W, O, keff, tb, &res)
-                       : oracle_window_unimproved(P, wp, T, wt, last, W, O, keff, tb, &res);
+                       ? oracle_window_improved(P, wp, T, wt, last, W, O, keff, order, tb, &res)
+                       : oracle_window_unimproved(P, wp, T, wt, last, W, O, keff, order, tb,
+                                                  &res);
     if (st != ORACLE_STATUS_OK) {
       if (n_windows) *n_windows = windows;
       return st;
@@ -269,13 +282,13 @@ static int align_pair_with(const uint8_t* read, uint32_t m, const uint8_t* ref, 
 }
 
 int oracle_align_pair(const uint8_t* read, uint32_t m, const uint8_t* ref, uint32_t n,
-                      int W, int O, int k, int variant,
+                      int W, int O, int k, int variant, int order,
                       int32_t* dist, int32_t* ref_consumed,
                       uint32_t* cigar, uint32_t cigar_cap, uint32_t* n_runs,
                       uint32_t* n_windows, uint64_t* cells) {
   oracle_tables* tb = (oracle_tables*)malloc(sizeof(oracle_tables));
   if (!tb) return ORACLE_STATUS_BAD_ARGS;
-  const int st = align_pair_with(read, m, ref, n, W, O, k, variant, tb, dist, ref_consumed,
+  const int st = align_pair_with(read, m, ref, n, W, O, k, variant, order, tb, dist, ref_consumed,
                                  cigar, cigar_cap, n_runs, n_windows, cells);
   free(tb);
   if (st != ORACLE_STATUS_OK) {
@@ -295,7 +308,7 @@ typedef struct {
   const uint64_t *read_off, *ref_off;
   const uint32_t *read_len, *ref_len;
   uint32_t n_pairs;
-  int W, O, k, variant;
+  int W, O, k, variant, order;
   int32_t *dist, *status, *ref_consumed;
   uint32_t* cigar;
   const uint64_t* cigar_off;
@@ -318,7 +331,8 @@ static void* batch_worker(void* arg) {
     const uint64_t ccap = job->cigar_off ? job->cigar_off[p + 1] - cbeg : 0;
     const int st = align_pair_with(job->reads + job->read_off[p], job->read_len[p],
                                    job->refs + job->ref_off[p], job->ref_len[p],
-                                   job->W, job->O, job->k, job->variant, tb, &dist, &rc,
+                                   job->W, job->O, job->k, job->variant, job->order, tb, &dist,
+                                   &rc,
                                    job->cigar ? job->cigar + cbeg : NULL, (uint32_t)ccap, &nr,
                                    &nw, &cells);
     if (st != ORACLE_STATUS_OK) {
@@ -339,8 +353,8 @@ static void* batch_worker(void* arg) {
 
 int oracle_align_batch(const uint8_t* reads, const uint64_t* read_off, const uint32_t* read_len,
                        const uint8_t* refs, const uint64_t* ref_off, const uint32_t* ref_len,
-                       uint32_t n_pairs, int W, int O, int k, int variant, int n_threads,
-                       int32_t* dist, int32_t* status, int32_t* ref_consumed,
+                       uint32_t n_pairs, int W, int O, int k, int variant, int order,
+                       int n_threads, int32_t* dist, int32_t* status, int32_t* ref_consumed,
                        uint32_t* cigar, const uint64_t* cigar_off, uint32_t* n_runs,
                        uint32_t* n_windows, uint64_t* cells) {
   if (n_threads <= 0) {
@@ -348,8 +362,9 @@ int oracle_align_batch(const uint8_t* reads, const uint64_t* read_off, const uin
     n_threads = c > 0 ? (int)c : 1;
   }
   if ((uint32_t)n_threads > n_pairs) n_threads = n_pairs > 0 ? (int)n_pairs : 1;
-  batch_job job = {reads, refs, read_off, ref_off, read_len, ref_len, n_pairs, W, O, k, variant,
-                   dist, status, ref_consumed, cigar, cigar_off, n_runs, n_windows, cells, 0};
+  batch_job job = {reads,  refs,   read_off,     ref_off, read_len, ref_len,  n_pairs,
+                   W,      O,      k,            variant, order,    dist,     status,
+                   ref_consumed, cigar, cigar_off, n_runs, n_windows, cells, 0};
   if (n_threads == 1) {
     batch_worker(&job);
     return 1;

@@ -42,6 +42,15 @@ enum {
   ORACLE_OP_SUBST = 8,
 };
 
+/* Traceback priority orders: when several edges leave a traceback state, the
+ * first possible one of the order is taken. An order packs four edge kinds,
+ * 2 bits each, highest priority in bits 0-1. The paper gives none; the
+ * default reading is M > S > I > D. Any permutation is valid: every edge the
+ * traceback may take leads to a state that still reaches the window's start,
+ * so the last window's edit count equals d_min under every order. */
+enum { ORACLE_EDGE_M = 0, ORACLE_EDGE_S = 1, ORACLE_EDGE_I = 2, ORACLE_EDGE_D = 3 };
+enum { ORACLE_ORDER_DEFAULT = 0xE4 /* M, S, I, D */ };
+
 enum {
   ORACLE_STATUS_OK = 0,
   ORACLE_STATUS_EXCEEDS_K = 1,    /* some window's minimum error count > k */
@@ -56,14 +65,16 @@ enum {
 uint64_t oracle_pack(const uint8_t* ascii, uint64_t n, uint8_t* out);
 
 /* Aligns one pair. `read`/`ref` point at the first byte of each packed
- * sequence. Per-window statistics are optional (NULL to skip):
+ * sequence; `order` is the traceback priority order (ORACLE_ORDER_DEFAULT,
+ * or any permutation packed as above). Per-window statistics are optional
+ * (NULL to skip):
  *   n_windows  - windows processed
  *   cells      - sum over windows of wt * (d_min + 1), the DC entries the
  *                improved algorithm must compute (rows 0..d_min over wt text
  *                columns).
  * Returns the status code. */
 int oracle_align_pair(const uint8_t* read, uint32_t m, const uint8_t* ref, uint32_t n,
-                      int W, int O, int k, int variant,
+                      int W, int O, int k, int variant, int order,
                       int32_t* dist, int32_t* ref_consumed,
                       uint32_t* cigar, uint32_t cigar_cap, uint32_t* n_runs,
                       uint32_t* n_windows, uint64_t* cells);
@@ -75,7 +86,8 @@ int oracle_align_pair(const uint8_t* read, uint32_t m, const uint8_t* ref, uint3
  * Returns the number of threads used. */
 int oracle_align_batch(const uint8_t* reads, const uint64_t* read_off, const uint32_t* read_len,
                        const uint8_t* refs, const uint64_t* ref_off, const uint32_t* ref_len,
-                       uint32_t n_pairs, int W, int O, int k, int variant, int n_threads,
+                       uint32_t n_pairs, int W, int O, int k, int variant, int order,
+                       int n_threads,
                        int32_t* dist, int32_t* status, int32_t* ref_consumed,
                        uint32_t* cigar, const uint64_t* cigar_off, uint32_t* n_runs,
                        uint32_t* n_windows, uint64_t* cells);

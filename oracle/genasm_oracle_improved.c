@@ -24,7 +24,8 @@
 static uint64_t full_mask(int wp) { return wp >= 64 ? ~0ull : ((1ull << wp) - 1ull); }
 
 int oracle_window_improved(const uint8_t* P, int wp, const uint8_t* T, int wt, int last,
-                           int W, int O, int k, oracle_tables* tb, oracle_window_result* res) {
+                           int W, int O, int k, int order, oracle_tables* tb,
+                           oracle_window_result* res) {
   const uint64_t mask = full_mask(wp);
   uint64_t eq[4]; /* eq[c] bit j clear iff pattern char P[wp-1-j] is c */
   for (int c = 0; c < 4; ++c) eq[c] = mask;
@@ -72,17 +73,19 @@ int oracle_window_improved(const uint8_t* P, int wp, const uint8_t* T, int wt, i
 #define STORED(dd, ii) (tb->R[(dd)][(ii)] << lo)
 #define CLEAR(x, b) ((b) < 0 || !(((x) >> (b)) & 1ull))
     const int text_left = i < wt;
+    const int m_ok = text_left && P[wp - 1 - j] == T[i] && CLEAR(STORED(d, i + 1), j - 1);
+    const int s_ok = d > 0 && text_left && CLEAR(STORED(d - 1, i + 1), j - 1);
+    const int i_ok = d > 0 && CLEAR(STORED(d - 1, i), j - 1);
+    const int d_ok = d > 0 && text_left && CLEAR(STORED(d - 1, i + 1), j);
+    const unsigned valid = (unsigned)m_ok << ORACLE_EDGE_M | (unsigned)s_ok << ORACLE_EDGE_S |
+                           (unsigned)i_ok << ORACLE_EDGE_I | (unsigned)d_ok << ORACLE_EDGE_D;
     uint8_t op;
-    if (text_left && P[wp - 1 - j] == T[i] && CLEAR(STORED(d, i + 1), j - 1)) {
-      op = ORACLE_OP_MATCH; ++i; --j; ++cp; ++ct;
-    } else if (d > 0 && text_left && CLEAR(STORED(d - 1, i + 1), j - 1)) {
-      op = ORACLE_OP_SUBST; ++i; --j; --d; ++cp; ++ct;
-    } else if (d > 0 && CLEAR(STORED(d - 1, i), j - 1)) {
-      op = ORACLE_OP_INS; --j; --d; ++cp;
-    } else if (d > 0 && text_left && CLEAR(STORED(d - 1, i + 1), j)) {
-      op = ORACLE_OP_DEL; ++i; --d; ++ct;
-    } else {
-      return ORACLE_STATUS_TB_STUCK;
+    switch (oracle_pick_edge(order, valid)) {
+      case ORACLE_EDGE_M: op = ORACLE_OP_MATCH; ++i; --j; ++cp; ++ct; break;
+      case ORACLE_EDGE_S: op = ORACLE_OP_SUBST; ++i; --j; --d; ++cp; ++ct; break;
+      case ORACLE_EDGE_I: op = ORACLE_OP_INS; --j; --d; ++cp; break;
+      case ORACLE_EDGE_D: op = ORACLE_OP_DEL; ++i; --d; ++ct; break;
+      default: return ORACLE_STATUS_TB_STUCK;
     }
 #undef STORED
 #undef CLEAR

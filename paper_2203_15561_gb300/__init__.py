@@ -102,6 +102,8 @@ def lib():
             so.ga_align_batch_tuned.argtypes = _ALIGN_ARGS + [_vp, _sz, ctypes.POINTER(ga_tuning), _vp]
             so.ga_align_plain.restype = _i
             so.ga_align_plain.argtypes = _ALIGN_ARGS + [_vp]
+            so.ga_align_batch_order.restype = _i
+            so.ga_align_batch_order.argtypes = _ALIGN_ARGS + [_i, _vp, _sz, _vp]
             so.ga_ablation_workspace_size.restype = _i
             so.ga_ablation_workspace_size.argtypes = [_u32, _i, _i, _i, _i, ctypes.POINTER(_sz)]
             so.ga_align_ablation.restype = _i
@@ -218,6 +220,29 @@ def ga_align_plain(d_reads, d_read_off, d_read_len, d_refs, d_ref_off, d_ref_len
                     d_dist, d_status, d_ref_consumed, d_cigar, d_cigar_off, d_n_runs, d_n_windows,
                     d_cells)
     return _check(lib().ga_align_plain(*a, _stream(stream)), "ga_align_plain")
+
+
+GA_TB_ORDER_DEFAULT = 0xE4
+TB_EDGES = "MSID"  # edge kinds of a traceback priority order, codes 0..3
+
+
+def tb_order_code(order: str) -> int:
+    """A traceback priority order such as "MSID" (M > S > I > D) packed as the C
+    ABI takes it: 2 bits per place, highest priority in bits 0-1."""
+    if sorted(order) != sorted(TB_EDGES):
+        raise ValueError(f"a traceback order is a permutation of {TB_EDGES!r}, got {order!r}")
+    return sum(TB_EDGES.index(e) << (2 * q) for q, e in enumerate(order))
+
+
+def ga_align_batch_order(d_reads, d_read_off, d_read_len, d_refs, d_ref_off, d_ref_len, n_pairs, W,
+                         O, k, d_dist, d_status, d_ref_consumed, d_cigar, d_cigar_off, d_n_runs,
+                         d_n_windows, d_cells, tb_order: int, d_workspace, ws_bytes,
+                         stream=None) -> int:
+    a = _align_args(d_reads, d_read_off, d_read_len, d_refs, d_ref_off, d_ref_len, n_pairs, W, O, k,
+                    d_dist, d_status, d_ref_consumed, d_cigar, d_cigar_off, d_n_runs, d_n_windows,
+                    d_cells)
+    return _check(lib().ga_align_batch_order(*a, tb_order, _ptr(d_workspace), ws_bytes,
+                                             _stream(stream)), "ga_align_batch_order")
 
 
 def ga_ablation_workspace_size(n_pairs: int, W: int, O: int, k: int, variant: int) -> int:

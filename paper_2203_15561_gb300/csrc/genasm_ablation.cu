@@ -81,8 +81,9 @@ __device__ __forceinline__ void ablation_window(const AlignParams& p, int r, int
   int cp = 0, ct = 0;
   bool unused = false;
   const bool ok =
-      tb_window<G, kFmtWide, V == 0>(r, gbase, trace, wp, wt, dmin, last, commit, ncols, S, 0, pmcol,
-                                     gs->pmb, tab, st.rw, writer, cp, ct, st.edits, unused);
+      tb_window<G, kFmtWide, V == 0>(r, gbase, trace, wp, wt, dmin, last, commit, ncols, S, 0,
+                                     p.tb_table, pmcol, gs->pmb, tab, st.rw, writer, cp, ct,
+                                     st.edits, unused);
   __syncwarp();
   if (ga) {
     if (table_bytes && writer && !exceeds) {

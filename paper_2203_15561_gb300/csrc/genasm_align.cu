@@ -114,8 +114,9 @@ __device__ __forceinline__ void step_window(const AlignParams& p, int r, int gba
   if (__any_sync(kFull, trace && band && !spilled)) {
     int c1 = 0, t1 = 0;
     const bool ok1 = tb_window<G, kFmtBand>(r, gbase, trace && band && !spilled, wp, wt, dmin, last,
-                                            commit, ncols, Sb, p.band_top, pmcol, gs->pmb, tab_smem,
-                                            st.rw, writer, c1, t1, st.edits, over);
+                                            commit, ncols, Sb, p.band_top, p.tb_table, pmcol,
+                                            gs->pmb, tab_smem, st.rw, writer, c1, t1, st.edits,
+                                            over);
     if (band) {
       ok = ok1;
       cp = c1;
@@ -140,8 +141,8 @@ __device__ __forceinline__ void step_window(const AlignParams& p, int r, int gba
   if (__any_sync(kFull, trace && wide && !spilled)) {
     int c2 = 0, t2 = 0;
     const bool ok2 = tb_window<G, kFmtWide>(r, gbase, trace && wide && !spilled, wp, wt, dmin, last,
-                                            commit, ncols, Sw, 0, pmcol, gs->pmb, tab_smem, st.rw,
-                                            writer, c2, t2, st.edits, unused);
+                                            commit, ncols, Sw, 0, p.tb_table, pmcol, gs->pmb,
+                                            tab_smem, st.rw, writer, c2, t2, st.edits, unused);
     if (wide && !spilled) {
       ok = ok2;
       cp = c2;
@@ -152,8 +153,8 @@ __device__ __forceinline__ void step_window(const AlignParams& p, int r, int gba
   if (__any_sync(kFull, global_tb)) {
     int c3 = 0, t3 = 0;
     const bool ok3 = tb_window<G, kFmtWide>(r, gbase, global_tb, wp, wt, dmin, last, commit, ncols,
-                                            Sw, 0, pmcol, gs->pmb, spill, st.rw, writer, c3, t3,
-                                            st.edits, unused);
+                                            Sw, 0, p.tb_table, pmcol, gs->pmb, spill, st.rw, writer,
+                                            c3, t3, st.edits, unused);
     if (global_tb) {
       ok = ok3;
       cp = c3;

@@ -41,6 +41,7 @@ int fill_params(const uint8_t* d_reads, const uint64_t* d_read_off, const uint32
   p->W = W;
   p->O = O;
   p->kmax = k < W ? k : W;
+  p->tb_table = ga::tb_table(ga::kTbOrderDefault);
   p->dist = d_dist;
   p->status = d_status;
   p->ref_consumed = d_ref_consumed;
@@ -159,6 +160,32 @@ int ga_align_batch_tuned(const uint8_t* d_reads, const uint64_t* d_read_off,
   if (n_pairs == 0) return GA_OK;
   ga::BatchPlan plan{};
   rc = resolve(W, O, k, tuning, &plan);
+  if (rc != GA_OK) return rc;
+  const ga::WorkspaceLayout L = ga::workspace_layout(n_pairs, plan);
+  if (!d_workspace || ws_bytes < L.total) return GA_ENOSPC;
+  return cuda_fail(ga::launch_batched(p, plan, d_workspace, reinterpret_cast<cudaStream_t>(stream)));
+}
+
+int ga_align_batch_order(const uint8_t* d_reads, const uint64_t* d_read_off,
+                         const uint32_t* d_read_len, const uint8_t* d_refs,
+                         const uint64_t* d_ref_off, const uint32_t* d_ref_len, uint32_t n_pairs,
+                         int W, int O, int k, int32_t* d_dist, int32_t* d_status,
+                         int32_t* d_ref_consumed, uint32_t* d_cigar, const uint64_t* d_cigar_off,
+                         uint32_t* d_n_runs, uint32_t* d_n_windows, uint64_t* d_cells,
+                         int tb_order, void* d_workspace, size_t ws_bytes, ga_stream_t stream) {
+  // A permutation of the four edge kinds, two bits each.
+  unsigned seen = 0;
+  for (int q = 0; q < 4; ++q) seen |= 1u << ((static_cast<unsigned>(tb_order) >> (2 * q)) & 3u);
+  if (tb_order < 0 || tb_order > 0xFF || seen != 0xFu) return GA_EINVAL;
+  ga::AlignParams p{};
+  int rc = fill_params(d_reads, d_read_off, d_read_len, d_refs, d_ref_off, d_ref_len, n_pairs, W,
+                       O, k, d_dist, d_status, d_ref_consumed, d_cigar, d_cigar_off, d_n_runs,
+                       d_n_windows, d_cells, &p);
+  if (rc != GA_OK) return rc;
+  if (n_pairs == 0) return GA_OK;
+  p.tb_table = ga::tb_table(static_cast<uint32_t>(tb_order));
+  ga::BatchPlan plan{};
+  rc = resolve(W, O, k, nullptr, &plan);
   if (rc != GA_OK) return rc;
   const ga::WorkspaceLayout L = ga::workspace_layout(n_pairs, plan);
   if (!d_workspace || ws_bytes < L.total) return GA_ENOSPC;

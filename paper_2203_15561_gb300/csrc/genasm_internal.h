@@ -19,6 +19,7 @@ struct AlignParams {
   uint32_t n_pairs;
   int W, O, kmax;  // kmax = min(k, W): no window needs rows above W
   int band_top;    // band tables for windows that are not the last (-1: wide only); set by the launchers
+  uint64_t tb_table;  // traceback decision table (tb_table(order) in genasm_window.cuh)
   int32_t* dist;
   int32_t* status;
   int32_t* ref_consumed;

@@ -82,6 +82,7 @@ extern "C" int ga_align_batch_noalloc(const uint8_t* d_reads, const uint64_t* d_
   p.W = W;
   p.O = O;
   p.kmax = k < W ? k : W;
+  p.tb_table = ga::tb_table(ga::kTbOrderDefault);
   p.dist = d_dist;
   p.status = d_status;
   p.ref_consumed = d_ref_consumed;

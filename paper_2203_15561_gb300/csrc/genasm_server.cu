@@ -528,6 +528,7 @@ extern "C" int ga_server_step(ga_server* s, uint32_t* n_active) {
     p.W = s->W;
     p.O = s->O;
     p.kmax = s->k < s->W ? s->k : s->W;
+    p.tb_table = ga::tb_table(ga::kTbOrderDefault);
     p.dist = s->d_dist;
     p.status = s->d_status;
     p.ref_consumed = s->d_ref_consumed;

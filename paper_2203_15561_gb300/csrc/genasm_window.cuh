@@ -578,6 +578,24 @@ struct RunWriter {
 enum : uint32_t { kTbM = 0, kTbS = 1, kTbI = 2, kTbD = 3, kTbStuck = 4 };
 constexpr uint32_t kTbOps = 0xF2187u;
 
+// The priority among possible edges as a decision table: nibble v holds the
+// code taken when the set of possible edges is v (bit c = code c possible),
+// kTbStuck for v = 0. tb_table(order) builds it from an order packed 2 bits
+// per place, highest priority first (0xE4: M > S > I > D).
+__host__ __device__ constexpr uint64_t tb_table(uint32_t order) {
+  uint64_t t = 0;
+  for (uint32_t v = 0; v < 16; ++v) {
+    uint32_t code = kTbStuck;
+    for (int p = 3; p >= 0; --p) {
+      const uint32_t c = (order >> (2 * p)) & 3u;
+      if ((v >> c) & 1u) code = c;
+    }
+    t |= static_cast<uint64_t>(code) << (4 * v);
+  }
+  return t;
+}
+constexpr uint32_t kTbOrderDefault = 0xE4u;
+
 // Step 5. Lane r of a group evaluates the state reached after r further
 // match steps from (i, j, d); the first lane whose state is a stop or whose
 // decision is not a match ends the run. The path then takes the matches and,
@@ -599,8 +617,8 @@ constexpr uint32_t kTbOps = 0xF2187u;
 template <int G, TableFmt kFmt, bool kFour = false>
 __device__ __forceinline__ bool tb_window(int r, int gbase, bool ga, int wp, int wt, int dmin,
                                           bool last, int commit, int ncols, int S, int band_top,
-                                          const uint64_t* pmcol, const uint32_t* pmb,
-                                          const void* tab,
+                                          uint64_t order_table, const uint64_t* pmcol,
+                                          const uint32_t* pmb, const void* tab,
                                           RunWriter& rw, bool writer, int& cp_out, int& ct_out,
                                           uint32_t& edits, bool& over) {
   // The walk is at text column ct and pattern bit wp-1-cp.
@@ -646,10 +664,12 @@ __device__ __forceinline__ bool tb_window(int r, int gbase, bool ga, int wp, int
       // Bit j of (x << 1) is bit j-1 of x, and 0 (active) for j = 0.
       const uint64_t bit = 1ull << (jl > 0 ? jl : 0);
       const uint64_t below = bit >> 1;
+      // Row -1 does not exist: the S, I and D edges need d >= 1 (at j = 0
+      // the shifted-in bit is active, so `none` alone cannot rule them out).
       m_ok = ((pm & bit) | (a & below)) == 0ull;
-      s_ok = (s & below) == 0ull;
-      i_ok = (in & below) == 0ull;
-      d_ok = (s & bit) == 0ull;
+      s_ok = d > 0 && (s & below) == 0ull;
+      i_ok = d > 0 && (in & below) == 0ull;
+      d_ok = d > 0 && (s & bit) == 0ull;
     } else {
       // Band entries: bit j of PM[T[i]], bit j-1 of column i+1, bit j of
       // column i+1 and bit j-1 of column i sit at kb, kb, kb+1 and kb-1.
@@ -661,15 +681,17 @@ __device__ __forceinline__ bool tb_window(int r, int gbase, bool ga, int wp, int
       const uint32_t s = tn[rowm + ic + 1] | none;
       const uint32_t in = tn[rowm + ic] | none;
       m_ok = ((pmv | a) & mk) == 0u;
-      s_ok = (s & mk) == 0u;
-      i_ok = (in & (mk >> 1)) == 0u;
-      d_ok = (s & (mk << 1)) == 0u;
+      s_ok = d > 0 && (s & mk) == 0u;
+      i_ok = d > 0 && (in & (mk >> 1)) == 0u;
+      d_ok = d > 0 && (s & (mk << 1)) == 0u;
     }
-    uint32_t code = m_ok ? kTbM : s_ok ? kTbS : i_ok ? kTbI : d_ok ? kTbD : kTbStuck;
+    uint32_t valid = static_cast<uint32_t>(m_ok) << kTbM | static_cast<uint32_t>(s_ok) << kTbS |
+                     static_cast<uint32_t>(i_ok) << kTbI | static_cast<uint32_t>(d_ok) << kTbD;
     // Text used up (il == wt): only an insertion leaves the column (R_wt[d]
     // bit j is clear iff j < d, so d >= 1 whenever the walk is consistent).
-    code = il == wt ? (d > 0 ? kTbI : kTbStuck) : code;
-    code = il > wt ? kTbStuck : code;
+    valid = il == wt ? (d > 0 ? 1u << kTbI : 0u) : valid;
+    valid = il > wt ? 0u : valid;
+    const uint32_t code = static_cast<uint32_t>(order_table >> (4 * valid)) & 15u;
     const uint32_t ends = group_bits<G>(__ballot_sync(kFull, !run || stop || code != kTbM), gbase);
     const bool ended = ends != 0u;
     const int L = ended ? __ffs(ends) - 1 : G;  // match steps taken this iteration

@@ -96,6 +96,13 @@ class DeviceBatch:
         else:
             ga_align_batch(*self._args(stats), self.workspace, self.ws_bytes, stream)
 
+    def align_order(self, tb_order: str, stats: bool = True, stream=None):
+        """The batched alignment with another traceback priority order ("MSID" is
+        the default M > S > I > D); see ga_align_batch_order."""
+        from . import ga_align_batch_order, tb_order_code
+        ga_align_batch_order(*self._args(stats), tb_order_code(tb_order), self.workspace,
+                             self.ws_bytes, stream)
+
     def ablation(self, variant: int, table_bytes=None, stats: bool = True, stream=None):
         """The alignment by ablation variant 0..3 (see ga_align_ablation) on the
         packed batch; table_bytes: optional int64 tensor of n x 5."""

@@ -256,3 +256,14 @@ def test_graph_step_matches_direct_call():
         assert_same(b, db.results(), ref, "graph")
     assert ga.ga_launch_count() - launches == 2 * 6  # 2 pack + 3 LPT + 1 align per replay
     g.close()
+
+
+@pytest.mark.parametrize("order", ["MSID", "MISD", "MDSI", "DIMS", "SDIM", "IDSM"])
+def test_traceback_orders(order):
+    pairs = edge_pairs(seed=len(order) * 7 + ord(order[0]), n_random=120) + indel_pairs(seed=3, n=20)
+    for b in (datagen.from_pairs(pairs), datagen.make_batch(4, pair_ids=range(500, 540))):
+        ref = oracle.align(b, tb_order=order)
+        db = DeviceBatch(b)
+        db.pack()
+        db.align_order(order)
+        assert_same(b, db.results(), ref, f"order {order}")

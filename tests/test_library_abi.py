@@ -46,6 +46,10 @@ def test_bad_arguments_rejected_before_any_cuda_call():
     assert L.ga_align_ablation(*([None] * 6 + [0, 64, 24, 64] + [None] * 8), 4, None, None, 0,
                                None) == ga.GA_EINVAL          # variant outside 0..3
     assert L.ga_ablation_workspace_size(10, 64, 24, 64, 7, ctypes.byref(sz)) == ga.GA_EINVAL
+    for bad in (0xE5, 0x1E4, -1, 0):   # not a permutation of the four edge kinds
+        assert L.ga_align_batch_order(*([None] * 6 + [0, 64, 24, 64] + [None] * 8), bad, None, 0,
+                                      None) == ga.GA_EINVAL
+    assert ga.tb_order_code("MSID") == ga.GA_TB_ORDER_DEFAULT
     assert L.ga_pack_2bit(None, 16, None, None, None) == ga.GA_EINVAL
     assert L.ga_pack_2bit(None, 0, None, None, None) == ga.GA_OK  # nothing to do
 

@@ -40,10 +40,10 @@ def tiny_lev_free_end(P: str, T: str) -> int:
     return min(prev)
 
 
-def check_pairs(pairs, variant="unimproved", mutant=None, brute=True, k=64):
+def check_pairs(pairs, variant="unimproved", mutant=None, brute=True, k=64, tb_order="MSID"):
     """Return a list of failure descriptions (empty = all pins hold)."""
     b = datagen.from_pairs(pairs)
-    r = oracle.align(b, variant=variant, k=k, mutant=mutant)
+    r = oracle.align(b, variant=variant, k=k, mutant=mutant, tb_order=tb_order)
     fails = []
     for p, (P, T) in enumerate(pairs):
         st = int(r.status[p])
@@ -256,3 +256,63 @@ def test_planted_mistakes_are_caught(mutant):
 def test_no_mutant_in_default_build():
     pairs = random_windows(100, seed=2)
     assert not check_pairs(pairs)
+
+
+# ---- traceback priority orders --------------------------------------------
+
+ALL_ORDERS = ["".join(o) for o in itertools.permutations("MSID")]
+
+
+@pytest.mark.parametrize("order", ALL_ORDERS)
+def test_every_order_single_windows(order):
+    # Under any priority order a last window's traceback costs exactly d_min
+    # (brute force) and its CIGAR rebuilds the read.
+    strings = list(all_strings(3))
+    pairs = [(P, T) for P in strings if P for T in strings] + random_windows(250, seed=21)
+    for variant in ("unimproved", "improved"):
+        fails = check_pairs(pairs, variant=variant, tb_order=order)
+        assert not fails, (order, variant, fails[:5])
+
+
+@pytest.mark.parametrize("order", ALL_ORDERS)
+def test_every_order_improved_equals_unimproved(order):
+    for config, ids in ((2, [0, 5]), (4, range(100, 112)), (1, range(0, 200))):
+        b = datagen.make_batch(config, pair_ids=list(ids))
+        ru = oracle.align(b, variant="unimproved", tb_order=order)
+        ri = oracle.align(b, variant="improved", tb_order=order)
+        assert (ru.status == 0).all() and (ri.status == 0).all()
+        np.testing.assert_array_equal(ru.dist, ri.dist)
+        np.testing.assert_array_equal(ru.ref_consumed, ri.ref_consumed)
+        for q in range(b.n_pairs):
+            np.testing.assert_array_equal(ru.runs(q), ri.runs(q))
+            rb, ed, used, ok = pins.replay(b.read(q), b.ref(q), ru.cigar_str(q))
+            assert rb == b.read(q) and ok and ed == ru.dist[q] and used == ru.ref_consumed[q]
+
+
+def test_order_decides_between_equal_cost_paths():
+    # Read "A" on reference "C" (one window, the last): both a substitution
+    # and an insertion cost 1, a deletion cannot start the path (after it the
+    # remaining "A" would face no text). Read "AC" on "CAC": an insertion of A
+    # then a match of C, or a deletion of C then two matches, both cost 1; a
+    # substitution cannot start it ("C" does not follow at T[1]).
+    b = datagen.from_pairs([("A", "C"), ("AC", "CAC")])
+    expect = {
+        "MSID": [("1X", 1), ("1I1=", 1)],
+        "MISD": [("1I", 0), ("1I1=", 1)],
+        "MDSI": [("1X", 1), ("1D2=", 3)],
+        "DIMS": [("1I", 0), ("1D2=", 3)],
+        "SDIM": [("1X", 1), ("1D2=", 3)],
+    }
+    for order, rows in expect.items():
+        for variant in ("unimproved", "improved"):
+            r = oracle.align(b, variant=variant, tb_order=order)
+            got = [(r.cigar_str(q), int(r.ref_consumed[q])) for q in range(2)]
+            assert got == rows, (order, variant, got)
+            assert list(r.dist) == [1, 1]
+
+
+def test_bad_order_rejected():
+    b = datagen.from_pairs([("A", "C")])
+    for bad in ("MSI", "MSIX", "MMSI"):
+        with pytest.raises(ValueError):
+            oracle.align(b, tb_order=bad)
