@@ -70,29 +70,31 @@ static void unpack(const uint8_t* packed, uint32_t start, uint32_t len, uint8_t*
 /* Plain GenASM window: full k+1 rows, four vectors stored per entry         */
 /* ------------------------------------------------------------------------ */
 
-static uint64_t wp_mask(int wp) { return wp >= 64 ? ~0ull : ((1ull << wp) - 1ull); }
+static oracle_vec wp_mask(int wp) {
+  return wp >= 128 ? ~(oracle_vec)0 : (((oracle_vec)1 << wp) - 1);
+}
 
 /* R_wt[d]: bit j is clear iff j < d. */
-static uint64_t init_row(int d, int wp) {
+static oracle_vec init_row(int d, int wp) {
 #if GA_ORACLE_MUTANT == 3
   d = d + 1; /* planted mistake: off-by-one initial column */
 #endif
   if (d >= wp) return 0;
-  return (~0ull << d) & wp_mask(wp);
+  return (~(oracle_vec)0 << d) & wp_mask(wp);
 }
 
 int oracle_window_unimproved(const uint8_t* P, int wp, const uint8_t* T, int wt, int last,
                              int W, int O, int k, int order, oracle_tables* tb,
                              oracle_window_result* res) {
-  const uint64_t mask = wp_mask(wp);
-  uint64_t PM[4];
+  const oracle_vec mask = wp_mask(wp);
+  oracle_vec PM[4];
   for (int c = 0; c < 4; ++c) {
     PM[c] = mask;
     for (int j = 0; j < wp; ++j) {
 #if GA_ORACLE_MUTANT == 4
-      if (P[wp - 1 - j] != c) PM[c] &= ~(1ull << j); /* planted mistake: inverted mask */
+      if (P[wp - 1 - j] != c) PM[c] &= ~((oracle_vec)1 << j); /* planted mistake: inverted mask */
 #else
-      if (P[wp - 1 - j] == c) PM[c] &= ~(1ull << j);
+      if (P[wp - 1 - j] == c) PM[c] &= ~((oracle_vec)1 << j);
 #endif
     }
   }
@@ -101,8 +103,8 @@ int oracle_window_unimproved(const uint8_t* P, int wp, const uint8_t* T, int wt,
   for (int d = 0; d <= k; ++d) {
     tb->R[d][wt] = init_row(d, wp);
     for (int i = wt - 1; i >= 0; --i) {
-      const uint64_t M = ((tb->R[d][i + 1] << 1) | PM[T[i]]) & mask;
-      uint64_t S = mask, I = mask, D = mask;
+      const oracle_vec M = ((tb->R[d][i + 1] << 1) | PM[T[i]]) & mask;
+      oracle_vec S = mask, I = mask, D = mask;
       if (d > 0) {
         S = (tb->R[d - 1][i + 1] << 1) & mask;
 #if GA_ORACLE_MUTANT == 1
@@ -155,7 +157,7 @@ int oracle_window_unimproved(const uint8_t* P, int wp, const uint8_t* T, int wt,
       break;
     }
     if (j < 0 || d < 0 || i > wt) return ORACLE_STATUS_TB_STUCK;
-    const uint64_t bit = 1ull << j;
+    const oracle_vec bit = (oracle_vec)1 << j;
     const unsigned valid = (unsigned)!(tb->Mv[d][i] & bit) << ORACLE_EDGE_M |
                            (unsigned)!(tb->Sv[d][i] & bit) << ORACLE_EDGE_S |
                            (unsigned)!(tb->Iv[d][i] & bit) << ORACLE_EDGE_I |
@@ -190,12 +192,13 @@ int oracle_window_unimproved(const uint8_t* P, int wp, const uint8_t* T, int wt,
 }
 
 int oracle_window_dmin(const uint8_t* P, int wp, const uint8_t* T, int wt, int k) {
-  if (wp < 1 || wp > 64 || wt < 0 || wt > 64 || k < 0) return -2;
-  if (k > 64) k = 64;
+  if (wp < 1 || wp > ORACLE_MAXW || wt < 0 || wt > ORACLE_MAXW || k < 0) return -2;
+  if (k > ORACLE_MAXW) k = ORACLE_MAXW;
   oracle_tables* tb = (oracle_tables*)malloc(sizeof(oracle_tables));
   if (!tb) return -3;
   oracle_window_result res;
-  int st = oracle_window_unimproved(P, wp, T, wt, 1, 64, 0, k, ORACLE_ORDER_DEFAULT, tb, &res);
+  int st = oracle_window_unimproved(P, wp, T, wt, 1, ORACLE_MAXW, 0, k, ORACLE_ORDER_DEFAULT, tb,
+                                    &res);
   free(tb);
   return st == ORACLE_STATUS_OK ? res.dmin : -1;
 }

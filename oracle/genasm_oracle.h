@@ -93,8 +93,8 @@ int oracle_align_batch(const uint8_t* reads, const uint64_t* read_off, const uin
                        uint32_t* n_windows, uint64_t* cells);
 
 /* One window of DC on its own, for tests that pin the distance calculation:
- * pattern codes P[0..wp), text codes T[0..wt) (one code per byte), wp <= 64,
- * wt <= 64. Returns d_min (the smallest d <= k whose R_0[d] holds the whole
+ * pattern codes P[0..wp), text codes T[0..wt) (one code per byte), wp <= 128,
+ * wt <= 128. Returns d_min (the smallest d <= k whose R_0[d] holds the whole
  * pattern) or -1 if it exceeds k. Uses the unimproved table. */
 int oracle_window_dmin(const uint8_t* P, int wp, const uint8_t* T, int wt, int k);
 

@@ -21,15 +21,17 @@
 #include "genasm_oracle.h"
 #include "genasm_oracle_internal.h"
 
-static uint64_t full_mask(int wp) { return wp >= 64 ? ~0ull : ((1ull << wp) - 1ull); }
+static oracle_vec full_mask(int wp) {
+  return wp >= 128 ? ~(oracle_vec)0 : (((oracle_vec)1 << wp) - 1);
+}
 
 int oracle_window_improved(const uint8_t* P, int wp, const uint8_t* T, int wt, int last,
                            int W, int O, int k, int order, oracle_tables* tb,
                            oracle_window_result* res) {
-  const uint64_t mask = full_mask(wp);
-  uint64_t eq[4]; /* eq[c] bit j clear iff pattern char P[wp-1-j] is c */
+  const oracle_vec mask = full_mask(wp);
+  oracle_vec eq[4]; /* eq[c] bit j clear iff pattern char P[wp-1-j] is c */
   for (int c = 0; c < 4; ++c) eq[c] = mask;
-  for (int j = 0; j < wp; ++j) eq[P[wp - 1 - j]] &= ~(1ull << j);
+  for (int j = 0; j < wp; ++j) eq[P[wp - 1 - j]] &= ~((oracle_vec)1 << j);
 
   /* Stored region (improvement 3). */
   const int commit = W - O;
@@ -37,22 +39,22 @@ int oracle_window_improved(const uint8_t* P, int wp, const uint8_t* T, int wt, i
   const int lo = (last || O == 0) ? 0 : O - 1;
 
   /* Two full-width rows for the recurrence; tb->R holds the stored part. */
-  uint64_t* prev = tb->Mv[0];
-  uint64_t* cur = tb->Mv[1];
+  oracle_vec* prev = tb->Mv[0];
+  oracle_vec* cur = tb->Mv[1];
   int dmin = -1;
   for (int d = 0; d <= k; ++d) {
-    cur[wt] = d >= wp ? 0 : ((~0ull << d) & mask);
+    cur[wt] = d >= wp ? 0 : ((~(oracle_vec)0 << d) & mask);
     for (int i = wt - 1; i >= 0; --i) {
-      uint64_t r = (cur[i + 1] << 1) | eq[T[i]];
+      oracle_vec r = (cur[i + 1] << 1) | eq[T[i]];
       if (d > 0) r &= (prev[i + 1] << 1) & (prev[i] << 1) & prev[i + 1];
       cur[i] = r & mask;
     }
     for (int i = 0; i < ncols; ++i) tb->R[d][i] = cur[i] >> lo;
-    if (!((cur[0] >> (wp - 1)) & 1ull)) { /* improvement 2: solution found */
+    if (!((cur[0] >> (wp - 1)) & 1)) { /* improvement 2: solution found */
       dmin = d;
       break;
     }
-    uint64_t* t = prev;
+    oracle_vec* t = prev;
     prev = cur;
     cur = t;
   }
@@ -71,7 +73,7 @@ int oracle_window_improved(const uint8_t* P, int wp, const uint8_t* T, int wt, i
     /* `clear(x, b)`: bit b of stored entry x is 0 (active); bit -1 is the
      * empty suffix and always active. */
 #define STORED(dd, ii) (tb->R[(dd)][(ii)] << lo)
-#define CLEAR(x, b) ((b) < 0 || !(((x) >> (b)) & 1ull))
+#define CLEAR(x, b) ((b) < 0 || !(((x) >> (b)) & 1))
     const int text_left = i < wt;
     const int m_ok = text_left && P[wp - 1 - j] == T[i] && CLEAR(STORED(d, i + 1), j - 1);
     const int s_ok = d > 0 && text_left && CLEAR(STORED(d - 1, i + 1), j - 1);

@@ -9,7 +9,11 @@
 
 #include "genasm_oracle.h"
 
-#define ORACLE_MAXW 64
+#define ORACLE_MAXW 128
+
+/* One window vector: bit j stands for the pattern suffix starting at
+ * P[wp-1-j]; 128 bits cover windows of up to 128 bases. */
+typedef unsigned __int128 oracle_vec;
 #define ORACLE_MAXROWS (ORACLE_MAXW + 1)
 #define ORACLE_MAXCOLS (ORACLE_MAXW + 1)
 
@@ -24,14 +28,14 @@ typedef struct {
 
 /* Scratch big enough for either implementation (one per host thread). */
 typedef struct {
-  uint64_t R[ORACLE_MAXROWS][ORACLE_MAXCOLS];
-  uint64_t Mv[ORACLE_MAXROWS][ORACLE_MAXCOLS];
-  uint64_t Sv[ORACLE_MAXROWS][ORACLE_MAXCOLS];
-  uint64_t Iv[ORACLE_MAXROWS][ORACLE_MAXCOLS];
-  uint64_t Dv[ORACLE_MAXROWS][ORACLE_MAXCOLS];
+  oracle_vec R[ORACLE_MAXROWS][ORACLE_MAXCOLS];
+  oracle_vec Mv[ORACLE_MAXROWS][ORACLE_MAXCOLS];
+  oracle_vec Sv[ORACLE_MAXROWS][ORACLE_MAXCOLS];
+  oracle_vec Iv[ORACLE_MAXROWS][ORACLE_MAXCOLS];
+  oracle_vec Dv[ORACLE_MAXROWS][ORACLE_MAXCOLS];
 } oracle_tables;
 
-/* P/T hold one 2-bit code per byte; 1 <= wp <= W <= 64, 0 <= wt <= W;
+/* P/T hold one 2-bit code per byte; 1 <= wp <= W <= 128, 0 <= wt <= W;
  * `last` says whether this window reaches the end of the read; 0 <= k <= W;
  * `order` is a traceback priority order (see genasm_oracle.h).
  * Return an ORACLE_STATUS_* code. */

@@ -40,10 +40,12 @@ def tiny_lev_free_end(P: str, T: str) -> int:
     return min(prev)
 
 
-def check_pairs(pairs, variant="unimproved", mutant=None, brute=True, k=64, tb_order="MSID"):
-    """Return a list of failure descriptions (empty = all pins hold)."""
+def check_pairs(pairs, variant="unimproved", mutant=None, brute=True, k=64, tb_order="MSID", W=64,
+                O=24):
+    """Return a list of failure descriptions (empty = all pins hold). The
+    brute-force distance applies to pairs that fit one window (m, n <= W)."""
     b = datagen.from_pairs(pairs)
-    r = oracle.align(b, variant=variant, k=k, mutant=mutant, tb_order=tb_order)
+    r = oracle.align(b, variant=variant, k=k, mutant=mutant, tb_order=tb_order, W=W, O=O)
     fails = []
     for p, (P, T) in enumerate(pairs):
         st = int(r.status[p])
@@ -60,7 +62,7 @@ def check_pairs(pairs, variant="unimproved", mutant=None, brute=True, k=64, tb_o
             fails.append(f"ref_consumed {int(r.ref_consumed[p])} != {used}")
         if not pins.canonical(cig) and P:
             fails.append(f"non-canonical cigar {cig}")
-        if brute and len(P) <= 64 and len(T) <= 64:
+        if brute and len(P) <= W and len(T) <= W:
             bf = tiny_lev_free_end(P, T) if len(P) * len(T) <= 400 else pins.free_end_distance(P.encode(), T.encode())
             if bf != int(r.dist[p]):
                 fails.append(f"dist {int(r.dist[p])} != brute {bf} for {P!r},{T!r}")
@@ -316,3 +318,62 @@ def test_bad_order_rejected():
     for bad in ("MSI", "MSIX", "MMSI"):
         with pytest.raises(ValueError):
             oracle.align(b, tb_order=bad)
+
+
+# ---- windows wider than 64 bases ------------------------------------------
+
+def long_windows(n, seed, lo=65, hi=128):
+    rnd = random.Random(seed)
+    out = []
+    for _ in range(n):
+        m = rnd.randint(lo, hi)
+        P = "".join(rnd.choice("ACGT") for _ in range(m))
+        if rnd.random() < 0.3:
+            T = "".join(rnd.choice("ACGT") for _ in range(rnd.randint(0, hi)))
+        else:
+            T = list(P)
+            for _ in range(rnd.randint(0, 12)):
+                x = rnd.randrange(len(T) + 1)
+                u = rnd.random()
+                if u < 0.33 and x < len(T):
+                    T[x] = rnd.choice("ACGT")
+                elif u < 0.66:
+                    T.insert(x, rnd.choice("ACGT"))
+                elif x < len(T):
+                    del T[x]
+            T = "".join(T)[:hi]
+        out.append((P, T))
+    return out
+
+
+@pytest.mark.parametrize("variant", ["unimproved", "improved"])
+def test_wide_single_windows_brute_force(variant):
+    # One window of up to 128 bases: the distance is the brute-force
+    # start-anchored, free-end edit distance; the CIGAR rebuilds the read.
+    fails = check_pairs(long_windows(120, seed=31), variant=variant, W=128, O=40, k=128)
+    assert not fails, fails[:5]
+
+
+def test_wide_window_dmin_matches_brute_force():
+    rnd = random.Random(5)
+    for _ in range(60):
+        P = np.array([rnd.randrange(4) for _ in range(rnd.randint(65, 128))], dtype=np.uint8)
+        T = np.array([rnd.randrange(4) for _ in range(rnd.randint(0, 128))], dtype=np.uint8)
+        s = lambda a: "".join("ACGT"[x] for x in a)
+        bf = pins.free_end_distance(s(P).encode(), s(T).encode())
+        assert oracle.window_dmin(P, T, k=128) == bf
+
+
+@pytest.mark.parametrize("W,O", [(128, 48), (100, 30), (96, 95), (65, 0)])
+def test_wide_windows_multi_window_pairs(W, O):
+    b = datagen.make_batch(4, pair_ids=list(range(40, 52)))
+    ru = oracle.align(b, W=W, O=O, k=W, variant="unimproved")
+    ri = oracle.align(b, W=W, O=O, k=W, variant="improved")
+    assert (ru.status == 0).all() and (ri.status == 0).all()
+    np.testing.assert_array_equal(ru.dist, ri.dist)
+    np.testing.assert_array_equal(ru.cells, ri.cells)
+    for q in range(b.n_pairs):
+        np.testing.assert_array_equal(ru.runs(q), ri.runs(q))
+        rb, ed, used, ok = pins.replay(b.read(q), b.ref(q), ru.cigar_str(q))
+        assert rb == b.read(q) and ok and ed == ru.dist[q] and used == ru.ref_consumed[q]
+        assert pins.canonical(ru.cigar_str(q))
