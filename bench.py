@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--plain-serve-seconds", type=float, default=1.0,
                     help="seconds of arrivals replayed through the plain per-request launch")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the window-size sweep")
     ap.add_argument("--no-ablation", action="store_true",
                     help="skip the ablation of the paper's three improvements (ga_align_ablation)")
     ap.add_argument("--tuning", default="",
@@ -347,6 +348,10 @@ def run_ours(args):
     if not args.no_ablation and ws == 1:
         ablation = run_ablation(db, dev, align_ms)
 
+    sweep = None
+    if not args.no_sweep and ws == 1:
+        sweep = run_window_sweep(db, dev, ga)
+
     # ---- CPU oracle baseline (rank 0, N = 1 only) ----
     cpu = None
     if not args.no_cpu and rank == 0 and ws == 1:
@@ -376,6 +381,7 @@ def run_ours(args):
             "p99_latency_ms": serving["served"]["p99_ms"] if serving else None,
             "serving": serving,
             "ablation": ablation,
+            "window_sweep": sweep,
             "bit_exact_repeat": same,
             "roofline": roofline,
             "cpu_baseline": cpu,
@@ -501,6 +507,37 @@ def run_serving(args, dev):
     return {"workload": "serving-poisson-2000rps (1-64 workload-4 pairs per request, seed 5, "
                         f"{args.serve_seconds:g} s of arrivals, pool of {pool_n} distinct pairs)",
             "offered_pairs_per_s": offered, "served": served, "plain_per_request": plain}
+
+
+def run_window_sweep(db, dev, ga):
+    """The batched alignment of the same batch at other window sizes W (overlap O = 3W/8, the
+    64/24 ratio; no error cap): W <= 64 on the on-chip kernels, W > 64 on the 128-bit kernel."""
+    import torch
+
+    n = db.n
+    rows = []
+    for Wv in (32, 48, 64, 96, 128):
+        Ov = (3 * Wv) // 8
+        need = ga.ga_workspace_size(n, Wv, Ov, Wv)
+        wsb = torch.empty(max(need, 1), dtype=torch.uint8, device=dev)
+        args = (db.reads, db.read_off, db.read_len, db.refs, db.ref_off, db.ref_len, n, Wv, Ov, Wv,
+                db.dist, db.status, db.ref_consumed, db.cigar, db.cigar_off, db.n_runs, db.n_windows,
+                db.cells, wsb, need)
+        ga.ga_align_batch(*args)  # warm-up, with statistics
+        torch.cuda.synchronize(dev)
+        windows = int(db.n_windows[:n].sum())
+        ok = bool((db.status[:n] == 0).all())
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ga.ga_align_batch(*args)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1)
+        rows.append({"W": Wv, "O": Ov, "k": Wv, "ms": ms, "pairs_per_s": n / (ms * 1e-3),
+                     "windows": windows, "all_ok": ok,
+                     "kernel": "128-bit, tables in the workspace" if Wv > 64 else "on-chip tables"})
+        del wsb
+    return {"workload": "long-10kb-10000pairs (as the headline)", "rows": rows}
 
 
 def run_ablation(db, dev, align_ms):

@@ -69,8 +69,13 @@ typedef struct CUstream_st* ga_stream_t; /* = cudaStream_t; NULL = legacy defaul
 #define GA_OP_MATCH 7 /* '=' */
 #define GA_OP_SUBST 8 /* 'X' */
 
-/* Largest window the kernels support (one 64-bit vector per DP entry). */
-#define GA_MAX_W 64
+/* Largest window: ga_align_batch, _tuned, _order and the workspace sizes
+ * take W <= GA_MAX_W; windows of 65..128 bases run on a kernel with 128-bit
+ * window vectors and tables in the workspace. The other entry points (the
+ * plain kernel, the server, the no-alloc form, the autotuner and graph, the
+ * ablation) keep their tables on chip and take W <= GA_MAX_W_ONCHIP. */
+#define GA_MAX_W 128
+#define GA_MAX_W_ONCHIP 64
 
 /* Library version, e.g. 100 for 0.1.0. */
 int ga_version(void);
@@ -327,7 +332,9 @@ int ga_measure_int_peak(double out[3], ga_stream_t stream);
  * the sum over windows of wt * (d_min + 1), the DP entries of rows 0..d_min.
  * Workspace: d_workspace of ws_bytes >= ga_workspace_size(...); its contents
  * on entry do not matter. Concurrent calls need separate workspaces.
- * Limits: 1 <= W <= 64, 0 <= O < W, k >= 0 (k >= W means no cap).
+ * Limits: 1 <= W <= GA_MAX_W (128), 0 <= O < W, k >= 0 (k >= W means no
+ * cap). Windows wider than GA_MAX_W_ONCHIP (64) run on the 128-bit kernel:
+ * one warp per pair, tables in the workspace, no tuning.
  * Errors: GA_EINVAL, GA_ENOSPC (workspace too small), GA_ECUDA.
  */
 int ga_align_batch(const uint8_t* d_reads, const uint64_t* d_read_off, const uint32_t* d_read_len,
@@ -411,7 +418,7 @@ int ga_align_ablation(const uint8_t* d_reads, const uint64_t* d_read_off,
  * ga_align_plain - the same alignment as ga_align_batch, computed by the
  * plain GPU GenASM form: one pair per thread block, one launch, pairs in
  * index order, no work queue, no tuning, no workspace. Outputs are identical
- * to ga_align_batch's. Errors: GA_EINVAL, GA_ECUDA.
+ * to ga_align_batch's. W <= GA_MAX_W_ONCHIP. Errors: GA_EINVAL, GA_ECUDA.
  */
 int ga_align_plain(const uint8_t* d_reads, const uint64_t* d_read_off, const uint32_t* d_read_len,
                    const uint8_t* d_refs, const uint64_t* d_ref_off, const uint32_t* d_ref_len,

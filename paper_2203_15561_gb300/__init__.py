@@ -38,7 +38,8 @@ GA_OP_MATCH = 7
 GA_OP_SUBST = 8
 OP_CHARS = {GA_OP_INS: "I", GA_OP_DEL: "D", GA_OP_MATCH: "=", GA_OP_SUBST: "X"}
 
-GA_MAX_W = 64
+GA_MAX_W = 128
+GA_MAX_W_ONCHIP = 64
 
 
 class GenasmError(RuntimeError):

@@ -20,6 +20,7 @@ int cuda_fail(cudaError_t e) {
 }
 
 bool bad_wok(int W, int O, int k) { return W < 1 || W > GA_MAX_W || O < 0 || O >= W || k < 0; }
+bool wide_window(int W) { return W > GA_MAX_W_ONCHIP; }
 
 int fill_params(const uint8_t* d_reads, const uint64_t* d_read_off, const uint32_t* d_read_len,
                 const uint8_t* d_refs, const uint64_t* d_ref_off, const uint32_t* d_ref_len,
@@ -74,6 +75,16 @@ int resolve(int W, int O, int k, const ga_tuning* t, ga::BatchPlan* plan) {
   return cuda_fail(e);
 }
 
+int launch_wide_checked(const ga::AlignParams& p, void* d_workspace, size_t ws_bytes,
+                        ga_stream_t stream) {
+  size_t need = 0;
+  const cudaError_t e = ga::wide_workspace_bytes(p.n_pairs, &need);
+  if (e != cudaSuccess) return cuda_fail(e);
+  if (!d_workspace || ws_bytes < need) return GA_ENOSPC;
+  return cuda_fail(
+      ga::launch_wide(p, true, d_workspace, ws_bytes, reinterpret_cast<cudaStream_t>(stream)));
+}
+
 }  // namespace
 
 extern "C" {
@@ -104,6 +115,7 @@ int ga_pack_2bit(const uint8_t* d_ascii, uint64_t n_chars, uint8_t* d_packed,
 
 int ga_workspace_size(uint32_t n_pairs, int W, int O, int k, size_t* bytes_out) {
   if (!bytes_out || bad_wok(W, O, k)) return GA_EINVAL;
+  if (wide_window(W)) return cuda_fail(ga::wide_workspace_bytes(n_pairs, bytes_out));
   ga::BatchPlan plan{};
   const int rc = resolve(W, O, k, nullptr, &plan);
   if (rc != GA_OK) return rc;
@@ -114,6 +126,7 @@ int ga_workspace_size(uint32_t n_pairs, int W, int O, int k, size_t* bytes_out) 
 int ga_workspace_size_tuned(uint32_t n_pairs, int W, int O, int k, const ga_tuning* tuning,
                             size_t* bytes_out) {
   if (!bytes_out || bad_wok(W, O, k)) return GA_EINVAL;
+  if (wide_window(W)) return cuda_fail(ga::wide_workspace_bytes(n_pairs, bytes_out));
   ga::BatchPlan plan{};
   const int rc = resolve(W, O, k, tuning, &plan);
   if (rc != GA_OK) return rc;
@@ -158,6 +171,7 @@ int ga_align_batch_tuned(const uint8_t* d_reads, const uint64_t* d_read_off,
                        d_n_windows, d_cells, &p);
   if (rc != GA_OK) return rc;
   if (n_pairs == 0) return GA_OK;
+  if (wide_window(W)) return launch_wide_checked(p, d_workspace, ws_bytes, stream);
   ga::BatchPlan plan{};
   rc = resolve(W, O, k, tuning, &plan);
   if (rc != GA_OK) return rc;
@@ -184,6 +198,7 @@ int ga_align_batch_order(const uint8_t* d_reads, const uint64_t* d_read_off,
   if (rc != GA_OK) return rc;
   if (n_pairs == 0) return GA_OK;
   p.tb_table = ga::tb_table(static_cast<uint32_t>(tb_order));
+  if (wide_window(W)) return launch_wide_checked(p, d_workspace, ws_bytes, stream);
   ga::BatchPlan plan{};
   rc = resolve(W, O, k, nullptr, &plan);
   if (rc != GA_OK) return rc;
@@ -206,7 +221,8 @@ int ga_align_batch(const uint8_t* d_reads, const uint64_t* d_read_off, const uin
 
 int ga_ablation_workspace_size(uint32_t n_pairs, int W, int O, int k, int variant,
                                size_t* bytes_out) {
-  if (!bytes_out || bad_wok(W, O, k) || variant < 0 || variant > 3) return GA_EINVAL;
+  if (!bytes_out || bad_wok(W, O, k) || wide_window(W) || variant < 0 || variant > 3)
+    return GA_EINVAL;
   return cuda_fail(ga::ablation_workspace_bytes(n_pairs, variant, bytes_out));
 }
 
@@ -218,7 +234,7 @@ int ga_align_ablation(const uint8_t* d_reads, const uint64_t* d_read_off,
                       uint32_t* d_n_windows, uint64_t* d_cells, int variant,
                       uint64_t* d_table_bytes, void* d_workspace, size_t ws_bytes,
                       ga_stream_t stream) {
-  if (variant < 0 || variant > 3) return GA_EINVAL;
+  if (variant < 0 || variant > 3 || wide_window(W)) return GA_EINVAL;
   ga::AlignParams p{};
   const int rc = fill_params(d_reads, d_read_off, d_read_len, d_refs, d_ref_off, d_ref_len,
                              n_pairs, W, O, k, d_dist, d_status, d_ref_consumed, d_cigar,
@@ -245,7 +261,7 @@ int ga_align_plain(const uint8_t* d_reads, const uint64_t* d_read_off, const uin
                              n_pairs, W, O, k, d_dist, d_status, d_ref_consumed, d_cigar,
                              d_cigar_off, d_n_runs, d_n_windows, d_cells, &p);
   if (rc != GA_OK) return rc;
-  if (n_pairs > 0x7fffffffu) return GA_EINVAL;  // one block per pair
+  if (wide_window(W) || n_pairs > 0x7fffffffu) return GA_EINVAL;  // on-chip tables; block per pair
   return cuda_fail(ga::launch_plain(p, reinterpret_cast<cudaStream_t>(stream)));
 }
 

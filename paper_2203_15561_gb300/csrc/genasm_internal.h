@@ -77,6 +77,11 @@ bool step_variant_exists(int G);
 
 WorkspaceLayout workspace_layout(uint32_t n_pairs, const BatchPlan& plan);
 
+// Windows of 65..128 bases (genasm_wide.cu): 128-bit vectors, tables in the
+// workspace, one warp per pair, pairs longest first when lpt is set.
+cudaError_t wide_workspace_bytes(uint32_t n_pairs, size_t* bytes);
+cudaError_t launch_wide(const AlignParams& p, bool lpt, void* ws, size_t ws_bytes, cudaStream_t s);
+
 // Ablation kernels (genasm_ablation.cu): variant 0..3, see ga_align_ablation.
 cudaError_t ablation_workspace_bytes(uint32_t n_pairs, int variant, size_t* bytes);
 cudaError_t launch_ablation(const AlignParams& p, int variant, uint64_t* table_bytes, void* ws,

@@ -66,7 +66,7 @@ extern "C" int ga_align_batch_noalloc(const uint8_t* d_reads, const uint64_t* d_
                                       uint32_t* d_n_runs, uint32_t* d_n_windows,
                                       uint64_t* d_cells, ga_stream_t stream) {
   if (n_pairs > GA_NOALLOC_MAX_PAIRS) return GA_ENOSPC;
-  if (W < 1 || W > GA_MAX_W || O < 0 || O >= W || k < 0) return GA_EINVAL;
+  if (W < 1 || W > GA_MAX_W_ONCHIP || O < 0 || O >= W || k < 0) return GA_EINVAL;
   if (n_pairs == 0) return GA_OK;
   if (!d_reads || !d_read_off || !d_read_len || !d_refs || !d_ref_off || !d_ref_len || !d_dist ||
       !d_status || !d_ref_consumed || !d_cigar || !d_cigar_off || !d_n_runs)

@@ -217,7 +217,7 @@ constexpr uint64_t kListPairs = 1ull << 16;       // pairs harvested per step (a
 }  // namespace
 
 extern "C" int ga_server_create(size_t budget_bytes, int W, int O, int k, ga_server** out) {
-  if (!out || W < 1 || W > GA_MAX_W || O < 0 || O >= W || k < 0) return GA_EINVAL;
+  if (!out || W < 1 || W > GA_MAX_W_ONCHIP || O < 0 || O >= W || k < 0) return GA_EINVAL;
   ga_server* s = new ga_server();
   s->W = W;
   s->O = O;

@@ -63,7 +63,9 @@ void store_tuning(int W, int O, int k, const ga_tuning* t) {
 
 namespace {
 
-int bad_wok(int W, int O, int k) { return W < 1 || W > GA_MAX_W || O < 0 || O >= W || k < 0; }
+int bad_wok(int W, int O, int k) {
+  return W < 1 || W > GA_MAX_W_ONCHIP || O < 0 || O >= W || k < 0;
+}
 
 // Candidate tunings for a workload whose windows keep about `rows` rows.
 std::vector<ga_tuning> candidates(int rows) {

@@ -1,0 +1,306 @@
+// Windows wider than 64 bases (64 < W <= 128).
+//
+// The same window algorithm as the W <= 64 kernels (GenASM DC with row early
+// termination, tables of the AND of the four vectors for the reachable
+// columns, the cooperative traceback), with 128-bit window vectors
+// (unsigned __int128; bit j stands for the pattern suffix starting at
+// P[wp-1-j]). One warp aligns one pair: lane c owns the four text columns
+// [4c, 4c+4) of the DC wavefront and looks c match steps ahead in the
+// traceback. The table of a window (rows 0..d_min, up to 129 x 129 entries
+// of 16 bytes) lives in the warp's area of the workspace; the PM[T[i]]
+// columns (2 KB) in shared memory. Pairs are handed out longest first from
+// a device counter, as in the batched kernel.
+#include <algorithm>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "genasm.h"
+#include "genasm_internal.h"
+#include "genasm_pair.cuh"
+#include "genasm_window.cuh"
+
+namespace ga {
+
+namespace {
+
+using u128 = unsigned __int128;
+
+constexpr int kWW = 128;             // widest window
+constexpr int kWRows = kWW + 1;      // rows 0..128
+constexpr int kWStride = kWW + 2;    // entries per table row (columns 0..wt, even)
+constexpr int kWLanes = 32;          // lanes per pair
+constexpr int kWC = kWW / kWLanes;   // text columns per lane
+constexpr int kWWarps = 4;           // pairs (warps) per block
+constexpr size_t kWTableEntries = static_cast<size_t>(kWRows) * kWStride;
+
+__device__ __forceinline__ u128 shfl_down128(u128 v, int delta) {
+  const uint64_t lo = __shfl_down_sync(kFull, static_cast<uint64_t>(v), delta);
+  const uint64_t hi = __shfl_down_sync(kFull, static_cast<uint64_t>(v >> 64), delta);
+  return (static_cast<u128>(hi) << 64) | lo;
+}
+
+__device__ __forceinline__ bool bit128(u128 v, int b) { return static_cast<bool>((v >> b) & 1u); }
+
+__device__ __forceinline__ void stg128(u128* p, u128 v) {
+  *reinterpret_cast<ulonglong2*>(p) =
+      make_ulonglong2(static_cast<unsigned long long>(v), static_cast<unsigned long long>(v >> 64));
+}
+
+__device__ __forceinline__ u128 ldg128(const u128* p) {
+  const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(p);
+  return (static_cast<u128>(v.y) << 64) | v.x;
+}
+
+// Pattern masks by warp ballots (lane r contributes bit j = r + 32q) and the
+// PM[T[i]] columns i = r + 32q (all ones at i >= wt).
+__device__ __forceinline__ void wide_masks(int r, const uint8_t* read, uint32_t pos_p, int wp,
+                                           const uint8_t* ref, uint32_t pos_t, int wt,
+                                           u128* pmcol) {
+  u128 L = 0, H = 0;
+  uint32_t ct[kWC];
+#pragma unroll
+  for (int q = 0; q < kWC; ++q) {
+    const int j = r + kWLanes * q;
+    const uint32_t cp = j < wp ? base_at(read, pos_p + static_cast<uint32_t>(wp - 1 - j)) : 0u;
+    ct[q] = j < wt ? base_at(ref, pos_t + static_cast<uint32_t>(j)) : 0u;
+    L |= static_cast<u128>(__ballot_sync(kFull, cp & 1u)) << (kWLanes * q);
+    H |= static_cast<u128>(__ballot_sync(kFull, cp >> 1)) << (kWLanes * q);
+  }
+  const u128 pm0 = L | H, pm1 = ~L | H, pm2 = L | ~H, pm3 = ~(L & H);
+#pragma unroll
+  for (int q = 0; q < kWC; ++q) {
+    const int i = r + kWLanes * q;
+    const uint32_t c = ct[q];
+    const u128 v = c == 0 ? pm0 : c == 1 ? pm1 : c == 2 ? pm2 : pm3;
+    pmcol[i] = i < wt ? v : ~static_cast<u128>(0);
+  }
+}
+
+// DC with row early termination (the column-strip wavefront of dc_window):
+// stores rows 0..d_min, columns 0..ncols-1 (and column wt = R_wt[d] when it
+// is column 128) at row stride kWStride. Returns d_min or -1 above kmax.
+__device__ __forceinline__ int wide_dc(int r, int wp, int wt, int kmax, int ncols,
+                                       const u128* pmcol, u128* tab) {
+  constexpr int C = kWC;
+  const int c0 = r * C;
+  u128 pm[C], P[C], PS[C];
+#pragma unroll
+  for (int x = 0; x < C; ++x) {
+    pm[x] = pmcol[c0 + x];
+    P[x] = ~static_cast<u128>(0);
+    PS[x] = ~static_cast<u128>(0);
+  }
+  u128 Pr = ~static_cast<u128>(0), PrS = Pr, leftmost = Pr, initv = Pr;
+  const int n_store = max(0, min(C, ncols - c0));
+  const bool store_end = r == kWLanes - 1 && ncols > kWW;
+  const int t_last = kmax + kWLanes - 1;
+  bool going = wt > 0;
+  int first = -1;  // lane 0: first solved row
+  for (int t = 0; __any_sync(kFull, going); ++t) {
+    const int d = t - (kWLanes - 1 - r);
+    const u128 from_right = shfl_down128(leftmost, 1);
+    const u128 right = r == kWLanes - 1 ? initv : from_right;  // R_{c0+C}[d]
+    const u128 low = d < 0 ? 1u : 0u;  // rows below 0 are all ones
+    u128 X[C];
+#pragma unroll
+    for (int x = 0; x < C; ++x) {
+      const u128 up_r = x == C - 1 ? Pr : P[x + 1];
+      const u128 up_rs = x == C - 1 ? PrS : PS[x + 1];
+      X[x] = up_rs & PS[x] & up_r;
+    }
+    u128 curS = (right << 1) | low;
+    PrS = curS;
+    Pr = right;
+#pragma unroll
+    for (int x = C - 1; x >= 0; --x) {
+      const u128 nv = (curS | pm[x]) & X[x];
+      curS = (nv << 1) | low;
+      P[x] = nv;
+      PS[x] = curS;
+    }
+    leftmost = P[0];
+    initv <<= 1;
+    if (going && d >= 0 && d < kWRows) {
+      u128* row = tab + static_cast<size_t>(d) * kWStride;
+#pragma unroll
+      for (int x = 0; x < C; ++x)
+        if (x < n_store) stg128(row + c0 + x, P[x]);
+      if (store_end) stg128(row + kWW, right);
+    }
+    if (first < 0 && d >= 0 && d <= kmax && !bit128(P[0], wp - 1)) first = d;
+    const bool more = first < 0 && t + 1 <= t_last;
+    const bool any_more = __shfl_sync(kFull, more ? 1u : 0u, 0) != 0u;
+    going = going && any_more;
+  }
+  int found = __shfl_sync(kFull, first, 0);
+  if (wt == 0) found = wp <= kmax ? wp : -1;  // R_0 = R_wt: d_min = wp
+  return found;
+}
+
+// The cooperative traceback of tb_window over 128-bit table entries.
+__device__ __forceinline__ bool wide_tb(int r, bool run, int wp, int wt, int dmin, bool last,
+                                        int commit, int ncols, uint64_t order_table,
+                                        const u128* pmcol, const u128* tab, RunWriter& rw,
+                                        bool writer, int& cp_out, int& ct_out,
+                                        uint32_t& edits) {
+  int d = dmin, cp = 0, ct = 0;
+  bool ok = true;
+  int rowd = run ? dmin * kWStride : 0;
+  const int cmax = ncols >= 2 ? ncols - 2 : 0;
+  while (__any_sync(kFull, run)) {
+    const int lim = last ? wp - cp : min(commit - cp, commit - ct);
+    const bool stop = r >= lim;
+    const int il = ct + r;
+    const int jl = wp - 1 - cp - r;
+    const int ic = min(il, cmax);
+    const int rowm = max(rowd - kWStride, 0);
+    const u128 pm = pmcol[min(il, kWW - 1)];
+    const u128 a = ldg128(tab + rowd + ic + 1);
+    const u128 s = ldg128(tab + rowm + ic + 1);
+    const u128 in = ldg128(tab + rowm + ic);
+    const int jc = jl > 0 ? jl : 0;
+    // Bit j of (x << 1) is bit j-1 of x, and 0 (active) for j = 0.
+    const bool below_active = jc == 0;
+    const bool m_ok = !bit128(pm, jc) && (below_active || !bit128(a, jc - 1));
+    const bool s_ok = d > 0 && (below_active || !bit128(s, jc - 1));
+    const bool i_ok = d > 0 && (below_active || !bit128(in, jc - 1));
+    const bool d_ok = d > 0 && !bit128(s, jc);
+    uint32_t valid = static_cast<uint32_t>(m_ok) << kTbM | static_cast<uint32_t>(s_ok) << kTbS |
+                     static_cast<uint32_t>(i_ok) << kTbI | static_cast<uint32_t>(d_ok) << kTbD;
+    valid = il == wt ? (d > 0 ? 1u << kTbI : 0u) : valid;  // text used up: only insertions
+    valid = il > wt ? 0u : valid;
+    const uint32_t code = static_cast<uint32_t>(order_table >> (4 * valid)) & 15u;
+    const uint32_t ends = __ballot_sync(kFull, !run || stop || code != kTbM);
+    const bool ended = ends != 0u;
+    const int L = ended ? __ffs(ends) - 1 : kWLanes;
+    const uint32_t ecode = __shfl_sync(kFull, code, ended ? L : 0);
+    const bool live = run && ended && L < lim;
+    const bool edit = live && ecode != kTbStuck;
+    ok = ok && !(live && ecode == kTbStuck);
+    rw.append(run, static_cast<uint32_t>(L), edit, (kTbOps >> (4u * ecode)) & 15u, writer);
+    const int Lr = run ? L : 0;
+    const int e = edit ? 1 : 0;
+    d -= e;
+    rowd -= edit ? kWStride : 0;
+    cp += Lr + (e & (ecode != kTbD));
+    ct += Lr + (e & (ecode != kTbI));
+    edits += e;
+    run = run && (!ended || edit);
+  }
+  cp_out = cp;
+  ct_out = ct;
+  return ok;
+}
+
+__device__ __forceinline__ void wide_window(const AlignParams& p, int r, PairState& st,
+                                            u128* pmcol, u128* tab) {
+  const bool writer = r == 0;
+  const int commit = p.W - p.O;
+  const int wp = static_cast<int>(min(static_cast<uint32_t>(p.W), st.m - st.pos_p));
+  const int wt = static_cast<int>(min(static_cast<uint32_t>(p.W), st.n - st.pos_t));
+  const bool last = st.pos_p + static_cast<uint32_t>(wp) == st.m;
+  const int ncols = last ? wt + 1 : min(wt, commit) + 1;
+  wide_masks(r, st.read, st.pos_p, wp, st.ref, st.pos_t, wt, pmcol);
+  __syncwarp();
+  const int dmin = wide_dc(r, wp, wt, p.kmax, ncols, pmcol, tab);
+  __syncwarp();
+  int cp = 0, ct = 0;
+  const bool ok = wide_tb(r, dmin >= 0, wp, wt, dmin, last, commit, ncols, p.tb_table, pmcol, tab,
+                          st.rw, writer, cp, ct, st.edits);
+  __syncwarp();
+  if (dmin < 0) {
+    st.status = kPairExceedsK;
+  } else if (!ok || cp + ct == 0) {
+    st.status = kPairTbStuck;
+  } else if (st.rw.full) {
+    st.status = kPairCigarFull;
+  } else {
+    ++st.windows;
+    st.cells += static_cast<uint64_t>(wt) * static_cast<uint64_t>(dmin + 1);
+    st.pos_p += static_cast<uint32_t>(cp);
+    st.pos_t += static_cast<uint32_t>(ct);
+  }
+  if (st.status != kPairOk || st.pos_p >= st.m) finish_pair(p, st, writer);
+}
+
+struct WideArgs {
+  uint32_t* queue;
+  const uint32_t* order;  // pair order (longest first), or nullptr: index order
+  u128* tables;           // per warp: kWTableEntries entries
+};
+
+__global__ void __launch_bounds__(kWLanes * kWWarps, 1) align_wide_kernel(const AlignParams p,
+                                                                          const WideArgs a) {
+  __shared__ u128 pmcols[kWWarps][kWW];
+  const int r = threadIdx.x & 31;
+  const int w = threadIdx.x >> 5;
+  u128* tab = a.tables + (static_cast<size_t>(blockIdx.x) * kWWarps + w) * kWTableEntries;
+  PairState st;
+  for (;;) {
+    uint32_t idx = 0;
+    if (r == 0) idx = atomicAdd(a.queue, 1u);
+    idx = __shfl_sync(kFull, idx, 0);
+    if (idx >= p.n_pairs) break;
+    begin_pair(p, a.order ? a.order[idx] : idx, st, r == 0);
+    while (st.busy) wide_window(p, r, st, pmcols[w], tab);
+  }
+}
+
+struct WideLayout {
+  size_t queue, hist, order, tables, total;
+};
+
+cudaError_t wide_blocks(int* blocks) {
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, align_wide_kernel,
+                                                      kWLanes * kWWarps, 0);
+  *blocks = per_sm * sms;
+  return e;
+}
+
+WideLayout wide_layout(uint32_t n_pairs, int blocks) {
+  auto up = [](size_t x) { return (x + 255) & ~static_cast<size_t>(255); };
+  WideLayout L{};
+  L.queue = 0;
+  L.hist = up(L.queue + 256);
+  L.order = up(L.hist + sizeof(uint32_t) * kLptBuckets);
+  L.tables = up(L.order + sizeof(uint32_t) * static_cast<size_t>(n_pairs));
+  L.total = up(L.tables + static_cast<size_t>(blocks) * kWWarps * kWTableEntries * sizeof(u128));
+  return L;
+}
+
+}  // namespace
+
+cudaError_t wide_workspace_bytes(uint32_t n_pairs, size_t* bytes) {
+  int blocks = 0;
+  const cudaError_t e = wide_blocks(&blocks);
+  if (e != cudaSuccess) return e;
+  *bytes = wide_layout(n_pairs, blocks).total;
+  return cudaSuccess;
+}
+
+cudaError_t launch_wide(const AlignParams& p, bool lpt, void* ws, size_t ws_bytes,
+                        cudaStream_t s) {
+  if (p.n_pairs == 0) return cudaSuccess;
+  int blocks = 0;
+  cudaError_t e = wide_blocks(&blocks);
+  if (e != cudaSuccess) return e;
+  const WideLayout L = wide_layout(p.n_pairs, blocks);
+  if (ws_bytes < L.total || blocks < 1) return cudaErrorInvalidValue;
+  char* w = static_cast<char*>(ws);
+  uint32_t* hist = reinterpret_cast<uint32_t*>(w + L.hist);
+  uint32_t* order = reinterpret_cast<uint32_t*>(w + L.order);
+  if ((e = cudaMemsetAsync(w, 0, L.order, s)) != cudaSuccess) return e;
+  if (lpt && (e = launch_lpt_order(p.read_len, p.n_pairs, hist, order, s)) != cudaSuccess) return e;
+  const WideArgs a{reinterpret_cast<uint32_t*>(w + L.queue), lpt ? order : nullptr,
+                   reinterpret_cast<u128*>(w + L.tables)};
+  align_wide_kernel<<<blocks, kWLanes * kWWarps, 0, s>>>(p, a);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace ga
