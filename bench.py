@@ -605,7 +605,8 @@ def run_e2e(args, batch, db, dev, stream, ga, barrier, max_over_ranks, sum_over_
     class Slot:
         def __init__(self, d):
             self.db = d
-            self.stream = torch.cuda.Stream(device=dev)
+            self.stream = torch.cuda.Stream(device=dev)      # inputs in, alignment
+            self.stream_out = torch.cuda.Stream(device=dev)  # CIGAR out
             self.graph = d.graph(pack=True)
             self.d_meta = [d.read_off, d.ref_off, d.read_len, d.ref_len, d.cigar_off]
             self.cws = torch.empty(max(cws, 1), dtype=torch.uint8, device=dev)
@@ -616,6 +617,7 @@ def run_e2e(args, batch, db, dev, stream, ga, barrier, max_over_ranks, sum_over_
             self.h_off = torch.empty(n + 1, dtype=torch.int64).pin_memory()
             self.h_out = torch.empty(max(cap, 1), dtype=torch.int32).pin_memory()
             self.ev = torch.cuda.Event()
+            self.ev_out = torch.cuda.Event()
 
     slots = [Slot(db), Slot(DeviceBatch(batch, W=W, O=O, k=K, device=dev))]
     d2h_total = 0
@@ -627,6 +629,7 @@ def run_e2e(args, batch, db, dev, stream, ga, barrier, max_over_ranks, sum_over_
             s.db.ascii_refs.copy_(h_refs, non_blocking=True)
             for d, h in zip(s.d_meta, meta):
                 d.copy_(h, non_blocking=True)
+            s.stream.wait_event(s.ev_out)  # this slot's previous CIGAR read-back is done
             s.graph.launch(s.stream)
             ga.ga_cigar_compact(s.db.cigar, s.db.cigar_off, s.db.n_runs, n, s.d_out, cap, s.d_out_off,
                                 s.cws, cws, s.stream)
@@ -640,8 +643,10 @@ def run_e2e(args, batch, db, dev, stream, ga, barrier, max_over_ranks, sum_over_
         s = slots[k % 2]
         s.ev.synchronize()
         total = int(s.h_off[n])
-        with torch.cuda.stream(s.stream):
+        with torch.cuda.stream(s.stream_out):
+            s.stream_out.wait_event(s.ev)
             s.h_out[:total].copy_(s.d_out[:total], non_blocking=True)
+            s.ev_out.record(s.stream_out)
         d2h_total += 4 * n * 2 + 8 * (n + 1) + 4 * total
 
     def run(steps):
@@ -652,6 +657,7 @@ def run_e2e(args, batch, db, dev, stream, ga, barrier, max_over_ranks, sum_over_
         finish(steps - 1)
         for s in slots:
             s.stream.synchronize()
+            s.stream_out.synchronize()
 
     run(max(2, args.warmup))
     d2h_total = 0
@@ -673,8 +679,9 @@ def run_e2e(args, batch, db, dev, stream, ga, barrier, max_over_ranks, sum_over_
     return {"value": sum_over_ranks(n) * args.steps / dt, "unit": "pairs/s",
             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h_total // args.steps),
             "ms_per_step": 1e3 * dt / args.steps, "compacted_cigar_matches": bool(ok),
-            "pipeline": "two slots (double-buffered device batches, one stream each): the copies "
-                        "of step k overlap the alignment of step k+1"}
+            "pipeline": "two slots (double-buffered device batches; per slot one stream for the "
+                        "inputs and the alignment, one for the CIGAR read-back): the copies of "
+                        "step k overlap the alignment of step k+1"}
 
 
 def main():
