@@ -31,6 +31,10 @@ METRIC = "10kb pairs/s & Gbases/s: batched+served vs plain GPU GenASM, bit-exact
 WORKLOAD = 2
 W, O, K = 64, 24, 64
 OPS_PER_CELL = 6  # 2 funnel shifts + 4 three-input logic ops per 64-bit DP cell
+# Shared memory per traceback step: the three 4-byte band entries the step
+# tests (row d at column i+1, row d-1 at columns i and i+1) and its 4-byte
+# pattern-mask entry.
+SMEM_BYTES_PER_TB_STEP = 16
 
 
 def parse():
@@ -243,6 +247,8 @@ def run_ours(args):
     assert (res.status == 0).all(), "alignment failed on the benchmark workload"
     cells = int(res.cells.sum())
     windows = int(res.n_windows.sum())
+    # Traceback steps: one per CIGAR op (the run lengths of every pair).
+    tb_steps = int(sum(int((res.runs(q) >> 4).sum(dtype=np.uint64)) for q in range(n)))
 
     # ---- batched (the headline): autotuned, alignment replayed from a CUDA graph ----
     if args.tuning:
@@ -322,6 +328,19 @@ def run_ours(args):
                 "peak_lop3": peaks[0] / 1e12, "peak_shf": peaks[1] / 1e12,
                 "algorithmic_ops_per_launch": cells * OPS_PER_CELL, "cells_per_launch": cells,
                 "windows_per_launch": windows, "align_ms": align_ms, "pack_ms": pack_ms}
+    # Shared-memory side (secondary bound): the DC stores rows 0..d_min of the
+    # W-O+1 traceback columns of a window as 4-byte band entries (cells x
+    # (W-O+1)/W entries, exact for the windows with wt = W that are not the
+    # last), and each traceback step reads 16 bytes.
+    smem_peaks = ga.ga_measure_smem_peak()
+    smem_bytes = 4 * cells * (W - O + 1) // W + SMEM_BYTES_PER_TB_STEP * tb_steps
+    smem_achieved = smem_bytes / (align_ms * 1e-3)
+    roofline["smem"] = {"achieved": smem_achieved / 1e9, "peak": smem_peaks[0] / 1e9,
+                        "unit": "GB/s", "frac": smem_achieved / smem_peaks[0],
+                        "algorithmic_bytes_per_launch": smem_bytes, "tb_steps_per_launch": tb_steps,
+                        "peak_store": smem_peaks[1] / 1e9,
+                        "peak_source": "measured on this GPU by ga_measure_smem_peak (16-byte loads, "
+                                       "no bank conflicts, all SMs)"}
     # DRAM bytes per launch from the committed ncu summary, only while the
     # kernel sources are the ones those counters were taken from.
     prof = ROOT / "profiles" / "align_batched_workload2_counters.md"

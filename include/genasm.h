@@ -312,6 +312,18 @@ uint64_t ga_launch_count(void);
 int ga_measure_int_peak(double out[3], ga_stream_t stream);
 
 /*
+ * ga_measure_smem_peak - measures, on the current device, the shared-memory
+ * bandwidth in bytes/s summed over all SMs: out[0] for 16-byte loads, out[1]
+ * for 16-byte stores, each by every thread of 8 blocks of 256 threads per
+ * SM, with no bank conflicts. Runs two synchronous microbenchmarks (a few
+ * tens of milliseconds each) on the given stream. This is the roofline
+ * denominator for the shared-memory side of the alignment (the DC's table
+ * stores and the traceback's reads, improvements (1)-(3) of Sec. I).
+ * Errors: GA_EINVAL for NULL out, GA_ECUDA.
+ */
+int ga_measure_smem_peak(double out[2], ga_stream_t stream);
+
+/*
  * ga_align_batch - align n_pairs (read, reference) pairs (GenASM DC + TB over
  * windows of W bases with overlap O, error cap k), batched: one persistent
  * launch over a device work queue, pairs handed out longest first.

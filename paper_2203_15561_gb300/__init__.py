@@ -97,6 +97,8 @@ def lib():
             so.ga_cigar_compact_workspace_size.argtypes = [_u32, ctypes.POINTER(_sz)]
             so.ga_measure_int_peak.restype = _i
             so.ga_measure_int_peak.argtypes = [ctypes.POINTER(ctypes.c_double), _vp]
+            so.ga_measure_smem_peak.restype = _i
+            so.ga_measure_smem_peak.argtypes = [ctypes.POINTER(ctypes.c_double), _vp]
             so.ga_align_batch.restype = _i
             so.ga_align_batch.argtypes = _ALIGN_ARGS + [_vp, _sz, _vp]
             so.ga_align_batch_tuned.restype = _i
@@ -182,6 +184,13 @@ def ga_measure_int_peak(stream=None) -> tuple[float, float, float]:
     out = (ctypes.c_double * 3)()
     _check(lib().ga_measure_int_peak(out, _stream(stream)), "ga_measure_int_peak")
     return float(out[0]), float(out[1]), float(out[2])
+
+
+def ga_measure_smem_peak(stream=None) -> tuple[float, float]:
+    """(shared-memory load bytes/s, store bytes/s) measured on the current device."""
+    out = (ctypes.c_double * 2)()
+    _check(lib().ga_measure_smem_peak(out, _stream(stream)), "ga_measure_smem_peak")
+    return float(out[0]), float(out[1])
 
 
 def _align_args(d_reads, d_read_off, d_read_len, d_refs, d_ref_off, d_ref_len, n_pairs, W, O, k,

@@ -6,7 +6,9 @@
 // 3-input logic ops ((a|b)&c and a&b&c on each 32-bit half). No datasheet
 // figure is assumed for sm_103a: these microbenchmarks measure the issue rate
 // of exactly those instructions (inline PTX lop3.b32 / shf.l.wrap.b32, many
-// independent chains per thread, full occupancy on every SM).
+// independent chains per thread, full occupancy on every SM). A second
+// microbenchmark measures the shared-memory bandwidth the table stores and
+// traceback reads draw on (16-byte accesses, no bank conflicts).
 #include <atomic>
 #include <cstdint>
 
@@ -121,6 +123,83 @@ cudaError_t measure_int_peak(double out[3], cudaStream_t s) {
   e = time_mode<0>(buf, blocks, iters, s, &out[0]);
   if (e == cudaSuccess) e = time_mode<1>(buf, blocks, iters, s, &out[1]);
   if (e == cudaSuccess) e = time_mode<2>(buf, blocks, iters / 2, s, &out[2]);
+  cudaFree(buf);
+  return e;
+}
+
+constexpr int kSmemRows = 4;  // rows of 256 x 16 bytes per block
+
+// MODE 0: 16-byte shared loads, 1: 16-byte shared stores. A warp's access
+// covers 512 contiguous bytes (four full 128-byte wavefronts); a thread
+// touches kSmemRows addresses 4 KB apart per unrolled step.
+template <int MODE>
+__global__ void __launch_bounds__(256) smem_peak_kernel(uint32_t* out, int iters, uint32_t seed) {
+  extern __shared__ __align__(16) uint4 sm[];
+  const int t = threadIdx.x;
+  for (int r = 0; r < kSmemRows; ++r) sm[r * 256 + t] = make_uint4(t ^ seed, r, seed, t);
+  __syncthreads();
+  const uint32_t base = static_cast<uint32_t>(__cvta_generic_to_shared(sm)) + 16u * t;
+  uint32_t x = seed;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+#pragma unroll
+      for (int r = 0; r < kSmemRows; ++r) {
+        const uint32_t a = base + 4096u * r;
+        if (MODE == 0) {
+          uint32_t v0, v1, v2, v3;
+          asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                       : "=r"(v0), "=r"(v1), "=r"(v2), "=r"(v3) : "r"(a));
+          x ^= lop3_xor(v0, v1, v2) ^ v3;
+        } else {
+          asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};"
+                       ::"r"(a), "r"(x), "r"(x ^ 1u), "r"(x ^ 2u), "r"(x ^ 3u) : "memory");
+          x += 1u;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  out[blockIdx.x * blockDim.x + t] = x ^ sm[t].x;
+}
+
+template <int MODE>
+static cudaError_t time_smem(uint32_t* buf, int blocks, int iters, cudaStream_t s, double* bytes_s) {
+  constexpr size_t kBytes = sizeof(uint4) * 256 * kSmemRows;
+  cudaEvent_t e0, e1;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e != cudaSuccess) return e;
+  if ((e = cudaEventCreate(&e1)) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return e;
+  }
+  smem_peak_kernel<MODE><<<blocks, 256, kBytes, s>>>(buf, iters / 8, 1u);  // warm-up
+  cudaEventRecord(e0, s);
+  smem_peak_kernel<MODE><<<blocks, 256, kBytes, s>>>(buf, iters, 12345u);
+  cudaEventRecord(e1, s);
+  count_launches(2);
+  e = cudaEventSynchronize(e1);
+  float ms = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) return e;
+  *bytes_s = static_cast<double>(blocks) * 256.0 * iters * kUnroll * kSmemRows * 16.0 / (ms * 1e-3);
+  return cudaSuccess;
+}
+
+cudaError_t measure_smem_peak(double out[2], cudaStream_t s) {
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  const int blocks = sms * 8;  // 2048 threads and 128 KB of shared memory per SM
+  uint32_t* buf = nullptr;
+  if ((e = cudaMalloc(&buf, sizeof(uint32_t) * blocks * 256)) != cudaSuccess) return e;
+  const int iters = 2048;
+  e = time_smem<0>(buf, blocks, iters, s, &out[0]);
+  if (e == cudaSuccess) e = time_smem<1>(buf, blocks, iters, s, &out[1]);
   cudaFree(buf);
   return e;
 }

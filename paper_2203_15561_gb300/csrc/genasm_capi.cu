@@ -157,6 +157,11 @@ int ga_measure_int_peak(double out[3], ga_stream_t stream) {
   return cuda_fail(ga::measure_int_peak(out, reinterpret_cast<cudaStream_t>(stream)));
 }
 
+int ga_measure_smem_peak(double out[2], ga_stream_t stream) {
+  if (!out) return GA_EINVAL;
+  return cuda_fail(ga::measure_smem_peak(out, reinterpret_cast<cudaStream_t>(stream)));
+}
+
 int ga_align_batch_tuned(const uint8_t* d_reads, const uint64_t* d_read_off,
                          const uint32_t* d_read_len, const uint8_t* d_refs,
                          const uint64_t* d_ref_off, const uint32_t* d_ref_len, uint32_t n_pairs,

@@ -102,6 +102,7 @@ bool stored_tuning(int W, int O, int k, struct ga_tuning_s* out);
 void store_tuning(int W, int O, int k, const struct ga_tuning_s* t);
 
 cudaError_t measure_int_peak(double out[3], cudaStream_t s);
+cudaError_t measure_smem_peak(double out[2], cudaStream_t s);
 
 size_t compact_workspace_bytes(uint32_t n_pairs);
 cudaError_t launch_compact(const uint32_t* cigar, const uint64_t* cigar_off, const uint32_t* n_runs,

@@ -8,7 +8,7 @@
         selected counters of each captured launch (from
         `ncu -i <report> --page raw --csv`)
     python -m paper_2203_15561_gb300.ncu_summary source-hash
-        hash of the CUDA sources, recorded next to counters so that stale
+        hash of the batched kernel's sources, recorded next to counters so that stale
         counters are recognised
 
 Reads only the files it is given; runs nothing.
@@ -41,6 +41,8 @@ FULL_METRICS = [
     "smsp__sass_inst_executed_op_shared_st.sum",
     "l1tex__data_bank_conflicts_pipe_lsu_mem_shared_op_ld.sum",
     "l1tex__data_bank_conflicts_pipe_lsu_mem_shared_op_st.sum",
+    "l1tex__data_pipe_lsu_wavefronts_mem_shared.sum",
+    "l1tex__data_pipe_lsu_wavefronts_mem_shared.sum.pct_of_peak_sustained_elapsed",
     "smsp__average_warps_issue_stalled_wait_per_issue_active.ratio",
     "smsp__average_warps_issue_stalled_short_scoreboard_per_issue_active.ratio",
     "smsp__average_warps_issue_stalled_branch_resolving_per_issue_active.ratio",
@@ -50,12 +52,17 @@ FULL_METRICS = [
 ]
 
 
+# The translation unit of the batched alignment kernel: the sources its
+# counters depend on.
+KERNEL_SOURCES = [CSRC / "genasm_align.cu", CSRC / "genasm_window.cuh", CSRC / "genasm_pair.cuh",
+                  CSRC / "genasm_internal.h", CSRC.parent.parent / "include" / "genasm.h"]
+
+
 def source_hash() -> str:
     h = hashlib.sha256()
-    for p in sorted(CSRC.glob("*")):
-        if p.suffix in (".cu", ".cuh", ".h"):
-            h.update(p.name.encode())
-            h.update(p.read_bytes())
+    for p in KERNEL_SOURCES:
+        h.update(p.name.encode())
+        h.update(p.read_bytes())
     return h.hexdigest()[:16]
 
 

@@ -51,6 +51,8 @@ def test_bad_arguments_rejected_before_any_cuda_call():
                                       None) == ga.GA_EINVAL
     assert ga.tb_order_code("MSID") == ga.GA_TB_ORDER_DEFAULT
     assert L.ga_pack_2bit(None, 16, None, None, None) == ga.GA_EINVAL
+    assert L.ga_measure_int_peak(None, None) == ga.GA_EINVAL
+    assert L.ga_measure_smem_peak(None, None) == ga.GA_EINVAL
     assert L.ga_pack_2bit(None, 0, None, None, None) == ga.GA_OK  # nothing to do
 
 
