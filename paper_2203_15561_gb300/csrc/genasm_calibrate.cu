@@ -131,7 +131,9 @@ constexpr int kSmemRows = 4;  // rows of 256 x 16 bytes per block
 
 // MODE 0: 16-byte shared loads, 1: 16-byte shared stores. A warp's access
 // covers 512 contiguous bytes (four full 128-byte wavefronts); a thread
-// touches kSmemRows addresses 4 KB apart per unrolled step.
+// touches kSmemRows addresses 4 KB apart per unrolled step. The accesses are
+// volatile: the addresses repeat every iteration, and plain loads of
+// unchanging shared memory may be hoisted out of the loop.
 template <int MODE>
 __global__ void __launch_bounds__(256) smem_peak_kernel(uint32_t* out, int iters, uint32_t seed) {
   extern __shared__ __align__(16) uint4 sm[];
@@ -148,11 +150,11 @@ __global__ void __launch_bounds__(256) smem_peak_kernel(uint32_t* out, int iters
         const uint32_t a = base + 4096u * r;
         if (MODE == 0) {
           uint32_t v0, v1, v2, v3;
-          asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+          asm volatile("ld.volatile.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
                        : "=r"(v0), "=r"(v1), "=r"(v2), "=r"(v3) : "r"(a));
           x ^= lop3_xor(v0, v1, v2) ^ v3;
         } else {
-          asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};"
+          asm volatile("st.volatile.shared.v4.u32 [%0], {%1, %2, %3, %4};"
                        ::"r"(a), "r"(x), "r"(x ^ 1u), "r"(x ^ 2u), "r"(x ^ 3u) : "memory");
           x += 1u;
         }
