@@ -156,13 +156,13 @@ __device__ __forceinline__ bool wide_tb(int r, bool run, int wp, int wt, int dmi
     const int ic = min(il, cmax);
     const int rowm = max(rowd - kWStride, 0);
     const u128 pm = pmcol[min(il, kWW - 1)];
-    const u128 a = ldg128(tab + rowd + ic + 1);
     const u128 s = ldg128(tab + rowm + ic + 1);
     const u128 in = ldg128(tab + rowm + ic);
     const int jc = jl > 0 ? jl : 0;
     // Bit j of (x << 1) is bit j-1 of x, and 0 (active) for j = 0.
     const bool below_active = jc == 0;
-    const bool m_ok = !bit128(pm, jc) && (below_active || !bit128(a, jc - 1));
+    // On the walk's active cells matching bases always allow M (see tb_window).
+    const bool m_ok = !bit128(pm, jc);
     const bool s_ok = d > 0 && (below_active || !bit128(s, jc - 1));
     const bool i_ok = d > 0 && (below_active || !bit128(in, jc - 1));
     const bool d_ok = d > 0 && !bit128(s, jc);

@@ -611,6 +611,12 @@ constexpr uint32_t kTbOrderDefault = 0xE4u;
 // band stops before the iteration that would need it and sets `over`; its
 // caller redoes the window with a wide table.
 //
+// The match edge needs no table entry: the walk only visits active cells,
+// and at an active cell whose bases match, bit j-1 of R_{i+1}[d] is active
+// too (equal leading bases can always be paired at no cost), so M is
+// possible exactly when PM[T[i]] has bit j clear. The S, I and D tests read
+// rows d-1 of columns i+1 and i.
+//
 // kFour walks a plain GenASM four-vector table (see dc_window): at cell (i,
 // d) the edge is M if bit j of M_i[d] is 0 (i < wt), else S, I, D by bit j of
 // S_i[d], I_i[d], D_i[d] (all ones in row 0).
@@ -657,16 +663,13 @@ __device__ __forceinline__ bool tb_window(int r, int gbase, bool ga, int wp, int
       const int jl = wp - 1 - cp - r;
       const uint64_t* tw = static_cast<const uint64_t*>(tab);
       const uint64_t pm = pmcol[min(il, kPmCols - 1)];
-      const uint64_t a = tw[rowd + ic + 1];
-      const uint64_t none = d > 0 ? 0ull : ~0ull;  // row -1 does not exist
-      const uint64_t s = tw[rowm + ic + 1] | none;
-      const uint64_t in = tw[rowm + ic] | none;
+      const uint64_t s = tw[rowm + ic + 1];
+      const uint64_t in = tw[rowm + ic];
       // Bit j of (x << 1) is bit j-1 of x, and 0 (active) for j = 0.
       const uint64_t bit = 1ull << (jl > 0 ? jl : 0);
       const uint64_t below = bit >> 1;
-      // Row -1 does not exist: the S, I and D edges need d >= 1 (at j = 0
-      // the shifted-in bit is active, so `none` alone cannot rule them out).
-      m_ok = ((pm & bit) | (a & below)) == 0ull;
+      // Row -1 does not exist: the S, I and D edges need d >= 1.
+      m_ok = (pm & bit) == 0ull;
       s_ok = d > 0 && (s & below) == 0ull;
       i_ok = d > 0 && (in & below) == 0ull;
       d_ok = d > 0 && (s & bit) == 0ull;
@@ -676,11 +679,9 @@ __device__ __forceinline__ bool tb_window(int r, int gbase, bool ga, int wp, int
       const uint32_t* tn = static_cast<const uint32_t*>(tab);
       const uint32_t pmv = pmb[min(il, kPmCols - 1)];
       const uint32_t mk = 1u << kb;
-      const uint32_t a = tn[rowd + ic + 1];
-      const uint32_t none = d > 0 ? 0u : ~0u;
-      const uint32_t s = tn[rowm + ic + 1] | none;
-      const uint32_t in = tn[rowm + ic] | none;
-      m_ok = ((pmv | a) & mk) == 0u;
+      const uint32_t s = tn[rowm + ic + 1];
+      const uint32_t in = tn[rowm + ic];
+      m_ok = (pmv & mk) == 0u;
       s_ok = d > 0 && (s & mk) == 0u;
       i_ok = d > 0 && (in & (mk >> 1)) == 0u;
       d_ok = d > 0 && (s & (mk << 1)) == 0u;
