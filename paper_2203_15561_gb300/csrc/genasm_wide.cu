@@ -6,10 +6,16 @@
 // (unsigned __int128; bit j stands for the pattern suffix starting at
 // P[wp-1-j]). One warp aligns one pair: lane c owns the four text columns
 // [4c, 4c+4) of the DC wavefront and looks c match steps ahead in the
-// traceback. The table of a window (rows 0..d_min, up to 129 x 129 entries
-// of 16 bytes) lives in the warp's area of the workspace; the PM[T[i]]
-// columns (2 KB) in shared memory. Pairs are handed out longest first from
-// a device counter, as in the batched kernel.
+// traceback. The window tables live in the warp's area of the workspace. A
+// window that is not the last keeps only the 64 bits of each entry around
+// the diagonals its traceback can follow (band entries: bits
+// [wp-1-A-i, wp-A-i+62] of R_i, A = min(39, O-1)) for rows 0..d_min of
+// columns 0..W-O: half the bytes of the full entries, so the tables of all
+// resident warps stay in L2 (in shared memory they would leave room for a
+// third of the warps). A last window and a window whose traceback leaves the
+// band use the full 16-byte entries (rows 0..d_min, up to 129 x 129). The
+// PM[T[i]] columns (2 KB) are in shared memory. Pairs are handed out longest
+// first from a device counter, as in the batched kernel.
 #include <algorithm>
 #include <cstdint>
 
@@ -33,6 +39,12 @@ constexpr int kWLanes = 32;          // lanes per pair
 constexpr int kWC = kWW / kWLanes;   // text columns per lane
 constexpr int kWWarps = 4;           // pairs (warps) per block
 constexpr size_t kWTableEntries = static_cast<size_t>(kWRows) * kWStride;
+constexpr int kWBandTop = 39;        // A, at most O-1
+constexpr int kWBandMinO = 24;       // band tables need O >= 24 (A >= 23)
+
+int wide_band_top(int O) { return O >= kWBandMinO ? std::min(kWBandTop, O - 1) : -1; }
+// Band table row stride (entries): columns 0..W-O, a multiple of a lane's 4.
+int wide_band_stride(int W, int O) { return (W - O + 1 + kWC - 1) / kWC * kWC; }
 
 __device__ __forceinline__ u128 shfl_down128(u128 v, int delta) {
   const uint64_t lo = __shfl_down_sync(kFull, static_cast<uint64_t>(v), delta);
@@ -78,12 +90,21 @@ __device__ __forceinline__ void wide_masks(int r, const uint8_t* read, uint32_t 
 }
 
 // DC with row early termination (the column-strip wavefront of dc_window):
-// stores rows 0..d_min, columns 0..ncols-1 (and column wt = R_wt[d] when it
-// is column 128) at row stride kWStride. Returns d_min or -1 above kmax.
-__device__ __forceinline__ int wide_dc(int r, int wp, int wt, int kmax, int ncols,
-                                       const u128* pmcol, u128* tab) {
+// stores rows 0..d_min below store_rows, columns 0..ncols-1, at row stride S:
+// full entries (kBand false; also column wt = R_wt[d] when it is column 128)
+// or the 64-bit band entries of a window that is not the last (kBand).
+// Returns d_min or -1 above kmax.
+template <bool kBand>
+__device__ __forceinline__ int wide_dc(int r, int wp, int wt, int kmax, int ncols, int S,
+                                       int store_rows, int band_top, const u128* pmcol,
+                                       void* tabv) {
   constexpr int C = kWC;
   const int c0 = r * C;
+  u128* tab = static_cast<u128*>(tabv);
+  uint64_t* btab = static_cast<uint64_t*>(tabv);
+  int band_sh[C];
+#pragma unroll
+  for (int x = 0; x < C; ++x) band_sh[x] = max(wp - 1 - band_top - c0 - x, 0);
   u128 pm[C], P[C], PS[C];
 #pragma unroll
   for (int x = 0; x < C; ++x) {
@@ -121,12 +142,23 @@ __device__ __forceinline__ int wide_dc(int r, int wp, int wt, int kmax, int ncol
     }
     leftmost = P[0];
     initv <<= 1;
-    if (going && d >= 0 && d < kWRows) {
-      u128* row = tab + static_cast<size_t>(d) * kWStride;
+    if (going && d >= 0 && d < store_rows) {
+      if constexpr (kBand) {
+        uint64_t* row = btab + d * S + c0;
+        if (n_store > 0) {
+          uint64_t E[C];
 #pragma unroll
-      for (int x = 0; x < C; ++x)
-        if (x < n_store) stg128(row + c0 + x, P[x]);
-      if (store_end) stg128(row + kWW, right);
+          for (int x = 0; x < C; ++x) E[x] = static_cast<uint64_t>(P[x] >> band_sh[x]);
+          *reinterpret_cast<ulonglong2*>(row) = make_ulonglong2(E[0], E[1]);
+          *reinterpret_cast<ulonglong2*>(row + 2) = make_ulonglong2(E[2], E[3]);
+        }
+      } else {
+        u128* row = tab + static_cast<size_t>(d) * S;
+#pragma unroll
+        for (int x = 0; x < C; ++x)
+          if (x < n_store) stg128(row + c0 + x, P[x]);
+        if (store_end) stg128(row + kWW, right);
+      }
     }
     if (first < 0 && d >= 0 && d <= kmax && !bit128(P[0], wp - 1)) first = d;
     const bool more = first < 0 && t + 1 <= t_last;
@@ -138,34 +170,58 @@ __device__ __forceinline__ int wide_dc(int r, int wp, int wt, int kmax, int ncol
   return found;
 }
 
-// The cooperative traceback of tb_window over 128-bit table entries.
+// The cooperative traceback of tb_window over the full 128-bit entries or
+// (kBand) the 64-bit band entries, where the bits a lane tests sit at k-1, k
+// and k+1, k = A - (cp - ct): a walk whose offset leaves the band stops
+// before the iteration that would need it and sets `over`. In a window that
+// is not the last the walk never reaches j = 0 (it stops W-O bases in).
+template <bool kBand>
 __device__ __forceinline__ bool wide_tb(int r, bool run, int wp, int wt, int dmin, bool last,
-                                        int commit, int ncols, uint64_t order_table,
-                                        const u128* pmcol, const u128* tab, RunWriter& rw,
-                                        bool writer, int& cp_out, int& ct_out,
-                                        uint32_t& edits) {
+                                        int commit, int ncols, int S, int band_top,
+                                        uint64_t order_table, const u128* pmcol, const void* tabv,
+                                        RunWriter& rw, bool writer, int& cp_out, int& ct_out,
+                                        uint32_t& edits, bool& over) {
+  const u128* tab = static_cast<const u128*>(tabv);
+  const uint64_t* btab = static_cast<const uint64_t*>(tabv);
   int d = dmin, cp = 0, ct = 0;
   bool ok = true;
-  int rowd = run ? dmin * kWStride : 0;
+  int rowd = run ? dmin * S : 0;
   const int cmax = ncols >= 2 ? ncols - 2 : 0;
   while (__any_sync(kFull, run)) {
+    int kb = 0;
+    if constexpr (kBand) {
+      kb = band_top - (cp - ct);
+      const bool in_band = static_cast<unsigned>(kb - 1) <= 61u;
+      over = over || (run && !in_band);
+      run = run && in_band;
+      kb = min(max(kb, 1), 62);
+    }
     const int lim = last ? wp - cp : min(commit - cp, commit - ct);
     const bool stop = r >= lim;
     const int il = ct + r;
     const int jl = wp - 1 - cp - r;
     const int ic = min(il, cmax);
-    const int rowm = max(rowd - kWStride, 0);
+    const int rowm = max(rowd - S, 0);
     const u128 pm = pmcol[min(il, kWW - 1)];
-    const u128 s = ldg128(tab + rowm + ic + 1);
-    const u128 in = ldg128(tab + rowm + ic);
     const int jc = jl > 0 ? jl : 0;
-    // Bit j of (x << 1) is bit j-1 of x, and 0 (active) for j = 0.
-    const bool below_active = jc == 0;
     // On the walk's active cells matching bases always allow M (see tb_window).
     const bool m_ok = !bit128(pm, jc);
-    const bool s_ok = d > 0 && (below_active || !bit128(s, jc - 1));
-    const bool i_ok = d > 0 && (below_active || !bit128(in, jc - 1));
-    const bool d_ok = d > 0 && !bit128(s, jc);
+    bool s_ok, i_ok, d_ok;
+    if constexpr (kBand) {
+      const uint64_t s = btab[rowm + ic + 1];
+      const uint64_t in = btab[rowm + ic];
+      s_ok = d > 0 && !((s >> kb) & 1u);
+      i_ok = d > 0 && !((in >> (kb - 1)) & 1u);
+      d_ok = d > 0 && !((s >> (kb + 1)) & 1u);
+    } else {
+      const u128 s = ldg128(tab + rowm + ic + 1);
+      const u128 in = ldg128(tab + rowm + ic);
+      // Bit j of (x << 1) is bit j-1 of x, and 0 (active) for j = 0.
+      const bool below_active = jc == 0;
+      s_ok = d > 0 && (below_active || !bit128(s, jc - 1));
+      i_ok = d > 0 && (below_active || !bit128(in, jc - 1));
+      d_ok = d > 0 && !bit128(s, jc);
+    }
     uint32_t valid = static_cast<uint32_t>(m_ok) << kTbM | static_cast<uint32_t>(s_ok) << kTbS |
                      static_cast<uint32_t>(i_ok) << kTbI | static_cast<uint32_t>(d_ok) << kTbD;
     valid = il == wt ? (d > 0 ? 1u << kTbI : 0u) : valid;  // text used up: only insertions
@@ -182,7 +238,7 @@ __device__ __forceinline__ bool wide_tb(int r, bool run, int wp, int wt, int dmi
     const int Lr = run ? L : 0;
     const int e = edit ? 1 : 0;
     d -= e;
-    rowd -= edit ? kWStride : 0;
+    rowd -= edit ? S : 0;
     cp += Lr + (e & (ecode != kTbD));
     ct += Lr + (e & (ecode != kTbI));
     edits += e;
@@ -193,8 +249,17 @@ __device__ __forceinline__ bool wide_tb(int r, bool run, int wp, int wt, int dmi
   return ok;
 }
 
-__device__ __forceinline__ void wide_window(const AlignParams& p, int r, PairState& st,
-                                            u128* pmcol, u128* tab) {
+struct WideArgs {
+  uint32_t* queue;
+  const uint32_t* order;  // pair order (longest first), or nullptr: index order
+  u128* tables;           // per warp: kWTableEntries entries (full or band)
+  int band_top;           // A, or -1: no band tables
+  int band_stride;        // band table row stride (entries)
+};
+
+__device__ __forceinline__ void wide_window(const AlignParams& p, const WideArgs& a, int r,
+                                            PairState& st, u128* pmcol, uint64_t* band,
+                                            u128* tab) {
   const bool writer = r == 0;
   const int commit = p.W - p.O;
   const int wp = static_cast<int>(min(static_cast<uint32_t>(p.W), st.m - st.pos_p));
@@ -203,12 +268,38 @@ __device__ __forceinline__ void wide_window(const AlignParams& p, int r, PairSta
   const int ncols = last ? wt + 1 : min(wt, commit) + 1;
   wide_masks(r, st.read, st.pos_p, wp, st.ref, st.pos_t, wt, pmcol);
   __syncwarp();
-  const int dmin = wide_dc(r, wp, wt, p.kmax, ncols, pmcol, tab);
-  __syncwarp();
-  int cp = 0, ct = 0;
-  const bool ok = wide_tb(r, dmin >= 0, wp, wt, dmin, last, commit, ncols, p.tb_table, pmcol, tab,
-                          st.rw, writer, cp, ct, st.edits);
-  __syncwarp();
+  // The whole warp works on this pair: every branch below is warp-uniform.
+  int dmin = -1, cp = 0, ct = 0;
+  bool ok = true, done = false;
+  if (!last && a.band_top >= 0) {
+    dmin = wide_dc<true>(r, wp, wt, p.kmax, ncols, a.band_stride, kWRows, a.band_top, pmcol, band);
+    __syncwarp();
+    if (dmin < 0) {
+      done = true;  // above the error cap
+    } else {
+      const RunWriter rw0 = st.rw;
+      const uint32_t edits0 = st.edits;
+      bool over = false;
+      ok = wide_tb<true>(r, true, wp, wt, dmin, last, commit, ncols, a.band_stride, a.band_top,
+                         p.tb_table, pmcol, band, st.rw, writer, cp, ct, st.edits, over);
+      __syncwarp();
+      done = !over;
+      if (over) {  // the offset left the band: redo with full entries
+        st.rw = rw0;
+        st.edits = edits0;
+        ok = true;
+        cp = ct = 0;
+      }
+    }
+  }
+  if (!done) {
+    dmin = wide_dc<false>(r, wp, wt, p.kmax, ncols, kWStride, kWRows, 0, pmcol, tab);
+    __syncwarp();
+    bool unused = false;
+    ok = wide_tb<false>(r, dmin >= 0, wp, wt, dmin, last, commit, ncols, kWStride, 0, p.tb_table,
+                        pmcol, tab, st.rw, writer, cp, ct, st.edits, unused);
+    __syncwarp();
+  }
   if (dmin < 0) {
     st.status = kPairExceedsK;
   } else if (!ok || cp + ct == 0) {
@@ -224,18 +315,13 @@ __device__ __forceinline__ void wide_window(const AlignParams& p, int r, PairSta
   if (st.status != kPairOk || st.pos_p >= st.m) finish_pair(p, st, writer);
 }
 
-struct WideArgs {
-  uint32_t* queue;
-  const uint32_t* order;  // pair order (longest first), or nullptr: index order
-  u128* tables;           // per warp: kWTableEntries entries
-};
-
 __global__ void __launch_bounds__(kWLanes * kWWarps, 1) align_wide_kernel(const AlignParams p,
                                                                           const WideArgs a) {
   __shared__ u128 pmcols[kWWarps][kWW];
   const int r = threadIdx.x & 31;
   const int w = threadIdx.x >> 5;
   u128* tab = a.tables + (static_cast<size_t>(blockIdx.x) * kWWarps + w) * kWTableEntries;
+  uint64_t* band = reinterpret_cast<uint64_t*>(tab);  // the same area, as 8-byte entries
   PairState st;
   for (;;) {
     uint32_t idx = 0;
@@ -243,7 +329,7 @@ __global__ void __launch_bounds__(kWLanes * kWWarps, 1) align_wide_kernel(const 
     idx = __shfl_sync(kFull, idx, 0);
     if (idx >= p.n_pairs) break;
     begin_pair(p, a.order ? a.order[idx] : idx, st, r == 0);
-    while (st.busy) wide_window(p, r, st, pmcols[w], tab);
+    while (st.busy) wide_window(p, a, r, st, pmcols[w], band, tab);
   }
 }
 
@@ -291,13 +377,15 @@ cudaError_t launch_wide(const AlignParams& p, bool lpt, void* ws, size_t ws_byte
   if (e != cudaSuccess) return e;
   const WideLayout L = wide_layout(p.n_pairs, blocks);
   if (ws_bytes < L.total || blocks < 1) return cudaErrorInvalidValue;
+
   char* w = static_cast<char*>(ws);
   uint32_t* hist = reinterpret_cast<uint32_t*>(w + L.hist);
   uint32_t* order = reinterpret_cast<uint32_t*>(w + L.order);
   if ((e = cudaMemsetAsync(w, 0, L.order, s)) != cudaSuccess) return e;
   if (lpt && (e = launch_lpt_order(p.read_len, p.n_pairs, hist, order, s)) != cudaSuccess) return e;
   const WideArgs a{reinterpret_cast<uint32_t*>(w + L.queue), lpt ? order : nullptr,
-                   reinterpret_cast<u128*>(w + L.tables)};
+                   reinterpret_cast<u128*>(w + L.tables), wide_band_top(p.O),
+                   wide_band_stride(p.W, p.O)};
   align_wide_kernel<<<blocks, kWLanes * kWWarps, 0, s>>>(p, a);
   count_launches(1);
   return cudaGetLastError();
