@@ -267,3 +267,13 @@ def test_traceback_orders(order):
         db.pack()
         db.align_order(order)
         assert_same(b, db.results(), ref, f"order {order}")
+
+
+def test_readme_example():
+    # The usage example of the repository's README, checked against the oracle.
+    batch = datagen.from_pairs([("ACGTACGTTTGA", "ACGTACCGTTGA"), ("GATTACA", "GATCACA")])
+    db = DeviceBatch(batch, W=64, O=24, k=64)
+    db.run("batched")
+    res = db.results()
+    assert_same(batch, res, oracle.align(batch), "readme")
+    assert res.cigar_str(1) == "3=1X3="
