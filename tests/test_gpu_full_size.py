@@ -65,9 +65,9 @@ def check_all_pairs(db, chunk=4096):
         torch.testing.assert_close(x + ins + dl, db.dist[a:b].to(torch.int64))
 
 
-def sample_against_oracle(batch, db, ids):
+def sample_against_oracle(batch, db, ids, W=64, O=24, k=64):
     sub = batch.subset(ids)
-    ref = oracle.align(sub)
+    ref = oracle.align(sub, W=W, O=O, k=k)
     idx = torch.tensor(ids, dtype=torch.int64, device=db.device)
     dist = db.dist[idx].cpu().numpy()
     rc = db.ref_consumed[idx].cpu().numpy()
@@ -103,3 +103,18 @@ def test_full_workload(config, n_oracle):
     sample_against_oracle(batch, db, ids)
     g.close()
     ga.ga_tuning_set(64, 24, 64, None)
+
+
+def test_full_workload_wide_windows():
+    # Workload 2 at W = 128 (the 128-bit kernel: band tables for windows that are not the
+    # last, full entries for last windows and band overflows): every pair's CIGAR is
+    # consistent with its distance and lengths, and a sample matches the oracle.
+    batch = datagen.make_batch(2, workers=WORKERS)
+    db = DeviceBatch(batch, W=128, O=48, k=128)
+    db.dist.fill_(-9)
+    db.run("batched", stats=True)
+    torch.cuda.synchronize()
+    check_all_pairs(db)
+    rng = np.random.default_rng(128)
+    ids = sorted(set(rng.integers(0, batch.n_pairs, 10).tolist()) | {0, batch.n_pairs - 1})
+    sample_against_oracle(batch, db, ids, W=128, O=48, k=128)
