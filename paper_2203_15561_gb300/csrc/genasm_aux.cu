@@ -1,8 +1,9 @@
 // Input stage of the hot path: ASCII -> 2-bit packer.
 //
 // Each thread turns 16 ASCII bytes (one 16-byte load) into 4 packed bytes
-// (one 4-byte store), so both sides of the copy are fully coalesced; the
-// kernel is bound by HBM bandwidth (1.25 bytes moved per base).
+// (one 4-byte store), two such chunks at a time, so both sides of the copy
+// are fully coalesced; the kernel is bound by HBM bandwidth (1.25 bytes moved
+// per base).
 #include <cstdint>
 
 #include <cuda_runtime.h>
@@ -20,15 +21,23 @@ __device__ __forceinline__ uint32_t code_of(uint32_t c, bool& ok) {
   return ok ? (((c >> 1) ^ (c >> 2)) & 3u) : 0u;
 }
 
+// 0x80 in each zero byte of v, exactly: the low 7 bits of a byte plus 0x7F
+// stay below 0x100, so no carry crosses a byte.
+__device__ __forceinline__ uint32_t zero_bytes(uint32_t v) {
+  return ~(((v & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | v) & 0x80808080u;
+}
+
+// The four bases of a word as one byte (base q at bits 2q), a word at a time:
+// code_of's bits 1-2 with G/T swapped, validity by comparing the lower-cased
+// bytes with a, c, g and t; other bytes code 0 and are counted in `bad`.
 __device__ __forceinline__ uint32_t pack4(uint32_t w, uint32_t& bad) {
-  uint32_t out = 0;
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    bool ok;
-    out |= code_of((w >> (8 * q)) & 0xffu, ok) << (2 * q);
-    bad += ok ? 0u : 1u;
-  }
-  return out;
+  const uint32_t u = w | 0x20202020u;
+  const uint32_t ok = zero_bytes(u ^ 0x61616161u) | zero_bytes(u ^ 0x63636363u) |
+                      zero_bytes(u ^ 0x67676767u) | zero_bytes(u ^ 0x74747474u);
+  bad += 4u - static_cast<uint32_t>(__popc(ok));
+  const uint32_t c = ((w >> 1) ^ (w >> 2)) & ((ok >> 7) * 3u);  // 2-bit code per byte
+  const uint32_t t = c | (c >> 6);
+  return (t | (t >> 12)) & 0xffu;
 }
 
 __global__ void pack_kernel(const uint8_t* __restrict__ ascii, uint64_t n, uint8_t* __restrict__ out,
@@ -36,12 +45,22 @@ __global__ void pack_kernel(const uint8_t* __restrict__ ascii, uint64_t n, uint8
   const uint64_t chunks = n / 16;
   uint32_t bad = 0;
   const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+  // Two chunks per iteration: both 16-byte loads are in flight together.
   for (uint64_t q = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; q < chunks;
-       q += stride) {
+       q += 2 * stride) {
+    const bool two = q + stride < chunks;
     const uint4 v = __ldcs(reinterpret_cast<const uint4*>(ascii) + q);
-    const uint32_t b0 = pack4(v.x, bad), b1 = pack4(v.y, bad), b2 = pack4(v.z, bad),
-                   b3 = pack4(v.w, bad);
-    reinterpret_cast<uint32_t*>(out)[q] = b0 | (b1 << 8) | (b2 << 16) | (b3 << 24);
+    const uint4 v2 = two ? __ldcs(reinterpret_cast<const uint4*>(ascii) + q + stride)
+                         : make_uint4(0x41414141u, 0x41414141u, 0x41414141u, 0x41414141u);
+    reinterpret_cast<uint32_t*>(out)[q] = pack4(v.x, bad) | (pack4(v.y, bad) << 8) |
+                                          (pack4(v.z, bad) << 16) | (pack4(v.w, bad) << 24);
+    uint32_t bad2 = 0;
+    const uint32_t p2 = pack4(v2.x, bad2) | (pack4(v2.y, bad2) << 8) | (pack4(v2.z, bad2) << 16) |
+                        (pack4(v2.w, bad2) << 24);
+    if (two) {
+      reinterpret_cast<uint32_t*>(out)[q + stride] = p2;
+      bad += bad2;
+    }
   }
   // Tail (n % 16 bytes): one thread, byte by byte.
   if (blockIdx.x == 0 && threadIdx.x == 0) {

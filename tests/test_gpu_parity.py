@@ -180,8 +180,11 @@ def test_long_workload_samples(config, ids):
 
 def test_pack_matches_oracle():
     rng = np.random.default_rng(0)
-    for n in (0, 1, 3, 4, 15, 16, 17, 1000, 4096 + 7):
-        a = rng.choice(np.frombuffer(b"ACGTacgtNn-", dtype=np.uint8), size=n)
+    for n in (0, 1, 3, 4, 15, 16, 17, 1000, 4096 + 7, 100_003):
+        if n == 100_003:  # every byte value
+            a = rng.integers(0, 256, size=n, dtype=np.uint8)
+        else:
+            a = rng.choice(np.frombuffer(b"ACGTacgtNn-", dtype=np.uint8), size=n)
         want, bad = oracle.pack(a)
         for off in (0, 1):  # aligned and unaligned source
             buf = torch.zeros(n + 16, dtype=torch.uint8, device="cuda")
