@@ -56,10 +56,6 @@ enum : int32_t { kPairOk = 0, kPairExceedsK = 1, kPairCigarFull = 2, kPairTbStuc
 // neighbouring columns with one 16-byte store.
 __host__ __device__ __forceinline__ int table_stride(int ncols) { return (ncols + 1) & ~1; }
 
-__device__ __forceinline__ uint64_t init_row(int d, int wp) {
-  return d >= wp ? 0ull : (~0ull << d);
-}
-
 __device__ __forceinline__ uint32_t base_at(const uint8_t* __restrict__ seq, uint32_t x) {
   return (static_cast<uint32_t>(__ldg(seq + (x >> 2))) >> (2u * (x & 3u))) & 3u;
 }
@@ -527,20 +523,9 @@ struct RunWriter {
   uint32_t op;
   uint32_t len;
   bool full;
-  // Appends `count` (>= 0) copies of op `o` when `take` is set.
-  __device__ __forceinline__ void push(bool take, uint32_t o, uint32_t count, bool writer) {
-    take = take && count > 0;
-    const bool merge = len > 0 && o == op;
-    const bool emit = take && len > 0 && !merge;
-    const bool room = n < cap;
-    stg32_if(emit && room && writer, out + n, (len << 4) | op);
-    n += (emit && room) ? 1u : 0u;
-    full = full || (emit && !room);
-    len = take ? (merge ? len + count : count) : len;
-    op = take ? o : op;
-  }
   // Appends L matches (when take_m) and then, when `edit`, one op `eop`:
-  // the two pushes of a traceback iteration in one step.
+  // the ops of one traceback iteration. A run is emitted when the next op
+  // differs from it.
   __device__ __forceinline__ void append(bool take_m, uint32_t L, bool edit, uint32_t eop,
                                          bool writer) {
     const bool tm = take_m && L > 0;
