@@ -35,6 +35,7 @@ OPS_PER_CELL = 6  # 2 funnel shifts + 4 three-input logic ops per 64-bit DP cell
 # tests (row d at column i+1, row d-1 at columns i and i+1) and its 4-byte
 # pattern-mask entry.
 SMEM_BYTES_PER_TB_STEP = 16
+WORKLOAD_NAME = "long-10kb-10000pairs (10 kb PacBio-like reads, 12% error, 5% flanks, seed 2)"
 
 
 def parse():
@@ -142,7 +143,7 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
         "data": "synthetic",
-        "config": {"workload": "long-10kb-10000pairs (10 kb PacBio-like reads, 12% error, seed 2)",
+        "config": {"workload": WORKLOAD_NAME,
                    "W": W, "O": O, "k": K, "sample_pairs_per_step": per_step},
         "gbases_per_s": bases * args.steps / tot / 1e9,
         "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": threads, "kind": "oracle",
@@ -386,7 +387,7 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": "long-10kb-10000pairs (10 kb PacBio-like reads, 12% error, 5% flanks, seed 2)",
+            "config": {"workload": WORKLOAD_NAME,
                        "W": W, "O": O, "k": K, "pairs_per_gpu": n, "read_bases_per_gpu": read_bases,
                        "kernel": "batched (persistent, LPT work queue, CUDA graph)",
                        ("tuning" if args.tuning else "autotuned"): {"lanes_per_pair": tuned.lanes_per_pair,

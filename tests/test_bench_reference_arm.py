@@ -1,0 +1,28 @@
+"""CPU check of bench.py's reference arm (the CPU oracle timed on the host
+cores): it runs without a GPU and prints one JSON line with the main arm's
+metric, workload and units."""
+import json
+import subprocess
+import sys
+from pathlib import Path
+
+ROOT = Path(__file__).resolve().parent.parent
+
+
+def test_reference_arm_prints_one_json_line():
+    out = subprocess.run([sys.executable, str(ROOT / "bench.py"), "--impl", "reference",
+                          "--steps", "1", "--warmup", "0"],
+                         capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    sys.path.insert(0, str(ROOT))
+    import bench
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC
+    assert d["unit"] == "pairs/s" and d["higher_is_better"] is True and d["value"] > 0
+    assert d["config"]["workload"] == bench.WORKLOAD_NAME
+    assert (d["config"]["W"], d["config"]["O"], d["config"]["k"]) == (bench.W, bench.O, bench.K)
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": "pairs/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
