@@ -342,6 +342,17 @@ def run_ours(args):
                         "peak_store": smem_peaks[1] / 1e9,
                         "peak_source": "measured on this GPU by ga_measure_smem_peak (16-byte loads, "
                                        "no bank conflicts, all SMs)"}
+    # The input stage (HBM bound): the ASCII reads and references in, the 2-bit
+    # packed bases out (1.25 bytes per base), over the event-timed packing.
+    pack_bytes = int(db.ascii_reads.numel() + db.ascii_refs.numel()) * 5 // 4
+    peaks_file = ROOT / "MEASURED_PEAKS.json"
+    hbm_peak = json.loads(peaks_file.read_text())["hbm_gbs"] if peaks_file.exists() else 6800.0
+    roofline["pack"] = {"bound": "hbm", "achieved": pack_bytes / (pack_ms * 1e-3) / 1e9,
+                        "peak": hbm_peak, "unit": "GB/s",
+                        "frac": pack_bytes / (pack_ms * 1e-3) / 1e9 / hbm_peak,
+                        "bytes_per_step": pack_bytes, "kernel": "pack_kernel (2 launches per step)",
+                        "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy)"
+                        if peaks_file.exists() else "fallback 6.8 TB/s"}
     # DRAM bytes per launch from the committed ncu summary, only while the
     # kernel sources are the ones those counters were taken from.
     prof = ROOT / "profiles" / "align_batched_workload2_counters.md"
