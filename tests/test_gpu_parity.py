@@ -82,14 +82,14 @@ def test_window_geometry(W, O):
         assert_same(b, run_gpu(b, kernel, W=W, O=O), ref, f"W{W}O{O}/{kernel}")
 
 
-def band_overflow_windows(batch, ref, W=64, O=24):
+def band_overflow_windows(batch, ref, W=64, O=24, A=None, width=30):
     """Windows (not the last) whose traceback offset (read minus reference
-    bases committed) leaves [A-30, A-1], A = min(22, O-1): the windows the
-    batched kernel must redo with a wide table. Replayed from the oracle's
-    CIGARs with the windowing rule (a window commits until W-O read or
-    reference bases are used; the last window is the one holding the read's
-    end)."""
-    A = min(22, O - 1)
+    bases committed) leaves [A-width, A-1], by default A = min(22, O-1) and
+    width 30 (32-bit band entries): the windows the batched kernel must redo
+    with a wide table. Replayed from the oracle's CIGARs with the windowing
+    rule (a window commits until W-O read or reference bases are used; the
+    last window is the one holding the read's end)."""
+    A = min(22, O - 1) if A is None else A
     commit = W - O
     n = 0
     for q in range(batch.n_pairs):
@@ -103,7 +103,7 @@ def band_overflow_windows(batch, ref, W=64, O=24):
             for _ in range(length):
                 if m - pos_p <= W:  # the last window: no band
                     break
-                out = out or not (A - 30 <= cp - ct <= A - 1)
+                out = out or not (A - width <= cp - ct <= A - 1)
                 cp += op in (7, 8, 1)
                 ct += op in (7, 8, 2)
                 if cp == commit or ct == commit:

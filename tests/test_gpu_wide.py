@@ -4,6 +4,8 @@ windows are pinned by brute force in test_oracle.py.
 """
 from __future__ import annotations
 
+import random
+
 import pytest
 
 import oracle
@@ -17,7 +19,7 @@ if not torch.cuda.is_available():
 
 import paper_2203_15561_gb300 as ga  # noqa: E402
 from paper_2203_15561_gb300.pipeline import DeviceBatch  # noqa: E402
-from test_gpu_parity import assert_same, edge_pairs, indel_pairs  # noqa: E402
+from test_gpu_parity import assert_same, band_overflow_windows, edge_pairs, indel_pairs  # noqa: E402
 from test_oracle import long_windows  # noqa: E402
 
 
@@ -63,3 +65,28 @@ def test_on_chip_entry_points_reject_wide_windows():
         db.align("plain")
     with pytest.raises(ga.GenasmError):
         db.ablation(0)
+
+
+def long_insertion_pairs(seed, n=24):
+    """Reads with one insertion of 30-45 bases inside a window that is not the
+    last: the traceback offset climbs past the top of a 64-bit band."""
+    rnd = random.Random(seed)
+    rs = lambda L: "".join(rnd.choice("ACGT") for _ in range(L))
+    pairs = []
+    for _ in range(n):
+        ref = rs(rnd.choice([600, 900]))
+        at = rnd.randrange(60, len(ref) - 300)
+        pairs.append((ref[:at] + rs(rnd.randint(30, 45)) + ref[at:], ref))
+    return pairs
+
+
+@pytest.mark.parametrize("W,O", [(80, 24), (128, 48)])
+def test_wide_band_overflow_redo(W, O):
+    # Windows whose offset leaves the 64-bit band (A = min(39, O-1), 62
+    # diagonals) are redone with full 16-byte entries.
+    b = datagen.from_pairs(long_insertion_pairs(seed=W))
+    ref = oracle.align(b, W=W, O=O, k=W)
+    assert band_overflow_windows(b, ref, W=W, O=O, A=min(39, O - 1), width=61) >= 3
+    db = DeviceBatch(b, W=W, O=O, k=W)
+    db.run("batched")
+    assert_same(b, db.results(), ref, f"W{W}O{O}/overflow")
