@@ -4,15 +4,16 @@
 // termination, tables of the AND of the four vectors for the reachable
 // columns, the cooperative traceback), with 128-bit window vectors
 // (unsigned __int128; bit j stands for the pattern suffix starting at
-// P[wp-1-j]). One warp aligns one pair: lane c owns the four text columns
-// [4c, 4c+4) of the DC wavefront and looks c match steps ahead in the
-// traceback. The window tables live in the warp's area of the workspace. A
+// P[wp-1-j]). A group of 16 lanes aligns one pair, two groups per warp:
+// lane c owns the eight text columns [8c, 8c+8) of the DC wavefront and
+// looks c match steps ahead in the traceback. The window tables live in the
+// group's area of the workspace. A
 // window that is not the last keeps only the 64 bits of each entry around
 // the diagonals its traceback can follow (band entries: bits
 // [wp-1-A-i, wp-A-i+62] of R_i, A = min(39, O-1)) for rows 0..d_min of
 // columns 0..W-O: half the bytes of the full entries, so the tables of all
 // resident warps stay in L2 (in shared memory they would leave room for a
-// third of the warps). A last window and a window whose traceback leaves the
+// third of the groups). A last window and a window whose traceback leaves the
 // band use the full 16-byte entries (rows 0..d_min, up to 129 x 129). The
 // PM[T[i]] columns (2 KB) are in shared memory. Pairs are handed out longest
 // first from a device counter, as in the batched kernel.
@@ -35,20 +36,23 @@ using u128 = unsigned __int128;
 constexpr int kWW = 128;             // widest window
 constexpr int kWRows = kWW + 1;      // rows 0..128
 constexpr int kWStride = kWW + 2;    // entries per table row (columns 0..wt, even)
-constexpr int kWLanes = 32;          // lanes per pair
-constexpr int kWC = kWW / kWLanes;   // text columns per lane
-constexpr int kWWarps = 4;           // pairs (warps) per block
+constexpr int kWG = 16;              // lanes per pair
+constexpr int kWThreads = 128;       // threads per block (kWThreads / kWG pairs)
 constexpr size_t kWTableEntries = static_cast<size_t>(kWRows) * kWStride;
 constexpr int kWBandTop = 39;        // A, at most O-1
 constexpr int kWBandMinO = 24;       // band tables need O >= 24 (A >= 23)
 
 int wide_band_top(int O) { return O >= kWBandMinO ? std::min(kWBandTop, O - 1) : -1; }
-// Band table row stride (entries): columns 0..W-O, a multiple of a lane's 4.
-int wide_band_stride(int W, int O) { return (W - O + 1 + kWC - 1) / kWC * kWC; }
+// Band table row stride (entries): columns 0..W-O, whole chunks of a lane's columns.
+int wide_band_stride(int W, int O) {
+  constexpr int C = kWW / kWG;
+  return (W - O + 1 + C - 1) / C * C;
+}
 
+template <int G>
 __device__ __forceinline__ u128 shfl_down128(u128 v, int delta) {
-  const uint64_t lo = __shfl_down_sync(kFull, static_cast<uint64_t>(v), delta);
-  const uint64_t hi = __shfl_down_sync(kFull, static_cast<uint64_t>(v >> 64), delta);
+  const uint64_t lo = __shfl_down_sync(kFull, static_cast<uint64_t>(v), delta, G);
+  const uint64_t hi = __shfl_down_sync(kFull, static_cast<uint64_t>(v >> 64), delta, G);
   return (static_cast<u128>(hi) << 64) | lo;
 }
 
@@ -64,41 +68,49 @@ __device__ __forceinline__ u128 ldg128(const u128* p) {
   return (static_cast<u128>(v.y) << 64) | v.x;
 }
 
-// Pattern masks by warp ballots (lane r contributes bit j = r + 32q) and the
-// PM[T[i]] columns i = r + 32q (all ones at i >= wt).
-__device__ __forceinline__ void wide_masks(int r, const uint8_t* read, uint32_t pos_p, int wp,
-                                           const uint8_t* ref, uint32_t pos_t, int wt,
-                                           u128* pmcol) {
+// Pattern masks by ballots within the group (lane r contributes bit j = r + Gq)
+// and the PM[T[i]] columns i = r + Gq (all ones at i >= wt). Groups with ga
+// false take part in the ballots only.
+template <int G>
+__device__ __forceinline__ void wide_masks(bool ga, int r, int gbase, const uint8_t* read,
+                                           uint32_t pos_p, int wp, const uint8_t* ref,
+                                           uint32_t pos_t, int wt, u128* pmcol) {
+  constexpr int Q = kWW / G;
   u128 L = 0, H = 0;
-  uint32_t ct[kWC];
+  uint32_t ct[Q];
 #pragma unroll
-  for (int q = 0; q < kWC; ++q) {
-    const int j = r + kWLanes * q;
-    const uint32_t cp = j < wp ? base_at(read, pos_p + static_cast<uint32_t>(wp - 1 - j)) : 0u;
-    ct[q] = j < wt ? base_at(ref, pos_t + static_cast<uint32_t>(j)) : 0u;
-    L |= static_cast<u128>(__ballot_sync(kFull, cp & 1u)) << (kWLanes * q);
-    H |= static_cast<u128>(__ballot_sync(kFull, cp >> 1)) << (kWLanes * q);
+  for (int q = 0; q < Q; ++q) {
+    const int j = r + G * q;
+    const uint32_t cp =
+        ga && j < wp ? base_at(read, pos_p + static_cast<uint32_t>(wp - 1 - j)) : 0u;
+    ct[q] = ga && j < wt ? base_at(ref, pos_t + static_cast<uint32_t>(j)) : 0u;
+    L |= static_cast<u128>(group_bits<G>(__ballot_sync(kFull, cp & 1u), gbase)) << (G * q);
+    H |= static_cast<u128>(group_bits<G>(__ballot_sync(kFull, cp >> 1), gbase)) << (G * q);
   }
   const u128 pm0 = L | H, pm1 = ~L | H, pm2 = L | ~H, pm3 = ~(L & H);
+  if (ga) {
 #pragma unroll
-  for (int q = 0; q < kWC; ++q) {
-    const int i = r + kWLanes * q;
-    const uint32_t c = ct[q];
-    const u128 v = c == 0 ? pm0 : c == 1 ? pm1 : c == 2 ? pm2 : pm3;
-    pmcol[i] = i < wt ? v : ~static_cast<u128>(0);
+    for (int q = 0; q < Q; ++q) {
+      const int i = r + G * q;
+      const uint32_t c = ct[q];
+      const u128 v = c == 0 ? pm0 : c == 1 ? pm1 : c == 2 ? pm2 : pm3;
+      pmcol[i] = i < wt ? v : ~static_cast<u128>(0);
+    }
   }
 }
 
-// DC with row early termination (the column-strip wavefront of dc_window):
-// stores rows 0..d_min below store_rows, columns 0..ncols-1, at row stride S:
-// full entries (kBand false; also column wt = R_wt[d] when it is column 128)
-// or the 64-bit band entries of a window that is not the last (kBand).
-// Returns d_min or -1 above kmax.
-template <bool kBand>
-__device__ __forceinline__ int wide_dc(int r, int wp, int wt, int kmax, int ncols, int S,
-                                       int store_rows, int band_top, const u128* pmcol,
-                                       void* tabv) {
-  constexpr int C = kWC;
+// DC with row early termination (the column-strip wavefront of dc_window,
+// lane c of the group owning text columns [Cc, Cc+C), C = 128/G): stores rows
+// 0..d_min below store_rows, columns 0..ncols-1, at row stride S: full
+// entries (kBand false; also column wt = R_wt[d] when it is column 128) or
+// the 64-bit band entries of a window that is not the last (kBand). Returns
+// d_min, or -1 above kmax or for a group with ga false (which only takes
+// part in the warp's votes).
+template <int G, bool kBand>
+__device__ __forceinline__ int wide_dc(bool ga, int r, int gbase, int wp, int wt, int kmax,
+                                       int ncols, int S, int store_rows, int band_top,
+                                       const u128* pmcol, void* tabv) {
+  constexpr int C = kWW / G;
   const int c0 = r * C;
   u128* tab = static_cast<u128*>(tabv);
   uint64_t* btab = static_cast<uint64_t*>(tabv);
@@ -108,20 +120,20 @@ __device__ __forceinline__ int wide_dc(int r, int wp, int wt, int kmax, int ncol
   u128 pm[C], P[C], PS[C];
 #pragma unroll
   for (int x = 0; x < C; ++x) {
-    pm[x] = pmcol[c0 + x];
+    pm[x] = ga ? pmcol[c0 + x] : ~static_cast<u128>(0);
     P[x] = ~static_cast<u128>(0);
     PS[x] = ~static_cast<u128>(0);
   }
   u128 Pr = ~static_cast<u128>(0), PrS = Pr, leftmost = Pr, initv = Pr;
   const int n_store = max(0, min(C, ncols - c0));
-  const bool store_end = r == kWLanes - 1 && ncols > kWW;
-  const int t_last = kmax + kWLanes - 1;
-  bool going = wt > 0;
-  int first = -1;  // lane 0: first solved row
+  const bool store_end = r == G - 1 && ncols > kWW;
+  const int t_last = kmax + G - 1;
+  bool going = ga && wt > 0;  // group-uniform
+  int first = -1;             // lane 0: first solved row
   for (int t = 0; __any_sync(kFull, going); ++t) {
-    const int d = t - (kWLanes - 1 - r);
-    const u128 from_right = shfl_down128(leftmost, 1);
-    const u128 right = r == kWLanes - 1 ? initv : from_right;  // R_{c0+C}[d]
+    const int d = t - (G - 1 - r);
+    const u128 from_right = shfl_down128<G>(leftmost, 1);
+    const u128 right = r == G - 1 ? initv : from_right;  // R_{c0+C}[d]
     const u128 low = d < 0 ? 1u : 0u;  // rows below 0 are all ones
     u128 X[C];
 #pragma unroll
@@ -146,11 +158,11 @@ __device__ __forceinline__ int wide_dc(int r, int wp, int wt, int kmax, int ncol
       if constexpr (kBand) {
         uint64_t* row = btab + d * S + c0;
         if (n_store > 0) {
-          uint64_t E[C];
 #pragma unroll
-          for (int x = 0; x < C; ++x) E[x] = static_cast<uint64_t>(P[x] >> band_sh[x]);
-          *reinterpret_cast<ulonglong2*>(row) = make_ulonglong2(E[0], E[1]);
-          *reinterpret_cast<ulonglong2*>(row + 2) = make_ulonglong2(E[2], E[3]);
+          for (int x = 0; x < C; x += 2)
+            *reinterpret_cast<ulonglong2*>(row + x) =
+                make_ulonglong2(static_cast<uint64_t>(P[x] >> band_sh[x]),
+                                static_cast<uint64_t>(P[x + 1] >> band_sh[x + 1]));
         }
       } else {
         u128* row = tab + static_cast<size_t>(d) * S;
@@ -162,12 +174,12 @@ __device__ __forceinline__ int wide_dc(int r, int wp, int wt, int kmax, int ncol
     }
     if (first < 0 && d >= 0 && d <= kmax && !bit128(P[0], wp - 1)) first = d;
     const bool more = first < 0 && t + 1 <= t_last;
-    const bool any_more = __shfl_sync(kFull, more ? 1u : 0u, 0) != 0u;
-    going = going && any_more;
+    const bool group_more = __shfl_sync(kFull, more ? 1u : 0u, gbase) != 0u;
+    going = going && group_more;
   }
-  int found = __shfl_sync(kFull, first, 0);
+  int found = __shfl_sync(kFull, first, gbase);
   if (wt == 0) found = wp <= kmax ? wp : -1;  // R_0 = R_wt: d_min = wp
-  return found;
+  return ga ? found : -1;
 }
 
 // The cooperative traceback of tb_window over the full 128-bit entries or
@@ -175,9 +187,10 @@ __device__ __forceinline__ int wide_dc(int r, int wp, int wt, int kmax, int ncol
 // and k+1, k = A - (cp - ct): a walk whose offset leaves the band stops
 // before the iteration that would need it and sets `over`. In a window that
 // is not the last the walk never reaches j = 0 (it stops W-O bases in).
-template <bool kBand>
-__device__ __forceinline__ bool wide_tb(int r, bool run, int wp, int wt, int dmin, bool last,
-                                        int commit, int ncols, int S, int band_top,
+// Groups with run false only take part in the votes.
+template <int G, bool kBand>
+__device__ __forceinline__ bool wide_tb(bool run, int r, int gbase, int wp, int wt, int dmin,
+                                        bool last, int commit, int ncols, int S, int band_top,
                                         uint64_t order_table, const u128* pmcol, const void* tabv,
                                         RunWriter& rw, bool writer, int& cp_out, int& ct_out,
                                         uint32_t& edits, bool& over) {
@@ -227,10 +240,10 @@ __device__ __forceinline__ bool wide_tb(int r, bool run, int wp, int wt, int dmi
     valid = il == wt ? (d > 0 ? 1u << kTbI : 0u) : valid;  // text used up: only insertions
     valid = il > wt ? 0u : valid;
     const uint32_t code = static_cast<uint32_t>(order_table >> (4 * valid)) & 15u;
-    const uint32_t ends = __ballot_sync(kFull, !run || stop || code != kTbM);
+    const uint32_t ends = group_bits<G>(__ballot_sync(kFull, !run || stop || code != kTbM), gbase);
     const bool ended = ends != 0u;
-    const int L = ended ? __ffs(ends) - 1 : kWLanes;
-    const uint32_t ecode = __shfl_sync(kFull, code, ended ? L : 0);
+    const int L = ended ? __ffs(ends) - 1 : G;
+    const uint32_t ecode = __shfl_sync(kFull, code, gbase + (ended ? L : 0));
     const bool live = run && ended && L < lim;
     const bool edit = live && ecode != kTbStuck;
     ok = ok && !(live && ecode == kTbStuck);
@@ -252,84 +265,124 @@ __device__ __forceinline__ bool wide_tb(int r, bool run, int wp, int wt, int dmi
 struct WideArgs {
   uint32_t* queue;
   const uint32_t* order;  // pair order (longest first), or nullptr: index order
-  u128* tables;           // per warp: kWTableEntries entries (full or band)
+  u128* tables;           // per group: kWTableEntries entries (full or band)
   int band_top;           // A, or -1: no band tables
   int band_stride;        // band table row stride (entries)
 };
 
+// One window of every busy group of the warp. The groups of a warp stay
+// converged: each pass runs when some group needs it, with per-group
+// predicates.
+template <int G>
 __device__ __forceinline__ void wide_window(const AlignParams& p, const WideArgs& a, int r,
-                                            PairState& st, u128* pmcol, uint64_t* band,
-                                            u128* tab) {
+                                            int gbase, PairState& st, u128* pmcol,
+                                            uint64_t* band, u128* tab) {
   const bool writer = r == 0;
+  const bool ga = st.busy;
   const int commit = p.W - p.O;
-  const int wp = static_cast<int>(min(static_cast<uint32_t>(p.W), st.m - st.pos_p));
-  const int wt = static_cast<int>(min(static_cast<uint32_t>(p.W), st.n - st.pos_t));
-  const bool last = st.pos_p + static_cast<uint32_t>(wp) == st.m;
-  const int ncols = last ? wt + 1 : min(wt, commit) + 1;
-  wide_masks(r, st.read, st.pos_p, wp, st.ref, st.pos_t, wt, pmcol);
+  int wp = 1, wt = 0, ncols = 1;
+  bool last = true;
+  if (ga) {
+    wp = static_cast<int>(min(static_cast<uint32_t>(p.W), st.m - st.pos_p));
+    wt = static_cast<int>(min(static_cast<uint32_t>(p.W), st.n - st.pos_t));
+    last = st.pos_p + static_cast<uint32_t>(wp) == st.m;
+    ncols = last ? wt + 1 : min(wt, commit) + 1;
+  }
+  wide_masks<G>(ga, r, gbase, st.read, st.pos_p, wp, st.ref, st.pos_t, wt, pmcol);
   __syncwarp();
-  // The whole warp works on this pair: every branch below is warp-uniform.
   int dmin = -1, cp = 0, ct = 0;
-  bool ok = true, done = false;
-  if (!last && a.band_top >= 0) {
-    dmin = wide_dc<true>(r, wp, wt, p.kmax, ncols, a.band_stride, kWRows, a.band_top, pmcol, band);
-    __syncwarp();
-    if (dmin < 0) {
-      done = true;  // above the error cap
-    } else {
-      const RunWriter rw0 = st.rw;
-      const uint32_t edits0 = st.edits;
-      bool over = false;
-      ok = wide_tb<true>(r, true, wp, wt, dmin, last, commit, ncols, a.band_stride, a.band_top,
-                         p.tb_table, pmcol, band, st.rw, writer, cp, ct, st.edits, over);
-      __syncwarp();
-      done = !over;
-      if (over) {  // the offset left the band: redo with full entries
-        st.rw = rw0;
-        st.edits = edits0;
-        ok = true;
-        cp = ct = 0;
-      }
+  bool ok = true, over = false;
+  // Windows that are not the last: band entries.
+  const bool use_band = ga && !last && a.band_top >= 0;
+  if (__any_sync(kFull, use_band)) {
+    const int d1 = wide_dc<G, true>(use_band, r, gbase, wp, wt, p.kmax, ncols, a.band_stride,
+                                    kWRows, a.band_top, pmcol, band);
+    if (use_band) dmin = d1;
+  }
+  __syncwarp();
+  const bool band_trace = use_band && dmin >= 0;  // (use_band && dmin < 0: above the cap)
+  const RunWriter rw0 = st.rw;
+  const uint32_t edits0 = st.edits;
+  if (__any_sync(kFull, band_trace)) {
+    int c1 = 0, t1 = 0;
+    const bool ok1 = wide_tb<G, true>(band_trace, r, gbase, wp, wt, dmin, last, commit, ncols,
+                                      a.band_stride, a.band_top, p.tb_table, pmcol, band, st.rw,
+                                      writer, c1, t1, st.edits, over);
+    if (band_trace) {
+      ok = ok1;
+      cp = c1;
+      ct = t1;
     }
   }
-  if (!done) {
-    dmin = wide_dc<false>(r, wp, wt, p.kmax, ncols, kWStride, kWRows, 0, pmcol, tab);
+  __syncwarp();
+  if (over) {  // the offset left the band: redo with full entries
+    st.rw = rw0;
+    st.edits = edits0;
+    ok = true;
+    cp = ct = 0;
+  }
+  // Last windows, windows without band tables and redone windows: full entries.
+  const bool full = ga && (!use_band || over);
+  if (__any_sync(kFull, full)) {
+    const int d2 = wide_dc<G, false>(full, r, gbase, wp, wt, p.kmax, ncols, kWStride, kWRows, 0,
+                                     pmcol, tab);
+    if (full) dmin = d2;
     __syncwarp();
+    int c2 = 0, t2 = 0;
     bool unused = false;
-    ok = wide_tb<false>(r, dmin >= 0, wp, wt, dmin, last, commit, ncols, kWStride, 0, p.tb_table,
-                        pmcol, tab, st.rw, writer, cp, ct, st.edits, unused);
-    __syncwarp();
+    const bool ok2 = wide_tb<G, false>(full && dmin >= 0, r, gbase, wp, wt, dmin, last, commit,
+                                       ncols, kWStride, 0, p.tb_table, pmcol, tab, st.rw, writer,
+                                       c2, t2, st.edits, unused);
+    if (full) {
+      ok = ok2;
+      cp = c2;
+      ct = t2;
+    }
   }
-  if (dmin < 0) {
-    st.status = kPairExceedsK;
-  } else if (!ok || cp + ct == 0) {
-    st.status = kPairTbStuck;
-  } else if (st.rw.full) {
-    st.status = kPairCigarFull;
-  } else {
-    ++st.windows;
-    st.cells += static_cast<uint64_t>(wt) * static_cast<uint64_t>(dmin + 1);
-    st.pos_p += static_cast<uint32_t>(cp);
-    st.pos_t += static_cast<uint32_t>(ct);
+  __syncwarp();
+  if (ga) {
+    if (dmin < 0) {
+      st.status = kPairExceedsK;
+    } else if (!ok || cp + ct == 0) {
+      st.status = kPairTbStuck;
+    } else if (st.rw.full) {
+      st.status = kPairCigarFull;
+    } else {
+      ++st.windows;
+      st.cells += static_cast<uint64_t>(wt) * static_cast<uint64_t>(dmin + 1);
+      st.pos_p += static_cast<uint32_t>(cp);
+      st.pos_t += static_cast<uint32_t>(ct);
+    }
+    if (st.status != kPairOk || st.pos_p >= st.m) finish_pair(p, st, writer);
   }
-  if (st.status != kPairOk || st.pos_p >= st.m) finish_pair(p, st, writer);
 }
 
-__global__ void __launch_bounds__(kWLanes * kWWarps, 1) align_wide_kernel(const AlignParams p,
-                                                                          const WideArgs a) {
-  __shared__ u128 pmcols[kWWarps][kWW];
-  const int r = threadIdx.x & 31;
-  const int w = threadIdx.x >> 5;
-  u128* tab = a.tables + (static_cast<size_t>(blockIdx.x) * kWWarps + w) * kWTableEntries;
+template <int G>
+__global__ void __launch_bounds__(kWThreads, 1) align_wide_kernel(const AlignParams p,
+                                                                  const WideArgs a) {
+  constexpr int kGroups = kWThreads / G;
+  __shared__ u128 pmcols[kGroups][kWW];
+  const int lane = threadIdx.x & 31;
+  const int group = threadIdx.x / G;
+  const int r = lane % G;
+  const int gbase = lane - r;
+  u128* tab = a.tables + (static_cast<size_t>(blockIdx.x) * kGroups + group) * kWTableEntries;
   uint64_t* band = reinterpret_cast<uint64_t*>(tab);  // the same area, as 8-byte entries
   PairState st;
+  st.busy = false;
+  bool drained = false;
   for (;;) {
-    uint32_t idx = 0;
-    if (r == 0) idx = atomicAdd(a.queue, 1u);
-    idx = __shfl_sync(kFull, idx, 0);
-    if (idx >= p.n_pairs) break;
-    begin_pair(p, a.order ? a.order[idx] : idx, st, r == 0);
-    while (st.busy) wide_window(p, a, r, st, pmcols[w], band, tab);
+    // Groups without a pair take the next one from the queue.
+    const bool want = !st.busy && !drained;
+    uint32_t idx = 0xffffffffu;
+    if (want && r == 0) idx = atomicAdd(a.queue, 1u);
+    idx = __shfl_sync(kFull, idx, gbase);
+    if (want) {
+      if (idx < p.n_pairs) begin_pair(p, a.order ? a.order[idx] : idx, st, r == 0);
+      else drained = true;
+    }
+    if (!__any_sync(kFull, st.busy || !drained)) break;
+    if (__any_sync(kFull, st.busy)) wide_window<G>(p, a, r, gbase, st, pmcols[group], band, tab);
   }
 }
 
@@ -342,8 +395,8 @@ cudaError_t wide_blocks(int* blocks) {
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, align_wide_kernel,
-                                                      kWLanes * kWWarps, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, align_wide_kernel<kWG>, kWThreads,
+                                                      0);
   *blocks = per_sm * sms;
   return e;
 }
@@ -355,7 +408,8 @@ WideLayout wide_layout(uint32_t n_pairs, int blocks) {
   L.hist = up(L.queue + 256);
   L.order = up(L.hist + sizeof(uint32_t) * kLptBuckets);
   L.tables = up(L.order + sizeof(uint32_t) * static_cast<size_t>(n_pairs));
-  L.total = up(L.tables + static_cast<size_t>(blocks) * kWWarps * kWTableEntries * sizeof(u128));
+  const size_t groups = static_cast<size_t>(blocks) * (kWThreads / kWG);
+  L.total = up(L.tables + groups * kWTableEntries * sizeof(u128));
   return L;
 }
 
@@ -377,7 +431,6 @@ cudaError_t launch_wide(const AlignParams& p, bool lpt, void* ws, size_t ws_byte
   if (e != cudaSuccess) return e;
   const WideLayout L = wide_layout(p.n_pairs, blocks);
   if (ws_bytes < L.total || blocks < 1) return cudaErrorInvalidValue;
-
   char* w = static_cast<char*>(ws);
   uint32_t* hist = reinterpret_cast<uint32_t*>(w + L.hist);
   uint32_t* order = reinterpret_cast<uint32_t*>(w + L.order);
@@ -386,7 +439,7 @@ cudaError_t launch_wide(const AlignParams& p, bool lpt, void* ws, size_t ws_byte
   const WideArgs a{reinterpret_cast<uint32_t*>(w + L.queue), lpt ? order : nullptr,
                    reinterpret_cast<u128*>(w + L.tables), wide_band_top(p.O),
                    wide_band_stride(p.W, p.O)};
-  align_wide_kernel<<<blocks, kWLanes * kWWarps, 0, s>>>(p, a);
+  align_wide_kernel<kWG><<<blocks, kWThreads, 0, s>>>(p, a);
   count_launches(1);
   return cudaGetLastError();
 }
