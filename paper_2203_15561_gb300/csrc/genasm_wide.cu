@@ -357,8 +357,9 @@ __device__ __forceinline__ void wide_window(const AlignParams& p, const WideArgs
   }
 }
 
+// Three blocks per SM (168 registers, no spills): 24 resident pairs per SM.
 template <int G>
-__global__ void __launch_bounds__(kWThreads, 1) align_wide_kernel(const AlignParams p,
+__global__ void __launch_bounds__(kWThreads, 3) align_wide_kernel(const AlignParams p,
                                                                   const WideArgs a) {
   constexpr int kGroups = kWThreads / G;
   __shared__ u128 pmcols[kGroups][kWW];
