@@ -357,10 +357,12 @@ __device__ __forceinline__ void wide_window(const AlignParams& p, const WideArgs
   }
 }
 
-// Three blocks per SM (168 registers, no spills): 24 resident pairs per SM.
-template <int G>
-__global__ void __launch_bounds__(kWThreads, 3) align_wide_kernel(const AlignParams p,
-                                                                  const WideArgs a) {
+// Compiled for two blocks per SM (205 registers: the lowest latency per pair)
+// and for three (168 registers, no spills: 24 resident pairs per SM, the
+// higher throughput once there are more pairs than the two-block grid holds).
+template <int G, int kBlocksPerSm>
+__global__ void __launch_bounds__(kWThreads, kBlocksPerSm) align_wide_kernel(const AlignParams p,
+                                                                             const WideArgs a) {
   constexpr int kGroups = kWThreads / G;
   __shared__ u128 pmcols[kGroups][kWW];
   const int lane = threadIdx.x & 31;
@@ -391,14 +393,22 @@ struct WideLayout {
   size_t queue, hist, order, tables, total;
 };
 
+template <int kBlocksPerSm>
 cudaError_t wide_blocks(int* blocks) {
   int dev = 0, sms = 0, per_sm = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, align_wide_kernel<kWG>, kWThreads,
-                                                      0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm, align_wide_kernel<kWG, kBlocksPerSm>, kWThreads, 0);
   *blocks = per_sm * sms;
+  return e;
+}
+
+// Both grids; the workspace holds the tables of the larger.
+cudaError_t wide_grids(int* blocks2, int* blocks3) {
+  cudaError_t e = wide_blocks<2>(blocks2);
+  if (e == cudaSuccess) e = wide_blocks<3>(blocks3);
   return e;
 }
 
@@ -417,21 +427,24 @@ WideLayout wide_layout(uint32_t n_pairs, int blocks) {
 }  // namespace
 
 cudaError_t wide_workspace_bytes(uint32_t n_pairs, size_t* bytes) {
-  int blocks = 0;
-  const cudaError_t e = wide_blocks(&blocks);
+  int b2 = 0, b3 = 0;
+  const cudaError_t e = wide_grids(&b2, &b3);
   if (e != cudaSuccess) return e;
-  *bytes = wide_layout(n_pairs, blocks).total;
+  *bytes = wide_layout(n_pairs, std::max(b2, b3)).total;
   return cudaSuccess;
 }
 
 cudaError_t launch_wide(const AlignParams& p, bool lpt, void* ws, size_t ws_bytes,
                         cudaStream_t s) {
   if (p.n_pairs == 0) return cudaSuccess;
-  int blocks = 0;
-  cudaError_t e = wide_blocks(&blocks);
+  int b2 = 0, b3 = 0;
+  cudaError_t e = wide_grids(&b2, &b3);
   if (e != cudaSuccess) return e;
-  const WideLayout L = wide_layout(p.n_pairs, blocks);
-  if (ws_bytes < L.total || blocks < 1) return cudaErrorInvalidValue;
+  const WideLayout L = wide_layout(p.n_pairs, std::max(b2, b3));
+  if (ws_bytes < L.total || b2 < 1 || b3 < 1) return cudaErrorInvalidValue;
+  // A batch that the two-block grid holds at once runs there (one round at the
+  // lowest latency per pair); larger batches run on the three-block grid.
+  const bool small = static_cast<uint64_t>(p.n_pairs) <= static_cast<uint64_t>(b2) * (kWThreads / kWG);
   char* w = static_cast<char*>(ws);
   uint32_t* hist = reinterpret_cast<uint32_t*>(w + L.hist);
   uint32_t* order = reinterpret_cast<uint32_t*>(w + L.order);
@@ -440,7 +453,8 @@ cudaError_t launch_wide(const AlignParams& p, bool lpt, void* ws, size_t ws_byte
   const WideArgs a{reinterpret_cast<uint32_t*>(w + L.queue), lpt ? order : nullptr,
                    reinterpret_cast<u128*>(w + L.tables), wide_band_top(p.O),
                    wide_band_stride(p.W, p.O)};
-  align_wide_kernel<kWG><<<blocks, kWThreads, 0, s>>>(p, a);
+  if (small) align_wide_kernel<kWG, 2><<<b2, kWThreads, 0, s>>>(p, a);
+  else align_wide_kernel<kWG, 3><<<b3, kWThreads, 0, s>>>(p, a);
   count_launches(1);
   return cudaGetLastError();
 }
