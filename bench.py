@@ -89,11 +89,13 @@ def make_inputs(pairs: int, rank: int, workers: int):
 # CPU oracle timing (the reference arm and the cpu_baseline key)
 # ---------------------------------------------------------------------------
 
-def time_oracle(batch, seconds: float, max_pairs: int | None = None):
-    """Times the oracle on growing prefixes of `batch` until one takes about
-    `seconds`; when the whole batch (or `max_pairs`) takes less, repeats it
-    until about `seconds` have passed. Returns (pairs/s, pairs per pass,
-    total seconds, threads, passes)."""
+def time_oracle(batch, seconds: float, max_pairs: int | None = None, variant: str = "unimproved",
+                threads: int = 0):
+    """Times the oracle (`variant`, on `threads` host threads, 0: all) on
+    growing prefixes of `batch` until one takes about `seconds`; when the
+    whole batch (or `max_pairs`) takes less, repeats it until about `seconds`
+    have passed. Returns (pairs/s, pairs per pass, total seconds, threads,
+    passes)."""
     import oracle
     n = 16
     limit = batch.n_pairs if max_pairs is None else min(max_pairs, batch.n_pairs)
@@ -101,7 +103,7 @@ def time_oracle(batch, seconds: float, max_pairs: int | None = None):
         n = min(n, limit)
         sub = batch.subset(range(n))
         t0 = time.perf_counter()
-        r = oracle.align(sub, W=W, O=O, k=K, variant="unimproved")
+        r = oracle.align(sub, W=W, O=O, k=K, variant=variant, threads=threads)
         dt = time.perf_counter() - t0
         if dt >= seconds:
             return n / dt, n, dt, r.threads, 1
@@ -109,7 +111,7 @@ def time_oracle(batch, seconds: float, max_pairs: int | None = None):
             passes, total = 1, dt
             while total < seconds:
                 t0 = time.perf_counter()
-                oracle.align(sub, W=W, O=O, k=K, variant="unimproved")
+                oracle.align(sub, W=W, O=O, k=K, variant=variant, threads=threads)
                 total += time.perf_counter() - t0
                 passes += 1
             return n * passes / total, n, total, r.threads, passes
@@ -392,6 +394,14 @@ def run_ours(args):
         cpu = {"value": pps, "unit": "pairs/s", "cores": threads, "kind": "oracle",
                "sample": f"{what} ({secs:.1f} s), plain GenASM four-vector oracle (C, -O2) over "
                          f"{threads} host threads"}
+        # The improved CPU variant (AND only, rows 0..d_min, reachable columns)
+        # on the same cores, and the plain oracle on one core: shorter samples.
+        ipps, inp, isecs, ithr, _ = time_oracle(batch, args.cpu_seconds / 3, variant="improved")
+        spps, snp, ssecs, _, _ = time_oracle(batch, args.cpu_seconds / 3, threads=1)
+        cpu["improved_oracle"] = {"value": ipps, "unit": "pairs/s", "cores": ithr,
+                                  "sample": f"{inp} pairs per pass, {isecs:.1f} s"}
+        cpu["single_core"] = {"value": spps, "unit": "pairs/s", "cores": 1,
+                              "sample": f"plain oracle, {snp} pairs per pass, {ssecs:.1f} s"}
 
     if rank == 0:
         line = {
