@@ -346,7 +346,7 @@ int ga_measure_smem_peak(double out[2], ga_stream_t stream);
  * on entry do not matter. Concurrent calls need separate workspaces.
  * Limits: 1 <= W <= GA_MAX_W (128), 0 <= O < W, k >= 0 (k >= W means no
  * cap). Windows wider than GA_MAX_W_ONCHIP (64) run on the 128-bit kernel:
- * one warp per pair, tables in the workspace, no tuning.
+ * 16 lanes per pair, tables in the workspace, no tuning.
  * Errors: GA_EINVAL, GA_ENOSPC (workspace too small), GA_ECUDA.
  */
 int ga_align_batch(const uint8_t* d_reads, const uint64_t* d_read_off, const uint32_t* d_read_len,

@@ -18,6 +18,7 @@ from __future__ import annotations
 import collections
 import csv
 import hashlib
+import re
 import sys
 from pathlib import Path
 
@@ -58,11 +59,19 @@ KERNEL_SOURCES = [CSRC / "genasm_align.cu", CSRC / "genasm_window.cuh", CSRC / "
                   CSRC / "genasm_internal.h", CSRC.parent.parent / "include" / "genasm.h"]
 
 
+def _code_only(text: str) -> str:
+    """C/C++ source without its comments and blank space: the counters depend
+    on the code alone, so editing a comment does not retire them."""
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    return "".join(text.split())
+
+
 def source_hash() -> str:
     h = hashlib.sha256()
     for p in KERNEL_SOURCES:
         h.update(p.name.encode())
-        h.update(p.read_bytes())
+        h.update(_code_only(p.read_text()).encode())
     return h.hexdigest()[:16]
 
 
