@@ -35,7 +35,14 @@ OPS_PER_CELL = 6  # 2 funnel shifts + 4 three-input logic ops per 64-bit DP cell
 # tests (row d at column i+1, row d-1 at columns i and i+1) and its 4-byte
 # pattern-mask entry.
 SMEM_BYTES_PER_TB_STEP = 16
-WORKLOAD_NAME = "long-10kb-10000pairs (10 kb PacBio-like reads, 12% error, 5% flanks, seed 2)"
+WORKLOAD_NAMES = {
+    2: "long-10kb-10000pairs (10 kb PacBio-like reads, 12% error, 5% flanks, seed 2)",
+    3: "paper-scale-138929pairs (lengths normal(10 kb, 1.5 kb), 12% error, 5% flanks, "
+       "20% decoys, seed 3)",
+    4: "mixed-100bp-50kb-200000pairs (log-uniform lengths; Illumina-like under 1 kb, "
+       "PacBio-like 8-15% above, seed 4)",
+}
+WORKLOAD_NAME = WORKLOAD_NAMES[WORKLOAD]
 
 
 def parse():
@@ -44,7 +51,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--pairs", type=int, default=10_000, help="pairs per GPU (workload 2 has 10,000)")
+    ap.add_argument("--workload", type=int, default=WORKLOAD, choices=sorted(WORKLOAD_NAMES),
+                    help="synthetic workload (2: the 10 kb headline; 3: paper scale; 4: mixed lengths)")
+    ap.add_argument("--pairs", type=int, default=0,
+                    help="pairs per GPU (default: the workload's size, 10,000 for workload 2)")
     ap.add_argument("--no-plain", action="store_true", help="skip timing the plain one-pair-per-block kernel")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
@@ -77,12 +87,12 @@ def host_cores() -> int:
         return os.cpu_count() or 1
 
 
-def make_inputs(pairs: int, rank: int, workers: int):
+def make_inputs(pairs: int, rank: int, workers: int, workload: int = WORKLOAD):
     from paper_2203_15561_gb300 import datagen
     from paper_2203_15561_gb300.multigpu import shard_pair_ids
     ids = shard_pair_ids(pairs, rank)  # weak scaling: disjoint pairs per rank
     w = workers or min(16, host_cores())
-    return datagen.make_batch(WORKLOAD, pair_ids=ids, workers=w)
+    return datagen.make_batch(workload, pair_ids=ids, workers=w)
 
 
 # ---------------------------------------------------------------------------
@@ -122,7 +132,7 @@ def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
-    batch = make_inputs(max(args.pairs // 10, 64), 0, args.workers)
+    batch = make_inputs(max(args.pairs // 10, 64), 0, args.workers, args.workload)
     # each step: the oracle on a bounded sample of the workload
     per_step = max(8, int(time_oracle(batch, 2.0, max_pairs=batch.n_pairs)[0] * 4.0))
     per_step = min(per_step, batch.n_pairs)
@@ -145,7 +155,7 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD_NAME,
+        "config": {"workload": WORKLOAD_NAMES[args.workload],
                    "W": W, "O": O, "k": K, "sample_pairs_per_step": per_step},
         "gbases_per_s": bases * args.steps / tot / 1e9,
         "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": threads, "kind": "oracle",
@@ -234,7 +244,7 @@ def run_ours(args):
     from paper_2203_15561_gb300.pipeline import DeviceBatch
 
     ga.lib()
-    batch = make_inputs(args.pairs, rank, args.workers)
+    batch = make_inputs(args.pairs, rank, args.workers, args.workload)
     n = batch.n_pairs
     read_bases = batch.read_bases
     db = DeviceBatch(batch, W=W, O=O, k=K, device=str(dev))
@@ -408,7 +418,7 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": WORKLOAD_NAME,
+            "config": {"workload": WORKLOAD_NAMES[args.workload],
                        "W": W, "O": O, "k": K, "pairs_per_gpu": n, "read_bases_per_gpu": read_bases,
                        "kernel": "batched (persistent, LPT work queue, CUDA graph)",
                        ("tuning" if args.tuning else "autotuned"): {"lanes_per_pair": tuned.lanes_per_pair,
@@ -727,6 +737,9 @@ def run_e2e(args, batch, db, dev, stream, ga, barrier, max_over_ranks, sum_over_
 
 def main():
     args = parse()
+    if args.pairs <= 0:
+        from paper_2203_15561_gb300 import datagen
+        args.pairs = datagen.CONFIG_N_PAIRS[args.workload]
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

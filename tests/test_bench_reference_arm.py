@@ -21,7 +21,7 @@ def test_reference_arm_prints_one_json_line():
     import bench
     assert d["impl"] == "reference" and d["metric"] == bench.METRIC
     assert d["unit"] == "pairs/s" and d["higher_is_better"] is True and d["value"] > 0
-    assert d["config"]["workload"] == bench.WORKLOAD_NAME
+    assert d["config"]["workload"] == bench.WORKLOAD_NAMES[2]
     assert (d["config"]["W"], d["config"]["O"], d["config"]["k"]) == (bench.W, bench.O, bench.K)
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": "pairs/s", "h2d_bytes_per_step": 0,
