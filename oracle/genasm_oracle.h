@@ -23,6 +23,12 @@
  * CIGAR runs are uint32 (length << 4 | op) with the BAM op codes
  * '=' 7, 'X' 8, 'I' 1, 'D' 2. 'I' is a read base absent from the reference,
  * 'D' a reference base absent from the read.
+ *
+ * Parity unpinned: the default traceback priority order (M > S > I > D) and
+ * the window commit rule (a window that is not the last stops once W-O
+ * pattern or W-O text bases are consumed) are readings of a paper that fixes
+ * neither; no published output can confirm them. Everything else here is
+ * pinned by the tests (brute-force distances, CIGAR replay, closed forms).
  */
 #ifndef GENASM_ORACLE_H
 #define GENASM_ORACLE_H
