@@ -4,6 +4,7 @@
 // (one 4-byte store), two such chunks at a time, so both sides of the copy
 // are fully coalesced; the kernel is bound by HBM bandwidth (1.25 bytes moved
 // per base).
+#include <algorithm>
 #include <cstdint>
 
 #include <cuda_runtime.h>
@@ -235,10 +236,11 @@ cudaError_t launch_compact(const uint32_t* cigar, const uint64_t* cigar_off, con
   scan_sums_kernel<<<1, kScanThreads, 0, s>>>(sums, chunks, grand);
   offsets_kernel<<<chunks, kScanThreads, 0, s>>>(n_runs, n, sums, grand, out_off);
   int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
   const uint64_t want = (static_cast<uint64_t>(n) * 32 + 255) / 256;
-  const int blocks = static_cast<int>(want > 16ull * sms ? 16ull * sms : want);
+  const int blocks = static_cast<int>(std::max<uint64_t>(1, std::min<uint64_t>(want, 16ull * sms)));
   gather_runs_kernel<<<blocks, 256, 0, s>>>(cigar, cigar_off, n_runs, n, out_off, out_cap, out);
   count_launches(4);
   return cudaGetLastError();
