@@ -371,7 +371,7 @@ def run_ours(args):
     # kernel sources are the ones those counters were taken from.
     prof = ROOT / "profiles" / "align_batched_workload2_counters.md"
     if prof.exists():
-        from paper_2203_15561_gb300.ncu_summary import source_hash
+        from paper_2203_15561_gb300.kernel_hash import source_hash
         fields = dict(l.split(":", 1) for l in prof.read_text().splitlines()
                       if l.startswith(("source_hash:", "traffic_bytes_per_launch:")))
         if fields.get("source_hash", "").strip() == source_hash():

@@ -208,7 +208,11 @@ int ga_workspace_size_tuned(uint32_t n_pairs, int W, int O, int k, const ga_tuni
  * GA_NOALLOC_MAX_PAIRS pairs, about 1 MB) is one static array that every GPU
  * loading the library holds until the process exits. The first call on a
  * device looks up that array's device address (cudaGetSymbolAddress with the
- * device current); make that first call before any stream capture. Every
+ * device current); make that first call before any stream capture. The
+ * address is kept per device for the life of the process: after
+ * cudaDeviceReset (or anything else that destroys the device's primary
+ * context) it is stale, so do not call this entry point on that device
+ * again in the same process. Every
  * call shares the array and overwrites what the previous call left there, so
  * calls whose work overlaps on the GPU (other streams, other host threads)
  * race: order them on one stream or wait between them. It runs with tables

@@ -241,7 +241,7 @@ __global__ void __launch_bounds__(256, 1) align_batched_kernel(const AlignParams
   GroupSmem* gs = reinterpret_cast<GroupSmem*>(base);
   uint64_t* table = base + sizeof(GroupSmem) / sizeof(uint64_t);
   const size_t group_id = static_cast<size_t>(blockIdx.x) * (blockDim.x / G) + group_in_block;
-  uint64_t* spill = a.spill + group_id * kSpillEntries;
+  uint64_t* spill = a.spill ? a.spill + group_id * kSpillEntries : nullptr;
   PairState st;
   st.busy = false;
   bool drained = false;
@@ -423,7 +423,8 @@ WorkspaceLayout workspace_layout(uint32_t n_pairs, const BatchPlan& plan) {
   return L;
 }
 
-cudaError_t launch_batched(const AlignParams& p, const BatchPlan& plan, void* ws, cudaStream_t s) {
+cudaError_t launch_batched(const AlignParams& p, const BatchPlan& plan, void* ws, cudaStream_t s,
+                           bool spill_area) {
   if (p.n_pairs == 0) return cudaSuccess;
   const WorkspaceLayout L = workspace_layout(p.n_pairs, plan);
   char* w = static_cast<char*>(ws);
@@ -434,8 +435,8 @@ cudaError_t launch_batched(const AlignParams& p, const BatchPlan& plan, void* ws
   if (e != cudaSuccess) return e;
   if (plan.lpt && (e = launch_lpt_order(p.read_len, p.n_pairs, hist, order, s)) != cudaSuccess)
     return e;
-  BatchArgs a{queue, plan.lpt ? order : nullptr, reinterpret_cast<uint64_t*>(w + L.spill),
-              plan.table_entries};
+  BatchArgs a{queue, plan.lpt ? order : nullptr,
+              spill_area ? reinterpret_cast<uint64_t*>(w + L.spill) : nullptr, plan.table_entries};
   const int threads = plan.pairs_per_block * plan.lanes_per_pair;
   AlignParams q = p;
   q.band_top = plan.band_top;

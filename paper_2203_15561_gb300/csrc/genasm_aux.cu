@@ -232,13 +232,15 @@ cudaError_t launch_compact(const uint32_t* cigar, const uint64_t* cigar_off, con
     const cudaError_t e = cudaMemsetAsync(out_off, 0, sizeof(uint64_t), s);
     return e;
   }
-  chunk_sum_kernel<<<chunks, kScanThreads, 0, s>>>(n_runs, n, sums);
-  scan_sums_kernel<<<1, kScanThreads, 0, s>>>(sums, chunks, grand);
-  offsets_kernel<<<chunks, kScanThreads, 0, s>>>(n_runs, n, sums, grand, out_off);
+  // The device query comes first, so that a failure leaves every output as
+  // it was (nothing is enqueued).
   int dev = 0, sms = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
+  chunk_sum_kernel<<<chunks, kScanThreads, 0, s>>>(n_runs, n, sums);
+  scan_sums_kernel<<<1, kScanThreads, 0, s>>>(sums, chunks, grand);
+  offsets_kernel<<<chunks, kScanThreads, 0, s>>>(n_runs, n, sums, grand, out_off);
   const uint64_t want = (static_cast<uint64_t>(n) * 32 + 255) / 256;
   const int blocks = static_cast<int>(std::max<uint64_t>(1, std::min<uint64_t>(want, 16ull * sms)));
   gather_runs_kernel<<<blocks, 256, 0, s>>>(cigar, cigar_off, n_runs, n, out_off, out_cap, out);

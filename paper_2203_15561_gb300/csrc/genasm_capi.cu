@@ -10,14 +10,24 @@
 #include "genasm_internal.h"
 #include "genasm_window.cuh"
 
-namespace {
+namespace ga {
 
+namespace {
 thread_local int g_last_cuda = 0;
+}  // namespace
 
 int cuda_fail(cudaError_t e) {
   g_last_cuda = static_cast<int>(e);
   return e == cudaSuccess ? GA_OK : GA_ECUDA;
 }
+
+int last_cuda_error() { return g_last_cuda; }
+
+}  // namespace ga
+
+namespace {
+
+using ga::cuda_fail;
 
 bool bad_wok(int W, int O, int k) { return W < 1 || W > GA_MAX_W || O < 0 || O >= W || k < 0; }
 bool wide_window(int W) { return W > GA_MAX_W_ONCHIP; }
@@ -104,7 +114,7 @@ const char* ga_strerror(int code) {
   }
 }
 
-int ga_last_cuda_error(void) { return g_last_cuda; }
+int ga_last_cuda_error(void) { return ga::last_cuda_error(); }
 
 int ga_pack_2bit(const uint8_t* d_ascii, uint64_t n_chars, uint8_t* d_packed,
                  uint32_t* d_n_invalid, ga_stream_t stream) {

@@ -9,6 +9,11 @@
 
 namespace ga {
 
+// Records `e` as the calling host thread's last CUDA error (what
+// ga_last_cuda_error reports) and maps it to GA_OK or GA_ECUDA.
+int cuda_fail(cudaError_t e);
+int last_cuda_error();
+
 struct AlignParams {
   const uint8_t* reads;
   const uint64_t* read_off;
@@ -112,7 +117,12 @@ cudaError_t launch_compact(const uint32_t* cigar, const uint64_t* cigar_off, con
 cudaError_t launch_pack(const uint8_t* ascii, uint64_t n, uint8_t* packed, uint32_t* n_invalid,
                         cudaStream_t s);
 cudaError_t launch_plain(const AlignParams& p, cudaStream_t s);
-cudaError_t launch_batched(const AlignParams& p, const BatchPlan& plan, void* ws, cudaStream_t s);
+// spill_area = false runs without the per-group global spill area (the kernel
+// gets a null spill pointer): only for plans whose shared tables hold every
+// error row of a wide window and that use no band tables, so that no window
+// can need it.
+cudaError_t launch_batched(const AlignParams& p, const BatchPlan& plan, void* ws, cudaStream_t s,
+                           bool spill_area = true);
 
 // Default tuning for (W, O, k) on the current device; fills G / pairs per
 // block / table entries / lpt. Returns cudaSuccess or the device query error.

@@ -96,19 +96,26 @@ extern "C" int ga_align_batch_noalloc(const uint8_t* d_reads, const uint64_t* d_
   // entries per pair: every window fits in shared memory, so the kernel
   // never needs a spill area (and runs without band tables, whose overflow
   // would need one).
+  constexpr int kAllRows = ga::kMaxRows * ga::kMaxStride + ga::kPmCols;
   ga::BatchPlan plan{};
-  cudaError_t e = ga::resolve_plan(W, O, k, 16, 2, ga::kMaxRows * ga::kMaxStride + ga::kPmCols, 1,
-                                   false, &plan);
-  if (e != cudaSuccess) return GA_ECUDA;
+  cudaError_t e = ga::resolve_plan(W, O, k, 16, 2, kAllRows, 1, false, &plan);
+  if (e == cudaErrorInvalidValue || e == cudaErrorInvalidConfiguration) {
+    cudaGetLastError();  // a refused launch shape, not a sticky error
+    return GA_EINVAL;
+  }
+  if (e != cudaSuccess) return ga::cuda_fail(e);
+  // The kernel runs without a spill area: every window must fit the shared
+  // table (all 65 rows of a wide table), and no band table may overflow.
+  if (plan.table_entries < kAllRows || plan.band_top >= 0) return GA_EINVAL;
   const ga::WorkspaceLayout L = ga::workspace_layout(n_pairs, plan);
   if (L.order != kOrderOffset || L.order + 4ull * n_pairs > kScratchBytes) return GA_ENOSPC;
 
   void* scratch = nullptr;
-  if (scratch_address(&scratch) != 0) return GA_ECUDA;
+  const int se = scratch_address(&scratch);
+  if (se != 0) return ga::cuda_fail(static_cast<cudaError_t>(se));
   // launch_batched clears the queue counters and the histogram (the array
-  // keeps the previous call's contents) and rebuilds the pair order; the
-  // spill area it would address past the order is never used with 65-row
-  // tables.
-  e = ga::launch_batched(p, plan, scratch, reinterpret_cast<cudaStream_t>(stream));
-  return e == cudaSuccess ? GA_OK : GA_ECUDA;
+  // keeps the previous call's contents) and rebuilds the pair order.
+  e = ga::launch_batched(p, plan, scratch, reinterpret_cast<cudaStream_t>(stream),
+                         /*spill_area=*/false);
+  return ga::cuda_fail(e);
 }

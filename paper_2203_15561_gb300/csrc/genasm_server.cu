@@ -85,6 +85,7 @@ struct Request {
   std::vector<uint64_t> read_at, ref_at;  // ASCII offsets inside `ascii`
   std::vector<uint32_t> read_len, ref_len;
   uint64_t runs = 0;            // CIGAR capacity: sum of read + ref + 1
+  uint64_t seq_words = 0;       // packed bytes held in the sequence arena (0 without pairs)
   uint64_t seq_off = 0, cig_off = 0, slot0 = 0;
   uint32_t done = 0;
   double t_submit = 0, t_admit = 0;
@@ -347,11 +348,19 @@ extern "C" int ga_server_submit(ga_server* s, const ga_request* req, uint64_t* t
 namespace {
 
 // Step 1: admission of waiting requests, in arrival order, while they fit.
-int admit(ga_server* s) {
+// A request without pairs takes no device space and no launch: it is
+// complete at admission and goes straight to `finished`.
+int admit(ga_server* s, std::vector<Request*>& finished) {
   uint64_t staged = 0;
   std::vector<Request*> batch;
   while (!s->pending.empty()) {
     Request* r = s->pending.front();
+    if (r->n == 0) {
+      r->t_admit = now_ms(s->t0);
+      finished.push_back(r);
+      s->pending.pop_front();
+      continue;
+    }
     const uint64_t abytes = r->ascii.size();
     if (staged + abytes > s->ascii_cap) break;
     uint64_t so = 0, co = 0, sl = 0;
@@ -365,6 +374,7 @@ int admit(ga_server* s) {
       s->cig_alloc.release(co, r->runs);
       break;
     }
+    r->seq_words = abytes / 4;
     r->seq_off = so;
     r->cig_off = co;
     r->slot0 = sl;
@@ -491,7 +501,7 @@ int harvest(ga_server* s, const std::vector<Request*>& finished) {
       res->pub.admit_ms = r->t_admit;
       res->pub.done_ms = now_ms(s->t0);
       s->ready.push_back(res);
-      s->seq_alloc.release(r->seq_off, r->ascii.size() / 4);
+      s->seq_alloc.release(r->seq_off, r->seq_words);
       s->cig_alloc.release(r->cig_off, r->runs);
       s->slot_alloc.release(r->slot0, r->n);
       for (uint64_t p = 0; p < n; ++p) s->slot_owner[a + p] = nullptr;
@@ -506,11 +516,10 @@ int harvest(ga_server* s, const std::vector<Request*>& finished) {
 
 extern "C" int ga_server_step(ga_server* s, uint32_t* n_active) {
   if (!s) return GA_EINVAL;
-  int rc = admit(s);
+  std::vector<Request*> finished;  // requests with no pairs finish at admission
+  int rc = admit(s, finished);
   if (rc != GA_OK) return rc;
   cudaStream_t st = s->stream;
-  std::vector<Request*> finished;
-  // Requests with no pairs finish at admission.
   if (!s->active.empty()) {
     const uint32_t na = static_cast<uint32_t>(s->active.size());
     std::memcpy(s->h_active, s->active.data(), 4ull * na);

@@ -94,6 +94,24 @@ def test_tight_budget_admits_by_memory():
         check_against_oracle(batches[t], r)
 
 
+def test_empty_request_between_real_ones():
+    # A request with no pairs completes at admission, without device space or a
+    # launch, and does not hold back the requests around it.
+    batches = request_batches(2, seed=11)
+    empty = datagen.from_pairs([])
+    srv = Server(1 << 30, step_windows=16)
+    tickets = [srv.submit(batches[0], tag=0), srv.submit(empty, tag=1), srv.submit(batches[1], tag=2)]
+    assert len(set(tickets)) == 3
+    got = drain(srv, 3, max_steps=20000)
+    waiting, active, _ = srv.pending()
+    srv.close()
+    assert sorted(got) == [0, 1, 2]
+    assert got[1].n_pairs == 0 and got[1].cigar.size == 0
+    assert waiting == 0 and active == 0
+    check_against_oracle(batches[0], got[0])
+    check_against_oracle(batches[1], got[2])
+
+
 def test_oversize_request_refused():
     srv = Server(1 << 30)
     big = datagen.from_pairs([("A" * 10_000_000, "C" * 10_000_000)])  # more runs than a step can return

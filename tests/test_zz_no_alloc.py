@@ -1,7 +1,8 @@
 """GPU test of ga_align_batch_noalloc, the entry point for callers that cannot
 allocate device memory (it takes no workspace and uses the library's static
 scratch). Its outputs must equal ga_align_batch's exactly, on two calls in a
-row (the second call finds the scratch as the first one left it).
+row (the second call finds the scratch as the first one left it), and the CPU
+oracle's.
 
 This file is collected last on purpose; it passes alone in a fresh process
 and after the other tests."""
@@ -9,6 +10,8 @@ from __future__ import annotations
 
 import numpy as np
 import pytest
+
+import oracle
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -59,10 +62,19 @@ def test_noalloc_matches_batched_twice(config, ids, k):
     db.pack()
     db.align("batched")
     want = _snapshot(db)
+    ref = oracle.align(b, W=db.W, O=db.O, k=k)
     for _ in range(2):
         _poison(db)
         _noalloc(db)
-        _assert_same(_snapshot(db), want)
+        got = _snapshot(db)
+        _assert_same(got, want)
+        for x, y in zip(got[:4], (ref.dist, ref.status, ref.ref_consumed, ref.n_runs)):
+            np.testing.assert_array_equal(x, y)
+        ok = ref.status == 0  # windows and DP entries are compared where the pair aligned
+        for x, y in zip(got[4:6], (ref.n_windows, ref.cells)):
+            np.testing.assert_array_equal(x[ok], y[ok])
+        for p in range(b.n_pairs):
+            assert np.array_equal(got[6][p], ref.runs(p)), f"pair {p}: CIGAR differs from the oracle"
 
 
 def test_noalloc_rejects_too_many_pairs():
