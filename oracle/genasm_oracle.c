@@ -153,7 +153,13 @@ int oracle_window_unimproved(const uint8_t* P, int wp, const uint8_t* T, int wt,
   for (;;) {
     if (last) {
       if (j < 0) break;
+#if GA_ORACLE_MUTANT == 11
+    } else if (cp == commit) { /* planted mistake: only the read side ends a window */
+#elif GA_ORACLE_MUTANT == 12
+    } else if (ct == commit) { /* planted mistake: only the reference side ends a window */
+#else
     } else if (cp == commit || ct == commit) {
+#endif
       break;
     }
     if (j < 0 || d < 0 || i > wt) return ORACLE_STATUS_TB_STUCK;

@@ -27,8 +27,10 @@
  * Parity unpinned: the default traceback priority order (M > S > I > D) and
  * the window commit rule (a window that is not the last stops once W-O
  * pattern or W-O text bases are consumed) are readings of a paper that fixes
- * neither; no published output can confirm them. Everything else here is
- * pinned by the tests (brute-force distances, CIGAR replay, closed forms).
+ * neither; no published output can confirm that they are the authors'. How
+ * this code applies them is pinned by the tests (hand-derived multi-window
+ * cases, a textbook restatement of the window driver), as is everything else
+ * (brute-force distances, CIGAR replay, closed forms).
  */
 #ifndef GENASM_ORACLE_H
 #define GENASM_ORACLE_H

@@ -67,6 +67,28 @@ class Batch:
         o = int(self.ref_off[p])
         return self.refs[o:o + int(self.ref_len[p])].tobytes()
 
+    def slice(self, a: int, b: int) -> "Batch":
+        """Pairs a..b-1 as a Batch of their own, sharing no offsets with this one.
+        Sequences are laid out back to back in pair order, so the pairs' bytes
+        are one contiguous range of each buffer; offsets are rebased to it."""
+        a, b = max(0, a), min(self.n_pairs, b)
+        if b <= a:
+            return from_pairs([], pair_ids=[], name=self.name)
+
+        def part(buf, off, ln):
+            lo = int(off[a])
+            hi = max(lo, int((off[b - 1] + (ln[b - 1] + 3) // 4 * 4)))
+            return buf[lo:max(hi, lo + 4)].copy(), (off[a:b] - np.uint64(lo)).astype(np.uint64)
+
+        rb, ro = part(self.reads, self.read_off, self.read_len.astype(np.uint64))
+        fb, fo = part(self.refs, self.ref_off, self.ref_len.astype(np.uint64))
+        if rb.shape[0] < 4:
+            rb = np.concatenate([rb, np.full(4 - rb.shape[0], ord("A"), np.uint8)])
+        if fb.shape[0] < 4:
+            fb = np.concatenate([fb, np.full(4 - fb.shape[0], ord("A"), np.uint8)])
+        return Batch(rb, ro, self.read_len[a:b].copy(), fb, fo, self.ref_len[a:b].copy(),
+                     self.pair_ids[a:b].copy(), self.name)
+
     def subset(self, idx: Sequence[int]) -> "Batch":
         return from_pairs([(self.read(int(p)), self.ref(int(p))) for p in idx],
                           pair_ids=[int(self.pair_ids[int(p)]) for p in idx],

@@ -98,3 +98,66 @@ def canonical(cigar: str) -> bool:
             return False
         last, num = ch, ""
     return num == ""
+
+
+def suffix_free_end(P: bytes, T: bytes) -> list[list[int]]:
+    """E[a][b] = fewest edits aligning the pattern suffix P[a:] to a text segment
+    T[b:b'] for the best b' >= b (textbook recurrence over suffixes:
+    E[len(P)][b] = 0; E[a][len(T)] = len(P) - a; otherwise the minimum of
+    insert P[a], delete T[b], pair P[a] with T[b])."""
+    m, n = len(P), len(T)
+    E = [[0] * (n + 1) for _ in range(m + 1)]
+    for a in range(m - 1, -1, -1):
+        E[a][n] = m - a
+        for b in range(n - 1, -1, -1):
+            E[a][b] = min(E[a + 1][b] + 1, E[a][b + 1] + 1, E[a + 1][b + 1] + (P[a] != T[b]))
+    return E
+
+
+def windowed_textbook(read: bytes, ref: bytes, W: int, O: int, order: str = "MSID"):
+    """The windowed alignment of the method, restated on textbook edit distances
+    instead of bit vectors: each window (read window P, reference window T,
+    both at most W bases, anchored at their first bases, reference end free)
+    has d_min = E[0][0]; the traceback walks from (0, 0, d_min) and takes the
+    first edge of `order` that keeps the remaining cost within budget
+    (M: equal bases and E[a+1][b+1] <= d; S: E[a+1][b+1] <= d-1; I: E[a+1][b]
+    <= d-1; D: E[a][b+1] <= d-1); a window that does not reach the read end
+    stops before a step once W-O read or W-O reference bases are committed,
+    the last window when the read is used up. Returns (distance,
+    reference bases consumed, windows, cells, CIGAR string)."""
+    pos_p = pos_t = windows = cells = 0
+    ops: list[str] = []
+    commit = W - O
+    while pos_p < len(read):
+        wp, wt = min(W, len(read) - pos_p), min(W, len(ref) - pos_t)
+        last = pos_p + wp == len(read)
+        P, T = read[pos_p:pos_p + wp], ref[pos_t:pos_t + wt]
+        E = suffix_free_end(P, T)
+        a = b = 0
+        d = E[0][0]
+        while True:
+            if (a == wp) if last else (a == commit or b == commit):
+                break
+            can = {
+                "M": b < wt and P[a] == T[b] and E[a + 1][b + 1] <= d,
+                "S": b < wt and d >= 1 and E[a + 1][b + 1] <= d - 1,
+                "I": d >= 1 and E[a + 1][b] <= d - 1,
+                "D": b < wt and d >= 1 and E[a][b + 1] <= d - 1,
+            }
+            edge = next(e for e in order if can[e])
+            ops.append({"M": "=", "S": "X", "I": "I", "D": "D"}[edge])
+            a += edge != "D"
+            b += edge != "I"
+            d -= edge != "M"
+        pos_p += a
+        pos_t += b
+        windows += 1
+        cells += wt * (E[0][0] + 1)
+    runs: list[list] = []
+    for o in ops:
+        if runs and runs[-1][1] == o:
+            runs[-1][0] += 1
+        else:
+            runs.append([1, o])
+    cigar = "".join(f"{n}{o}" for n, o in runs)
+    return sum(o != "=" for o in ops), pos_t, windows, cells, cigar

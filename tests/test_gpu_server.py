@@ -70,6 +70,51 @@ def test_same_alone_and_in_the_mix():
         check_against_oracle(b, mix)
 
 
+def test_workload5_two_seconds_every_request_against_oracle():
+    # Workload 5 as it arrives: Poisson requests at 2,000/s, each 1-64 fresh pairs of the
+    # workload-4 distribution (pair j of the stream is make_pair(4, j, seed=5)), submitted
+    # in real time for 2 s of arrivals while the server steps, then drained. Every served
+    # request must equal the oracle on the same pairs.
+    import os
+    import time
+
+    from fullparity import oracle_dense
+
+    reqs = datagen.make_requests(2000.0, 2.0, seed=5)
+    bounds = np.cumsum([0] + [len(r.pair_ids) for r in reqs])
+    assert bounds[-1] > 100_000
+    batch = datagen.make_batch(4, pair_ids=range(int(bounds[-1])), seed=5,
+                               workers=min(16, len(os.sched_getaffinity(0))))
+    parts = [batch.slice(int(bounds[i]), int(bounds[i + 1])) for i in range(len(reqs))]
+    srv = Server(8 << 30, step_windows=48)
+    got, nxt = {}, 0
+    t0 = time.perf_counter()
+    while len(got) < len(reqs):
+        now = time.perf_counter() - t0
+        while nxt < len(reqs) and reqs[nxt].arrival_s <= now:
+            srv.submit(parts[nxt], tag=nxt)
+            nxt += 1
+        srv.step()
+        for r in srv.poll(1024):
+            got[r.tag] = r
+        assert time.perf_counter() - t0 < 600, "server did not drain"
+    srv.close()
+    ref = oracle.align(batch)
+    dist = np.concatenate([got[i].dist for i in range(len(reqs))])
+    status = np.concatenate([got[i].status for i in range(len(reqs))])
+    rc = np.concatenate([got[i].ref_consumed for i in range(len(reqs))])
+    runs = np.concatenate([got[i].cigar for i in range(len(reqs))])
+    np.testing.assert_array_equal(status, ref.status)
+    np.testing.assert_array_equal(dist, ref.dist)
+    np.testing.assert_array_equal(rc, ref.ref_consumed)
+    if not np.array_equal(runs, oracle_dense(ref)):
+        for i in range(len(reqs)):
+            for q in range(got[i].n_pairs):
+                p = int(bounds[i]) + q
+                assert np.array_equal(got[i].runs(q), ref.runs(p)), f"request {i}, pair {p}"
+        raise AssertionError("CIGAR runs differ")
+
+
 def test_tight_budget_admits_by_memory():
     batches = request_batches(6, seed=9)
     # Just above the server's fixed needs: requests must wait for memory.

@@ -377,3 +377,84 @@ def test_wide_windows_multi_window_pairs(W, O):
         rb, ed, used, ok = pins.replay(b.read(q), b.ref(q), ru.cigar_str(q))
         assert rb == b.read(q) and ok and ed == ru.dist[q] and used == ru.ref_consumed[q]
         assert pins.canonical(ru.cigar_str(q))
+
+
+# ---- the commit rule of windows that are not the last (reading c5) ----------
+
+def _commit_rule_rows():
+    rows = []
+    for line in (GOLDEN / "commit_rule_w8.txt").read_text().splitlines():
+        if not line.strip() or line.startswith("#"):
+            continue
+        rd, rf, dist, used, nw, cells, cig = line.split("\t")
+        rows.append((rd, rf, int(dist), int(used), int(nw), int(cells), cig))
+    return rows
+
+
+def _commit_rule_mismatches(variant="unimproved", mutant=None):
+    rows = _commit_rule_rows()
+    b = datagen.from_pairs([(r[0], r[1]) for r in rows])
+    r = oracle.align(b, W=8, O=3, k=8, variant=variant, mutant=mutant)
+    bad = []
+    for p, (rd, rf, dist, used, nw, cells, cig) in enumerate(rows):
+        got = (int(r.dist[p]), int(r.ref_consumed[p]), int(r.n_windows[p]), int(r.cells[p]),
+               r.cigar_str(p))
+        if got != (dist, used, nw, cells, cig):
+            bad.append((rd, rf, got))
+    return bad
+
+
+@pytest.mark.parametrize("variant", ["unimproved", "improved"])
+def test_commit_rule_closed_forms(variant):
+    # Hand-derived W = 8, O = 3 alignments: a window stops once 5 read OR 5
+    # reference bases are committed, whichever comes first.
+    assert _commit_rule_mismatches(variant) == []
+
+
+@pytest.mark.parametrize("mutant", [11, 12])
+def test_commit_rule_mutants_are_caught(mutant):
+    # 11: only the read side ends a window; 12: only the reference side.
+    assert _commit_rule_mismatches(mutant=mutant), f"mutant {mutant} passed the commit-rule pins"
+
+
+def _random_multiwindow_pairs(n, seed, max_len):
+    rnd = random.Random(seed)
+    out = []
+    for _ in range(n):
+        m = rnd.randint(1, max_len)
+        read = [rnd.choice("ACGT") for _ in range(m)]
+        ref = list(read)
+        for _ in range(rnd.randint(0, max(1, m // 6))):
+            x = rnd.randrange(len(ref) + 1)
+            u = rnd.random()
+            if u < 0.3 and x < len(ref):
+                ref[x] = rnd.choice("ACGT")
+            elif u < 0.65:
+                ref.insert(x, rnd.choice("ACGT"))
+            elif x < len(ref):
+                del ref[x]
+        if rnd.random() < 0.2:
+            ref = [rnd.choice("ACGT") for _ in range(rnd.randint(0, max_len))]
+        if rnd.random() < 0.3:
+            ref = [rnd.choice("ACGT") for _ in range(rnd.randint(0, 6))] + ref
+        out.append(("".join(read), "".join(ref)))
+    return out
+
+
+@pytest.mark.parametrize("W,O,order", [(8, 3, "MSID"), (8, 0, "MSID"), (8, 7, "MSID"), (12, 5, "IDSM"),
+                                       (16, 6, "MSID"), (5, 1, "DIMS"), (24, 9, "MSID"),
+                                       (64, 24, "MSID")])
+def test_oracle_equals_textbook_windowed_model(W, O, order):
+    # The whole window driver (anchoring, the commit rule, the last window, the
+    # traceback priority, run merging, the window and cell counts) against the
+    # same method restated on textbook suffix edit distances (tests/pins.py).
+    pairs = _random_multiwindow_pairs(60 if W == 64 else 150, seed=W * 31 + O,
+                                      max_len=160 if W == 64 else 6 * W)
+    b = datagen.from_pairs(pairs)
+    for variant in ("unimproved", "improved"):
+        r = oracle.align(b, W=W, O=O, k=W, variant=variant, tb_order=order)
+        for p, (rd, rf) in enumerate(pairs):
+            want = pins.windowed_textbook(rd.encode(), rf.encode(), W, O, order)
+            got = (int(r.dist[p]), int(r.ref_consumed[p]), int(r.n_windows[p]), int(r.cells[p]),
+                   r.cigar_str(p))
+            assert got == want, (variant, rd, rf)
