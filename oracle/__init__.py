@@ -73,6 +73,11 @@ def lib(mutant: int | None = None):
                 _u8p, _u64p, _u32p, _u8p, _u64p, _u32p, ctypes.c_uint32,
                 ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                 _i32p, _i32p, _i32p, _u32p, _u64p, _u32p, _u32p, _u64p]
+            so.oracle_align_batch_ex.restype = ctypes.c_int
+            so.oracle_align_batch_ex.argtypes = [
+                _u8p, _u64p, _u32p, _u8p, _u64p, _u32p, ctypes.c_uint32,
+                ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                _u32p, _i32p, _i32p, _i32p, _i32p, _u32p, _u64p, _u32p, _u32p, _u64p]
             so.oracle_window_dmin.restype = ctypes.c_int
             so.oracle_window_dmin.argtypes = [_u8p, ctypes.c_int, _u8p, ctypes.c_int, ctypes.c_int]
             _libs[key] = so
@@ -115,6 +120,7 @@ class Result:
         self.dist = np.full(n, -1, dtype=np.int32)
         self.status = np.zeros(n, dtype=np.int32)
         self.ref_consumed = np.zeros(n, dtype=np.int32)
+        self.ref_start = np.zeros(n, dtype=np.int32)
         self.n_runs = np.zeros(n, dtype=np.uint32)
         self.n_windows = np.zeros(n, dtype=np.uint32)
         self.cells = np.zeros(n, dtype=np.uint64)
@@ -146,11 +152,15 @@ def tb_order_code(order: str) -> int:
 
 
 def align(batch, W: int = 64, O: int = 24, k: int = 64, variant: str = "unimproved",
-          threads: int = 0, mutant: int | None = None, tb_order: str = "MSID") -> Result:
+          threads: int = 0, mutant: int | None = None, tb_order: str = "MSID",
+          start_span=None) -> Result:
     """Align every pair of a ``datagen.Batch`` (ASCII layout) on host threads.
 
     The oracle packs the ASCII with its own packer, then runs the window driver.
     ``tb_order`` is the traceback's priority among possible edges.
+    ``start_span`` (an int for every pair, or one value per pair; None = 0)
+    enables the free-start first window: the alignment may begin at any of the
+    first start_span reference bases (``Result.ref_start``).
     """
     reads, bad_r = pack(batch.reads, mutant)
     refs, bad_f = pack(batch.refs, mutant)
@@ -162,11 +172,17 @@ def align(batch, W: int = 64, O: int = 24, k: int = 64, variant: str = "unimprov
     ref_len = np.ascontiguousarray(batch.ref_len, dtype=np.uint32)
     n = read_len.shape[0]
     res = Result(n, cigar_capacity(read_len, ref_len))
-    res.threads = lib(mutant).oracle_align_batch(
+    if start_span is None:
+        spans = None
+    else:
+        spans = np.ascontiguousarray(np.broadcast_to(np.asarray(start_span, dtype=np.uint32), (n,)))
+    res.threads = lib(mutant).oracle_align_batch_ex(
         _p(reads, _u8p), _p(read_off, _u64p), _p(read_len, _u32p),
         _p(refs, _u8p), _p(ref_off, _u64p), _p(ref_len, _u32p), n,
         W, O, k, VARIANTS[variant], tb_order_code(tb_order), threads,
+        _p(spans, _u32p) if spans is not None else None,
         _p(res.dist, _i32p), _p(res.status, _i32p), _p(res.ref_consumed, _i32p),
+        _p(res.ref_start, _i32p),
         _p(res.cigar, _u32p), _p(res.cigar_off, _u64p), _p(res.n_runs, _u32p),
         _p(res.n_windows, _u32p), _p(res.cells, _u64p))
     return res

@@ -210,16 +210,76 @@ int oracle_window_dmin(const uint8_t* P, int wp, const uint8_t* T, int wt, int k
 }
 
 /* ------------------------------------------------------------------------ */
+/* Free-start first window: the locate step, plain form                      */
+/* ------------------------------------------------------------------------ */
+
+/* Every row d = 0..k of the DC over the whole text T[0..L) (the same
+ * recurrence as a window, with a longer text), then, per candidate start
+ * column s, the first row whose R_s[d] holds the whole pattern. */
+int oracle_locate_unimproved(const uint8_t* P, int wp, const uint8_t* T, uint32_t L, uint32_t S,
+                             int k, oracle_vec* scratch, uint32_t* s_out, int* d_out) {
+  const oracle_vec mask = wp_mask(wp);
+  oracle_vec PM[4];
+  for (int c = 0; c < 4; ++c) {
+    PM[c] = mask;
+    for (int j = 0; j < wp; ++j)
+      if (P[wp - 1 - j] == c) PM[c] &= ~((oracle_vec)1 << j);
+  }
+  const uint32_t last_s = S < L ? S : L; /* candidates 0..last_s; s = L is the empty text */
+  int* first = (int*)malloc(sizeof(int) * ((size_t)last_s + 1));
+  if (!first) return 0;
+  for (uint32_t s = 0; s <= last_s; ++s) first[s] = -1;
+  oracle_vec* prev = scratch;
+  oracle_vec* cur = scratch + (size_t)L + 1;
+  for (int d = 0; d <= k; ++d) {
+    cur[L] = init_row(d, wp);
+    for (int64_t i = (int64_t)L - 1; i >= 0; --i) {
+      const oracle_vec M = ((cur[i + 1] << 1) | PM[T[i]]) & mask;
+      oracle_vec Sv = mask, Iv = mask, Dv = mask;
+      if (d > 0) {
+        Sv = (prev[i + 1] << 1) & mask;
+        Iv = (prev[i] << 1) & mask;
+        Dv = prev[i + 1];
+      }
+      cur[i] = M & Sv & Iv & Dv;
+    }
+    for (uint32_t s = 0; s <= last_s; ++s)
+      if (first[s] < 0 && !((cur[s] >> (wp - 1)) & 1)) first[s] = d;
+    oracle_vec* t = prev;
+    prev = cur;
+    cur = t;
+  }
+  int best = -1;
+  uint32_t at = 0;
+  for (uint32_t s = 0; s <= last_s; ++s) {
+#if GA_ORACLE_MUTANT == 13
+    if (first[s] >= 0 && (best < 0 || first[s] <= best)) { /* planted mistake: rightmost start */
+#else
+    if (first[s] >= 0 && (best < 0 || first[s] < best)) {
+#endif
+      best = first[s];
+      at = s;
+    }
+  }
+  free(first);
+  if (best < 0) return 0;
+  *s_out = at;
+  *d_out = best;
+  return 1;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Window driver and CIGAR writer                                            */
 /* ------------------------------------------------------------------------ */
 
 static int align_pair_with(const uint8_t* read, uint32_t m, const uint8_t* ref, uint32_t n,
-                           int W, int O, int k, int variant, int order, oracle_tables* tb,
-                           int32_t* dist, int32_t* ref_consumed,
-                           uint32_t* cigar, uint32_t cigar_cap, uint32_t* n_runs,
-                           uint32_t* n_windows, uint64_t* cells) {
+                           int W, int O, int k, int variant, int order, uint32_t start_span,
+                           oracle_tables* tb, int32_t* dist, int32_t* ref_consumed,
+                           int32_t* ref_start, uint32_t* cigar, uint32_t cigar_cap,
+                           uint32_t* n_runs, uint32_t* n_windows, uint64_t* cells) {
   *dist = -1;
   if (ref_consumed) *ref_consumed = -1;
+  if (ref_start) *ref_start = -1;
   if (n_runs) *n_runs = 0;
   if (n_windows) *n_windows = 0;
   if (cells) *cells = 0;
@@ -231,6 +291,35 @@ static int align_pair_with(const uint8_t* read, uint32_t m, const uint8_t* ref, 
   uint64_t ncells = 0;
   int64_t edits = 0;
   uint32_t run_op = 0, run_len = 0;
+
+  /* Free-start first window: locate where the read begins within the first
+   * start_span reference bases, then align from there. */
+  if (start_span > 0 && m > 0) {
+    const int wp = (int)(m < (uint32_t)W ? m : (uint32_t)W);
+    const uint64_t span_end = (uint64_t)start_span + (uint64_t)W;
+    const uint32_t L = span_end < n ? (uint32_t)span_end : n;
+    uint8_t* Tl = (uint8_t*)malloc((size_t)L + 1);
+    oracle_vec* scratch = (oracle_vec*)malloc(sizeof(oracle_vec) * 2 * ((size_t)L + 1));
+    if (!Tl || !scratch) {
+      free(Tl);
+      free(scratch);
+      return ORACLE_STATUS_BAD_ARGS;
+    }
+    unpack(read, 0, (uint32_t)wp, P);
+    unpack(ref, 0, L, Tl);
+    uint32_t s_star = 0;
+    int d_search = -1;
+    const int found =
+        variant == ORACLE_IMPROVED
+            ? oracle_locate_improved(P, wp, Tl, L, start_span, keff, scratch, &s_star, &d_search)
+            : oracle_locate_unimproved(P, wp, Tl, L, start_span, keff, scratch, &s_star, &d_search);
+    free(Tl);
+    free(scratch);
+    if (!found) return ORACLE_STATUS_EXCEEDS_K;
+    pos_t = s_star;
+    ncells += (uint64_t)L * (uint64_t)(d_search + 1);
+  }
+  if (ref_start) *ref_start = (int32_t)pos_t;
 
   while (pos_p < m) {
     const int wp = (int)((m - pos_p) < (uint32_t)W ? (m - pos_p) : (uint32_t)W);
@@ -290,22 +379,33 @@ static int align_pair_with(const uint8_t* read, uint32_t m, const uint8_t* ref, 
   return ORACLE_STATUS_OK;
 }
 
+int oracle_align_pair_ex(const uint8_t* read, uint32_t m, const uint8_t* ref, uint32_t n,
+                         int W, int O, int k, int variant, int order, uint32_t start_span,
+                         int32_t* dist, int32_t* ref_consumed, int32_t* ref_start,
+                         uint32_t* cigar, uint32_t cigar_cap, uint32_t* n_runs,
+                         uint32_t* n_windows, uint64_t* cells) {
+  oracle_tables* tb = (oracle_tables*)malloc(sizeof(oracle_tables));
+  if (!tb) return ORACLE_STATUS_BAD_ARGS;
+  const int st = align_pair_with(read, m, ref, n, W, O, k, variant, order, start_span, tb, dist,
+                                 ref_consumed, ref_start, cigar, cigar_cap, n_runs, n_windows,
+                                 cells);
+  free(tb);
+  if (st != ORACLE_STATUS_OK) {
+    *dist = -1;
+    if (ref_consumed) *ref_consumed = -1;
+    if (ref_start) *ref_start = -1;
+    if (n_runs) *n_runs = 0;
+  }
+  return st;
+}
+
 int oracle_align_pair(const uint8_t* read, uint32_t m, const uint8_t* ref, uint32_t n,
                       int W, int O, int k, int variant, int order,
                       int32_t* dist, int32_t* ref_consumed,
                       uint32_t* cigar, uint32_t cigar_cap, uint32_t* n_runs,
                       uint32_t* n_windows, uint64_t* cells) {
-  oracle_tables* tb = (oracle_tables*)malloc(sizeof(oracle_tables));
-  if (!tb) return ORACLE_STATUS_BAD_ARGS;
-  const int st = align_pair_with(read, m, ref, n, W, O, k, variant, order, tb, dist, ref_consumed,
-                                 cigar, cigar_cap, n_runs, n_windows, cells);
-  free(tb);
-  if (st != ORACLE_STATUS_OK) {
-    *dist = -1;
-    if (ref_consumed) *ref_consumed = -1;
-    if (n_runs) *n_runs = 0;
-  }
-  return st;
+  return oracle_align_pair_ex(read, m, ref, n, W, O, k, variant, order, 0, dist, ref_consumed,
+                              NULL, cigar, cigar_cap, n_runs, n_windows, cells);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -318,7 +418,8 @@ typedef struct {
   const uint32_t *read_len, *ref_len;
   uint32_t n_pairs;
   int W, O, k, variant, order;
-  int32_t *dist, *status, *ref_consumed;
+  const uint32_t* start_span;
+  int32_t *dist, *status, *ref_consumed, *ref_start;
   uint32_t* cigar;
   const uint64_t* cigar_off;
   uint32_t *n_runs, *n_windows;
@@ -333,25 +434,27 @@ static void* batch_worker(void* arg) {
   for (;;) {
     const uint32_t p = __atomic_fetch_add(&job->next, 1u, __ATOMIC_RELAXED);
     if (p >= job->n_pairs) break;
-    int32_t dist = -1, rc = -1;
+    int32_t dist = -1, rc = -1, rs = -1;
     uint32_t nr = 0, nw = 0;
     uint64_t cells = 0;
     const uint64_t cbeg = job->cigar_off ? job->cigar_off[p] : 0;
     const uint64_t ccap = job->cigar_off ? job->cigar_off[p + 1] - cbeg : 0;
     const int st = align_pair_with(job->reads + job->read_off[p], job->read_len[p],
                                    job->refs + job->ref_off[p], job->ref_len[p],
-                                   job->W, job->O, job->k, job->variant, job->order, tb, &dist,
-                                   &rc,
+                                   job->W, job->O, job->k, job->variant, job->order,
+                                   job->start_span ? job->start_span[p] : 0u, tb, &dist, &rc, &rs,
                                    job->cigar ? job->cigar + cbeg : NULL, (uint32_t)ccap, &nr,
                                    &nw, &cells);
     if (st != ORACLE_STATUS_OK) {
       dist = -1;
       rc = -1;
+      rs = -1;
       nr = 0;
     }
     job->dist[p] = dist;
     if (job->status) job->status[p] = st;
     if (job->ref_consumed) job->ref_consumed[p] = rc;
+    if (job->ref_start) job->ref_start[p] = rs;
     if (job->n_runs) job->n_runs[p] = nr;
     if (job->n_windows) job->n_windows[p] = nw;
     if (job->cells) job->cells[p] = cells;
@@ -366,14 +469,27 @@ int oracle_align_batch(const uint8_t* reads, const uint64_t* read_off, const uin
                        int n_threads, int32_t* dist, int32_t* status, int32_t* ref_consumed,
                        uint32_t* cigar, const uint64_t* cigar_off, uint32_t* n_runs,
                        uint32_t* n_windows, uint64_t* cells) {
+  return oracle_align_batch_ex(reads, read_off, read_len, refs, ref_off, ref_len, n_pairs, W, O, k,
+                               variant, order, n_threads, NULL, dist, status, ref_consumed, NULL,
+                               cigar, cigar_off, n_runs, n_windows, cells);
+}
+
+int oracle_align_batch_ex(const uint8_t* reads, const uint64_t* read_off, const uint32_t* read_len,
+                          const uint8_t* refs, const uint64_t* ref_off, const uint32_t* ref_len,
+                          uint32_t n_pairs, int W, int O, int k, int variant, int order,
+                          int n_threads, const uint32_t* start_span,
+                          int32_t* dist, int32_t* status, int32_t* ref_consumed, int32_t* ref_start,
+                          uint32_t* cigar, const uint64_t* cigar_off, uint32_t* n_runs,
+                          uint32_t* n_windows, uint64_t* cells) {
   if (n_threads <= 0) {
     long c = sysconf(_SC_NPROCESSORS_ONLN);
     n_threads = c > 0 ? (int)c : 1;
   }
   if ((uint32_t)n_threads > n_pairs) n_threads = n_pairs > 0 ? (int)n_pairs : 1;
-  batch_job job = {reads,  refs,   read_off,     ref_off, read_len, ref_len,  n_pairs,
-                   W,      O,      k,            variant, order,    dist,     status,
-                   ref_consumed, cigar, cigar_off, n_runs, n_windows, cells, 0};
+  batch_job job = {reads,   refs,       read_off, ref_off,      read_len,  ref_len,
+                   n_pairs, W,          O,        k,            variant,   order,
+                   start_span, dist,    status,   ref_consumed, ref_start, cigar,
+                   cigar_off, n_runs,   n_windows, cells,       0};
   if (n_threads == 1) {
     batch_worker(&job);
     return 1;

@@ -87,6 +87,28 @@ int oracle_align_pair(const uint8_t* read, uint32_t m, const uint8_t* ref, uint3
                       uint32_t* cigar, uint32_t cigar_cap, uint32_t* n_runs,
                       uint32_t* n_windows, uint64_t* cells);
 
+/* oracle_align_pair with a free-start first window (the locate step).
+ * start_span S is the largest reference offset at which the alignment may
+ * begin. With S = 0 this is oracle_align_pair. With S > 0 and a non-empty
+ * read, the pattern P = the first wp = min(W, m) read bases is searched in
+ * the text T = ref[0..L), L = min(n, S + W), with the GenASM recurrence:
+ * every start column s = 0..min(S, L) is a candidate (s = L is the empty
+ * text, reached with wp insertions); the smallest error count d_s over
+ * candidates whose whole pattern aligns from T[s] (text end free) is taken,
+ * and among its columns the leftmost, s*. The pair is then aligned by the
+ * window driver as usual, starting at read base 0 and reference base s*.
+ * *ref_start (optional) receives s* (0 without the locate step, -1 on
+ * failure); ref_consumed is the reference position where the alignment ends
+ * (so the CIGAR spans ref[s*..ref_consumed)); the distance counts the
+ * CIGAR's edits only; cells adds L * (d_s + 1), the DP entries of rows
+ * 0..d_s of the search. If no start column is within k edits the status is
+ * ORACLE_STATUS_EXCEEDS_K. */
+int oracle_align_pair_ex(const uint8_t* read, uint32_t m, const uint8_t* ref, uint32_t n,
+                         int W, int O, int k, int variant, int order, uint32_t start_span,
+                         int32_t* dist, int32_t* ref_consumed, int32_t* ref_start,
+                         uint32_t* cigar, uint32_t cigar_cap, uint32_t* n_runs,
+                         uint32_t* n_windows, uint64_t* cells);
+
 /* Aligns n_pairs pairs over n_threads host threads (<= 0: all online cores).
  * Offsets: read_off/ref_off are byte offsets into the packed arrays;
  * cigar_off has n_pairs + 1 entries (uint32 units), the capacity of pair p is
@@ -99,6 +121,16 @@ int oracle_align_batch(const uint8_t* reads, const uint64_t* read_off, const uin
                        int32_t* dist, int32_t* status, int32_t* ref_consumed,
                        uint32_t* cigar, const uint64_t* cigar_off, uint32_t* n_runs,
                        uint32_t* n_windows, uint64_t* cells);
+
+/* oracle_align_batch with per-pair start spans (NULL: all 0) and the
+ * alignment start per pair (ref_start, optional); see oracle_align_pair_ex. */
+int oracle_align_batch_ex(const uint8_t* reads, const uint64_t* read_off, const uint32_t* read_len,
+                          const uint8_t* refs, const uint64_t* ref_off, const uint32_t* ref_len,
+                          uint32_t n_pairs, int W, int O, int k, int variant, int order,
+                          int n_threads, const uint32_t* start_span,
+                          int32_t* dist, int32_t* status, int32_t* ref_consumed, int32_t* ref_start,
+                          uint32_t* cigar, const uint64_t* cigar_off, uint32_t* n_runs,
+                          uint32_t* n_windows, uint64_t* cells);
 
 /* One window of DC on its own, for tests that pin the distance calculation:
  * pattern codes P[0..wp), text codes T[0..wt) (one code per byte), wp <= 128,

@@ -18,6 +18,8 @@
  * Written independently of the four-vector version in genasm_oracle.c; the
  * test suite checks that the two agree bit for bit.
  */
+#include <stddef.h>
+
 #include "genasm_oracle.h"
 #include "genasm_oracle_internal.h"
 
@@ -97,4 +99,38 @@ int oracle_window_improved(const uint8_t* P, int wp, const uint8_t* T, int wt, i
   res->cp = cp;
   res->ct = ct;
   return ORACLE_STATUS_OK;
+}
+
+/* Free-start first window, locate step with improvement (2): rows are computed
+ * in order over the whole text T[0..L) and the search stops at the first row
+ * in which some candidate start column s = 0..min(S, L) holds the whole
+ * pattern; the leftmost such column is the alignment's start. */
+int oracle_locate_improved(const uint8_t* P, int wp, const uint8_t* T, uint32_t L, uint32_t S,
+                           int k, oracle_vec* scratch, uint32_t* s_out, int* d_out) {
+  const oracle_vec mask = full_mask(wp);
+  oracle_vec eq[4];
+  for (int c = 0; c < 4; ++c) eq[c] = mask;
+  for (int j = 0; j < wp; ++j) eq[P[wp - 1 - j]] &= ~((oracle_vec)1 << j);
+  const uint32_t last_s = S < L ? S : L;
+  oracle_vec* prev = scratch;
+  oracle_vec* cur = scratch + (size_t)L + 1;
+  for (int d = 0; d <= k; ++d) {
+    cur[L] = d >= wp ? 0 : ((~(oracle_vec)0 << d) & mask);
+    for (uint32_t x = L; x-- > 0;) {
+      oracle_vec r = (cur[x + 1] << 1) | eq[T[x]];
+      if (d > 0) r &= (prev[x + 1] << 1) & (prev[x] << 1) & prev[x + 1];
+      cur[x] = r & mask;
+    }
+    for (uint32_t s = 0; s <= last_s; ++s) {
+      if (!((cur[s] >> (wp - 1)) & 1)) {
+        *s_out = s;
+        *d_out = d;
+        return 1;
+      }
+    }
+    oracle_vec* t = prev;
+    prev = cur;
+    cur = t;
+  }
+  return 0;
 }

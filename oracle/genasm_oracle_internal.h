@@ -46,6 +46,19 @@ int oracle_window_improved(const uint8_t* P, int wp, const uint8_t* T, int wt, i
                            int W, int O, int k, int order, oracle_tables* tb,
                            oracle_window_result* res);
 
+/* Free-start first window, locate step (see oracle_align_pair_ex): pattern
+ * P[0..wp) (codes), text T[0..L) (codes), candidate start columns
+ * s = 0..S. Finds the smallest d <= k for which some start column s has the
+ * whole pattern aligned from T[s] with at most d edits (text end free) and
+ * the leftmost such s. Returns 1 and sets *s_out, *d_out, or 0 when no
+ * start column reaches the pattern within k edits. `scratch` holds at least
+ * 2 * (L + 1) vectors. Two independent implementations: every row 0..k over
+ * every column (plain), or rows in order until the first hit (improved). */
+int oracle_locate_unimproved(const uint8_t* P, int wp, const uint8_t* T, uint32_t L, uint32_t S,
+                             int k, oracle_vec* scratch, uint32_t* s_out, int* d_out);
+int oracle_locate_improved(const uint8_t* P, int wp, const uint8_t* T, uint32_t L, uint32_t S,
+                           int k, oracle_vec* scratch, uint32_t* s_out, int* d_out);
+
 /* The first edge kind of `order` whose bit is set in `valid` (bit e = edge
  * kind e is possible), or -1. */
 static inline int oracle_pick_edge(int order, unsigned valid) {

@@ -114,7 +114,17 @@ def suffix_free_end(P: bytes, T: bytes) -> list[list[int]]:
     return E
 
 
-def windowed_textbook(read: bytes, ref: bytes, W: int, O: int, order: str = "MSID"):
+def locate_textbook(P: bytes, T: bytes, S: int) -> tuple[int, int]:
+    """Free-start first window, restated on textbook edit distances: the
+    leftmost start s in 0..min(S, len(T)) at which the pattern P aligns to
+    T[s:b'] (best b') with the fewest edits, and that edit count."""
+    E = suffix_free_end(P, T)
+    best = min(E[0][s] for s in range(min(S, len(T)) + 1))
+    return next(s for s in range(min(S, len(T)) + 1) if E[0][s] == best), best
+
+
+def windowed_textbook(read: bytes, ref: bytes, W: int, O: int, order: str = "MSID",
+                      start_span: int = 0):
     """The windowed alignment of the method, restated on textbook edit distances
     instead of bit vectors: each window (read window P, reference window T,
     both at most W bases, anchored at their first bases, reference end free)
@@ -124,10 +134,18 @@ def windowed_textbook(read: bytes, ref: bytes, W: int, O: int, order: str = "MSI
     <= d-1; D: E[a][b+1] <= d-1); a window that does not reach the read end
     stops before a step once W-O read or W-O reference bases are committed,
     the last window when the read is used up. Returns (distance,
-    reference bases consumed, windows, cells, CIGAR string)."""
+    reference bases consumed, windows, cells, CIGAR string). With start_span
+    S > 0 the alignment first locates its start in the reference
+    (locate_textbook over the first min(len(ref), S + W) bases, cells += that
+    length times (edits + 1)) and returns the start as a sixth value."""
     pos_p = pos_t = windows = cells = 0
     ops: list[str] = []
     commit = W - O
+    if start_span > 0 and read:
+        L = min(len(ref), start_span + W)
+        pos_t, d = locate_textbook(read[:min(W, len(read))], ref[:L], start_span)
+        cells += L * (d + 1)
+    start = pos_t
     while pos_p < len(read):
         wp, wt = min(W, len(read) - pos_p), min(W, len(ref) - pos_t)
         last = pos_p + wp == len(read)
@@ -160,4 +178,5 @@ def windowed_textbook(read: bytes, ref: bytes, W: int, O: int, order: str = "MSI
         else:
             runs.append([1, o])
     cigar = "".join(f"{n}{o}" for n, o in runs)
-    return sum(o != "=" for o in ops), pos_t, windows, cells, cigar
+    out = (sum(o != "=" for o in ops), pos_t, windows, cells, cigar)
+    return out + (start,) if start_span > 0 else out

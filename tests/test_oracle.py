@@ -458,3 +458,110 @@ def test_oracle_equals_textbook_windowed_model(W, O, order):
             got = (int(r.dist[p]), int(r.ref_consumed[p]), int(r.n_windows[p]), int(r.cells[p]),
                    r.cigar_str(p))
             assert got == want, (variant, rd, rf)
+
+
+# ---- free-start first window (the locate step) ------------------------------
+
+def _free_start_rows():
+    rows = []
+    for line in (GOLDEN / "free_start.txt").read_text().splitlines():
+        if not line.strip() or line.startswith("#"):
+            continue
+        rd, rf, span, start, dist, used, cells, cig = line.split("\t")
+        rows.append((rd, rf, int(span), int(start), int(dist), int(used), int(cells), cig))
+    return rows
+
+
+def _free_start_mismatches(variant="unimproved", mutant=None):
+    rows = _free_start_rows()
+    b = datagen.from_pairs([(r[0], r[1]) for r in rows])
+    r = oracle.align(b, variant=variant, mutant=mutant, start_span=np.array([x[2] for x in rows]))
+    bad = []
+    for p, (rd, rf, span, start, dist, used, cells, cig) in enumerate(rows):
+        got = (int(r.ref_start[p]), int(r.dist[p]), int(r.ref_consumed[p]), int(r.cells[p]),
+               r.cigar_str(p))
+        if got != (start, dist, used, cells, cig):
+            bad.append((rd, rf, span, got))
+    return bad
+
+
+@pytest.mark.parametrize("variant", ["unimproved", "improved"])
+def test_free_start_closed_forms(variant):
+    assert _free_start_mismatches(variant) == []
+
+
+def test_free_start_rightmost_mutant_is_caught():
+    # 13: the search keeps the rightmost of equally good starts.
+    assert _free_start_mismatches(mutant=13)
+
+
+def _flanked_pairs(n, seed, max_len, max_flank):
+    rnd = random.Random(seed)
+    out = []
+    for P, T in _random_multiwindow_pairs(n, seed, max_len):
+        f = rnd.randint(0, max_flank)
+        out.append((P, "".join(rnd.choice("ACGT") for _ in range(f)) + T, f + rnd.randint(0, 4)))
+    return out
+
+
+@pytest.mark.parametrize("variant", ["unimproved", "improved"])
+def test_free_start_single_windows_brute_force(variant):
+    # Reads that fit one window: the start is the leftmost s in 0..S with the
+    # fewest edits of the read against the reference from s (end free, over
+    # the first S + 64 bases); the window from there costs its own
+    # brute-force distance; the CIGAR replays on the reference from the start.
+    rnd = random.Random(17)
+    cases = []
+    for _ in range(300):
+        m = rnd.randint(1, 64)
+        P = "".join(rnd.choice("ACGT") for _ in range(m))
+        T = "".join(rnd.choice("ACGT") for _ in range(rnd.randint(0, 90)))
+        if rnd.random() < 0.6 and T:
+            x = rnd.randint(0, len(T))
+            T = T[:x] + P[:rnd.randint(1, m)] + T[x:]
+        cases.append((P, T, rnd.randint(0, 40)))
+    b = datagen.from_pairs([(P, T) for P, T, _ in cases])
+    r = oracle.align(b, variant=variant, start_span=np.array([S for _, _, S in cases]))
+    for p, (P, T, S) in enumerate(cases):
+        assert int(r.status[p]) == 0
+        if S == 0:
+            continue
+        L = min(len(T), S + 64)
+        d_at = [pins.free_end_distance(P.encode(), T[s:L].encode()) for s in range(min(S, L) + 1)]
+        s_star = d_at.index(min(d_at))
+        assert int(r.ref_start[p]) == s_star, (P, T, S)
+        wt = min(64, len(T) - s_star)
+        d_win = pins.free_end_distance(P.encode(), T[s_star:s_star + wt].encode())
+        assert int(r.dist[p]) == d_win
+        assert int(r.cells[p]) == L * (min(d_at) + 1) + wt * (d_win + 1)
+        rb, ed, used, ok = pins.replay(P.encode(), T[s_star:].encode(), r.cigar_str(p))
+        assert rb == P.encode() and ok and ed == d_win and s_star + used == int(r.ref_consumed[p])
+
+
+@pytest.mark.parametrize("W,O", [(8, 3), (16, 6), (64, 24)])
+def test_free_start_equals_textbook_model(W, O):
+    pairs = _flanked_pairs(80 if W == 64 else 150, seed=W + 7 * O, max_len=160 if W == 64 else 6 * W,
+                           max_flank=3 * W)
+    b = datagen.from_pairs([(P, T) for P, T, _ in pairs])
+    spans = np.array([S for _, _, S in pairs])
+    for variant in ("unimproved", "improved"):
+        r = oracle.align(b, W=W, O=O, k=W, variant=variant, start_span=spans)
+        for p, (P, T, S) in enumerate(pairs):
+            want = pins.windowed_textbook(P.encode(), T.encode(), W, O, start_span=S)
+            got = (int(r.dist[p]), int(r.ref_consumed[p]), int(r.n_windows[p]), int(r.cells[p]),
+                   r.cigar_str(p))
+            if S > 0 and P:
+                got += (int(r.ref_start[p]),)
+            assert got == want, (variant, P, T, S)
+
+
+def test_free_start_improved_equals_unimproved_on_workloads():
+    for config, ids in ((2, [0, 3, 7]), (3, range(40, 52)), (4, range(200, 260)), (1, range(0, 100))):
+        b = datagen.make_batch(config, pair_ids=list(ids))
+        spans = (b.ref_len.astype(np.int64) + 19) // 20
+        ru = oracle.align(b, variant="unimproved", start_span=spans)
+        ri = oracle.align(b, variant="improved", start_span=spans)
+        for name in ("status", "dist", "ref_consumed", "ref_start", "n_runs", "n_windows", "cells"):
+            np.testing.assert_array_equal(getattr(ru, name), getattr(ri, name), err_msg=name)
+        for p in range(b.n_pairs):
+            np.testing.assert_array_equal(ru.runs(p), ri.runs(p))
