@@ -362,6 +362,46 @@ int ga_align_batch(const uint8_t* d_reads, const uint64_t* d_read_off, const uin
                    void* d_workspace, size_t ws_bytes, ga_stream_t stream);
 
 /*
+ * ga_align_batch_locate - ga_align_batch with a free-start first window:
+ * each pair's alignment may begin at any of the first d_start_span[p]
+ * reference bases instead of at reference base 0.
+ *
+ * The reference windows of long-read pairs usually hold the read's locus
+ * with a margin of unrelated sequence on each side; an alignment anchored at
+ * reference base 0 has to spend edits on that margin. Here the first read
+ * window's pattern (wp = min(W, read length) bases) is searched in the
+ * reference's first L = min(ref length, start_span + W) bases with the
+ * GenASM distance calculation (the recurrence of every window, over a longer
+ * text, Sec. I: the DP table of GenASM): every start column s = 0 ..
+ * min(start_span, L) is a candidate, s = L being the empty text (wp
+ * insertions). The alignment starts at the leftmost start with the fewest
+ * edits (text end free) and continues with the usual windows from read base
+ * 0 and that reference base. A span of 0 gives ga_align_batch's alignment.
+ *
+ * Inputs as ga_align_batch plus d_start_span (n_pairs uint32, device).
+ * Outputs as ga_align_batch plus d_ref_start (n_pairs int32, device): the
+ * reference base where the alignment (and the CIGAR) begins, 0 for a span of
+ * 0 or an empty read, -1 unless the status is GA_PAIR_OK. d_ref_consumed is
+ * the reference base where the alignment ends, so the CIGAR spans
+ * [d_ref_start, d_ref_consumed). The distance counts the CIGAR's edits only.
+ * d_cells adds the search's L * (its edit count + 1) DP entries. If no start
+ * reaches the whole pattern within k edits the pair's status is
+ * GA_PAIR_EXCEEDS_K. Workspace: ga_workspace_size(n_pairs, W, O, k) bytes.
+ * W <= GA_MAX_W_ONCHIP. Asynchronous on `stream`.
+ * Errors: GA_EINVAL (also W > GA_MAX_W_ONCHIP or NULL start spans / starts),
+ * GA_ENOSPC, GA_ECUDA.
+ */
+int ga_align_batch_locate(const uint8_t* d_reads, const uint64_t* d_read_off,
+                          const uint32_t* d_read_len, const uint8_t* d_refs,
+                          const uint64_t* d_ref_off, const uint32_t* d_ref_len,
+                          uint32_t n_pairs, int W, int O, int k,
+                          const uint32_t* d_start_span, int32_t* d_ref_start,
+                          int32_t* d_dist, int32_t* d_status, int32_t* d_ref_consumed,
+                          uint32_t* d_cigar, const uint64_t* d_cigar_off, uint32_t* d_n_runs,
+                          uint32_t* d_n_windows, uint64_t* d_cells,
+                          void* d_workspace, size_t ws_bytes, ga_stream_t stream);
+
+/*
  * ga_align_batch_order - ga_align_batch with another traceback priority
  * order. When several edges leave a traceback state, the first possible one
  * of tb_order is taken. Neither the paper nor GenASM fixes one;

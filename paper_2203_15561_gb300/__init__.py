@@ -111,6 +111,9 @@ def lib():
             so.ga_ablation_workspace_size.argtypes = [_u32, _i, _i, _i, _i, ctypes.POINTER(_sz)]
             so.ga_align_ablation.restype = _i
             so.ga_align_ablation.argtypes = _ALIGN_ARGS + [_i, _vp, _vp, _sz, _vp]
+            so.ga_align_batch_locate.restype = _i
+            so.ga_align_batch_locate.argtypes = _ALIGN_ARGS[:10] + [_vp, _vp] + _ALIGN_ARGS[10:] + [
+                _vp, _sz, _vp]
             _lib = so
         return _lib
 
@@ -230,6 +233,20 @@ def ga_align_plain(d_reads, d_read_off, d_read_len, d_refs, d_ref_off, d_ref_len
                     d_dist, d_status, d_ref_consumed, d_cigar, d_cigar_off, d_n_runs, d_n_windows,
                     d_cells)
     return _check(lib().ga_align_plain(*a, _stream(stream)), "ga_align_plain")
+
+
+def ga_align_batch_locate(d_reads, d_read_off, d_read_len, d_refs, d_ref_off, d_ref_len, n_pairs,
+                          W, O, k, d_start_span, d_ref_start, d_dist, d_status, d_ref_consumed,
+                          d_cigar, d_cigar_off, d_n_runs, d_n_windows, d_cells, d_workspace,
+                          ws_bytes, stream=None) -> int:
+    """ga_align_batch with a free-start first window: pair p may start at any of
+    its first d_start_span[p] reference bases; d_ref_start receives the start."""
+    a = _align_args(d_reads, d_read_off, d_read_len, d_refs, d_ref_off, d_ref_len, n_pairs, W, O, k,
+                    d_dist, d_status, d_ref_consumed, d_cigar, d_cigar_off, d_n_runs, d_n_windows,
+                    d_cells)
+    a = a[:10] + [_ptr(d_start_span), _ptr(d_ref_start)] + a[10:]
+    return _check(lib().ga_align_batch_locate(*a, _ptr(d_workspace), ws_bytes, _stream(stream)),
+                  "ga_align_batch_locate")
 
 
 GA_TB_ORDER_DEFAULT = 0xE4

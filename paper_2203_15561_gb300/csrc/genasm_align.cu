@@ -417,7 +417,8 @@ WorkspaceLayout workspace_layout(uint32_t n_pairs, const BatchPlan& plan) {
   L.queue = 0;
   L.hist = up(L.queue + 256);
   L.order = up(L.hist + sizeof(uint32_t) * kLptBuckets);
-  L.spill = up(L.order + sizeof(uint32_t) * static_cast<size_t>(n_pairs));
+  L.locate = up(L.order + sizeof(uint32_t) * static_cast<size_t>(n_pairs));
+  L.spill = up(L.locate + sizeof(int32_t) * static_cast<size_t>(n_pairs));
   const size_t groups = static_cast<size_t>(plan.blocks) * plan.pairs_per_block;
   L.total = up(L.spill + groups * sizeof(uint64_t) * kSpillEntries);
   return L;
@@ -443,6 +444,204 @@ cudaError_t launch_batched(const AlignParams& p, const BatchPlan& plan, void* ws
   variant_launch(plan.lanes_per_pair, plan.blocks, threads, plan.smem_bytes, s, q, a);
   count_launches(1);
   return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Free-start first window: the locate step. For a pair with start span S > 0
+// the first read window's pattern (wp = min(W, m) bases) is searched in the
+// reference's first L = min(n, S + W) bases with the DC recurrence; every
+// start column s = 0..min(S, L) is a candidate (s = L, the empty text, costs
+// wp insertions) and the leftmost column with the fewest edits is where the
+// alignment begins. One group of kLocateG lanes per pair.
+//
+// The long text is processed in 64-column chunks from its right end to its
+// left, each by the column-strip wavefront of dc_window (lane c owns 64/G
+// columns, one row per step, one row behind lane c+1). A chunk's right
+// neighbour column comes from the chunk processed before it: lane 0 records
+// its leftmost cell of every row in shared memory, and lane G-1 of the next
+// chunk reads it there (two buffers, swapped per chunk). The recurrence runs
+// right to left, so the chunks must all hold the same rows: a first pass
+// computes rows 0..kLocateCap and finds the start whenever some column gets
+// the whole pattern within that many edits; otherwise a second pass computes
+// rows 0..k. Columns past L use all-ones masks, which keep the initial column.
+// ---------------------------------------------------------------------------
+
+constexpr int kLocateG = 8;
+constexpr int kLocatePairsPerBlock = 8;
+constexpr int kLocateCap = 15;
+
+// One pass over the text: the lexicographically smallest (d << 32 | s) over
+// rows d <= rcap and candidate columns s <= smax with the whole pattern
+// active, or ~0. `nchunks` is warp-uniform; chunks at or past a group's own
+// count are skipped by its predicate. bnd: 2 * kMaxRows words of this group.
+template <int G>
+__device__ uint64_t locate_pass(int r, bool go, const uint8_t* __restrict__ ref, uint32_t L,
+                                uint32_t smax, int wp, int rcap, uint32_t nchunks,
+                                const uint64_t (&pmc)[4], uint64_t* bnd) {
+  constexpr int C = 64 / G;
+  const int c0 = r * C;
+  const uint64_t msb = 1ull << (wp - 1);
+  uint64_t* bin = bnd;
+  uint64_t* bout = bnd + kMaxRows;
+  for (int d = r; d <= rcap; d += G) bin[d] = d >= 64 ? 0ull : (~0ull << d);  // the initial column
+  __syncwarp();
+  const uint32_t own = (L + 63) / 64;  // this group's chunks
+  uint64_t best = ~0ull;
+  for (uint32_t ck = nchunks; ck-- > 0;) {
+    const bool live = go && ck < own;
+    const uint32_t cb = ck * 64u;
+    uint64_t pm[C];
+#pragma unroll
+    for (int x = 0; x < C; ++x) {
+      const uint32_t col = cb + static_cast<uint32_t>(c0 + x);
+      const bool in = live && col < L;
+      const uint32_t c = in ? base_at(ref, col) : 0u;
+      const uint64_t v = c == 0 ? pmc[0] : c == 1 ? pmc[1] : c == 2 ? pmc[2] : pmc[3];
+      pm[x] = in ? v : ~0ull;
+    }
+    uint64_t P[C], PS[C];
+#pragma unroll
+    for (int x = 0; x < C; ++x) {
+      P[x] = ~0ull;
+      PS[x] = ~0ull;
+    }
+    uint64_t Pr = ~0ull, PrS = ~0ull, leftmost = ~0ull;
+    for (int t = 0; t < rcap + G; ++t) {
+      const int d = t - (G - 1 - r);
+      const uint64_t from_right = __shfl_down_sync(kFull, leftmost, 1, G);
+      const uint64_t right = r == G - 1 ? (d <= rcap ? bin[d] : ~0ull) : from_right;
+      const uint32_t low = d < 0 ? 1u : 0u;
+      uint64_t X[C];
+#pragma unroll
+      for (int x = 0; x < C; ++x) {
+        const uint64_t up_r = x == C - 1 ? Pr : P[x + 1];
+        const uint64_t up_rs = x == C - 1 ? PrS : PS[x + 1];
+        X[x] = up_rs & PS[x] & up_r;
+      }
+      uint64_t curS = shl1(right, low);
+      PrS = curS;
+      Pr = right;
+#pragma unroll
+      for (int x = C - 1; x >= 0; --x) {
+        const uint64_t nv = (curS | pm[x]) & X[x];
+        curS = shl1(nv, low);
+        P[x] = nv;
+        PS[x] = curS;
+      }
+      leftmost = P[0];
+      const bool row = d >= 0 && d <= rcap;
+      if (r == 0 && row) bout[d] = P[0];
+      if (live && row) {
+#pragma unroll
+        for (int x = C - 1; x >= 0; --x) {  // leftmost candidate last, so it wins
+          const uint32_t col = cb + static_cast<uint32_t>(c0 + x);
+          const uint64_t key = (static_cast<uint64_t>(d) << 32) | col;
+          if (col <= smax && col < L && !(P[x] & msb) && key < best) best = key;
+        }
+      }
+    }
+    __syncwarp();
+    uint64_t* t = bin;
+    bin = bout;
+    bout = t;
+  }
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) best = min(best, __shfl_xor_sync(kFull, best, o, G));
+  return best;
+}
+
+struct LocateArgs {
+  const uint32_t* start_span;
+  int32_t* ref_start;
+  int32_t* locate_d;
+};
+
+__global__ void __launch_bounds__(kLocateG * kLocatePairsPerBlock)
+    locate_kernel(const AlignParams p, const LocateArgs a) {
+  constexpr int G = kLocateG;
+  __shared__ uint64_t bnd_all[kLocatePairsPerBlock][2 * kMaxRows];
+  const int lane = threadIdx.x & 31;
+  const int group = threadIdx.x / G;
+  const int r = lane % G;
+  const uint32_t pair = blockIdx.x * kLocatePairsPerBlock + group;
+  const bool valid = pair < p.n_pairs;
+  uint32_t m = 0, n = 0, S = 0;
+  if (valid) {
+    m = p.read_len[pair];
+    n = p.ref_len[pair];
+    S = a.start_span[pair];
+  }
+  const bool go = valid && S > 0 && m > 0;
+  const int wp = go ? static_cast<int>(min(m, static_cast<uint32_t>(p.W))) : 1;
+  const uint64_t span_end = static_cast<uint64_t>(S) + static_cast<uint64_t>(p.W);
+  const uint32_t L = go ? static_cast<uint32_t>(min(static_cast<uint64_t>(n), span_end)) : 0u;
+  // Pattern masks of the read's first wp bases (bytes past the read are not read).
+  uint64_t pmc[4] = {~0ull, ~0ull, ~0ull, ~0ull};
+  if (go) {
+    const uint8_t* read = p.reads + p.read_off[pair];
+    const uint32_t nbytes = (static_cast<uint32_t>(wp) + 3u) / 4u;
+    uint32_t Pw[4];
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+      uint32_t v = 0;
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const uint32_t bi = 4u * w + b;
+        if (bi < nbytes) v |= static_cast<uint32_t>(__ldg(read + bi)) << (8 * b);
+      }
+      Pw[w] = v;
+    }
+    pattern_masks(wp, Pw, pmc[0], pmc[1], pmc[2], pmc[3]);
+  }
+  const uint8_t* ref = valid ? p.refs + p.ref_off[pair] : p.refs;
+  // The empty text (s = L) is a candidate when S reaches it: wp insertions.
+  uint64_t best = ~0ull;
+  if (go && S >= L && wp <= p.kmax) best = (static_cast<uint64_t>(wp) << 32) | L;
+  const int cap1 = min(kLocateCap, p.kmax);
+  const uint32_t chunks = (L + 63) / 64;
+  const uint32_t nchunks = __reduce_max_sync(kFull, chunks);
+  const uint32_t smax = min(S, L);
+  uint64_t* bnd = bnd_all[group];
+  if (__any_sync(kFull, go && L > 0))
+    best = min(best, locate_pass<G>(r, go && L > 0, ref, L, smax, wp, cap1, nchunks, pmc, bnd));
+  // Nothing within cap1 edits: every row up to k.
+  const bool again = go && L > 0 && (best >> 32) > static_cast<uint64_t>(cap1) && p.kmax > cap1;
+  if (__any_sync(kFull, again)) {
+    const uint32_t n2 = __reduce_max_sync(kFull, again ? chunks : 0u);
+    const uint64_t b2 = locate_pass<G>(r, again, ref, L, smax, wp, p.kmax, n2, pmc, bnd);
+    if (again) best = min(best, b2);
+  }
+  if (valid && r == 0) {
+    if (!go) {
+      a.ref_start[pair] = 0;
+      a.locate_d[pair] = -1;
+    } else if (best == ~0ull) {
+      a.ref_start[pair] = -1;
+      a.locate_d[pair] = -1;
+    } else {
+      a.ref_start[pair] = static_cast<int32_t>(best & 0xffffffffu);
+      a.locate_d[pair] = static_cast<int32_t>(best >> 32);
+    }
+  }
+}
+
+cudaError_t launch_batched_locate(const AlignParams& p, const BatchPlan& plan,
+                                  const uint32_t* start_span, int32_t* ref_start, void* ws,
+                                  cudaStream_t s) {
+  if (p.n_pairs == 0) return cudaSuccess;
+  const WorkspaceLayout L = workspace_layout(p.n_pairs, plan);
+  int32_t* locate_d = reinterpret_cast<int32_t*>(static_cast<char*>(ws) + L.locate);
+  const uint32_t blocks = (p.n_pairs + kLocatePairsPerBlock - 1) / kLocatePairsPerBlock;
+  locate_kernel<<<blocks, kLocateG * kLocatePairsPerBlock, 0, s>>>(
+      p, LocateArgs{start_span, ref_start, locate_d});
+  count_launches(1);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  AlignParams q = p;
+  q.start_span = start_span;
+  q.ref_start = ref_start;
+  q.locate_d = locate_d;
+  return launch_batched(q, plan, ws, s);
 }
 
 }  // namespace ga

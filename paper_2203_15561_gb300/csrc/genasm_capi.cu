@@ -222,6 +222,31 @@ int ga_align_batch_order(const uint8_t* d_reads, const uint64_t* d_read_off,
   return cuda_fail(ga::launch_batched(p, plan, d_workspace, reinterpret_cast<cudaStream_t>(stream)));
 }
 
+int ga_align_batch_locate(const uint8_t* d_reads, const uint64_t* d_read_off,
+                          const uint32_t* d_read_len, const uint8_t* d_refs,
+                          const uint64_t* d_ref_off, const uint32_t* d_ref_len, uint32_t n_pairs,
+                          int W, int O, int k, const uint32_t* d_start_span, int32_t* d_ref_start,
+                          int32_t* d_dist, int32_t* d_status, int32_t* d_ref_consumed,
+                          uint32_t* d_cigar, const uint64_t* d_cigar_off, uint32_t* d_n_runs,
+                          uint32_t* d_n_windows, uint64_t* d_cells, void* d_workspace,
+                          size_t ws_bytes, ga_stream_t stream) {
+  ga::AlignParams p{};
+  int rc = fill_params(d_reads, d_read_off, d_read_len, d_refs, d_ref_off, d_ref_len, n_pairs, W,
+                       O, k, d_dist, d_status, d_ref_consumed, d_cigar, d_cigar_off, d_n_runs,
+                       d_n_windows, d_cells, &p);
+  if (rc != GA_OK) return rc;
+  if (wide_window(W)) return GA_EINVAL;  // the locate step runs with on-chip windows
+  if (n_pairs > 0 && (!d_start_span || !d_ref_start)) return GA_EINVAL;
+  if (n_pairs == 0) return GA_OK;
+  ga::BatchPlan plan{};
+  rc = resolve(W, O, k, nullptr, &plan);
+  if (rc != GA_OK) return rc;
+  const ga::WorkspaceLayout L = ga::workspace_layout(n_pairs, plan);
+  if (!d_workspace || ws_bytes < L.total) return GA_ENOSPC;
+  return cuda_fail(ga::launch_batched_locate(p, plan, d_start_span, d_ref_start, d_workspace,
+                                             reinterpret_cast<cudaStream_t>(stream)));
+}
+
 int ga_align_batch(const uint8_t* d_reads, const uint64_t* d_read_off, const uint32_t* d_read_len,
                    const uint8_t* d_refs, const uint64_t* d_ref_off, const uint32_t* d_ref_len,
                    uint32_t n_pairs, int W, int O, int k, int32_t* d_dist, int32_t* d_status,

@@ -34,6 +34,14 @@ struct AlignParams {
   uint32_t* n_windows;  // optional
   uint64_t* cells;      // optional
   const uint32_t* cigar_cap;  // optional per-pair CIGAR capacity (else cigar_off[p+1] - cigar_off[p])
+  // Free-start first window (set by the locate launcher, else null): the
+  // locate kernel writes ref_start (alignment start, -1 when the search found
+  // no start within k edits) and locate_d (the search's edit count, -1
+  // without a search); the alignment starts at ref_start and counts the
+  // search's L * (locate_d + 1) DP entries, L = min(ref_len, start_span + W).
+  const uint32_t* start_span;
+  int32_t* ref_start;
+  int32_t* locate_d;
 };
 
 // Resolved tuning of the batched kernel.
@@ -52,6 +60,7 @@ struct WorkspaceLayout {
   size_t queue;   // uint32 counters (256 B)
   size_t hist;    // uint32[kLptBuckets]
   size_t order;   // uint32[n_pairs]
+  size_t locate;  // int32[n_pairs]: the locate step's edit counts
   size_t spill;   // uint64[groups][kMaxRows * kMaxCols]
   size_t total;
 };
@@ -123,6 +132,13 @@ cudaError_t launch_plain(const AlignParams& p, cudaStream_t s);
 // can need it.
 cudaError_t launch_batched(const AlignParams& p, const BatchPlan& plan, void* ws, cudaStream_t s,
                            bool spill_area = true);
+
+// The batched alignment with a free-start first window: the locate kernel
+// over every pair (start spans d_start_span, starts into d_ref_start), then
+// the batched kernel starting each pair there.
+cudaError_t launch_batched_locate(const AlignParams& p, const BatchPlan& plan,
+                                  const uint32_t* start_span, int32_t* ref_start, void* ws,
+                                  cudaStream_t s);
 
 // Default tuning for (W, O, k) on the current device; fills G / pairs per
 // block / table entries / lpt. Returns cudaSuccess or the device query error.

@@ -34,6 +34,7 @@ __device__ __forceinline__ void finish_pair(const AlignParams& p, PairState& st,
     p.dist[st.pair] = ok ? static_cast<int32_t>(st.edits) : -1;
     p.status[st.pair] = st.status;
     p.ref_consumed[st.pair] = ok ? static_cast<int32_t>(st.pos_t) : -1;
+    if (p.ref_start && !ok) p.ref_start[st.pair] = -1;
     p.n_runs[st.pair] = ok ? st.rw.n : 0u;
     if (p.n_windows) p.n_windows[st.pair] = st.windows;
     if (p.cells) p.cells[st.pair] = st.cells;
@@ -57,6 +58,21 @@ __device__ __forceinline__ void begin_pair(const AlignParams& p, uint32_t pair, 
   st.status = kPairOk;
   st.busy = true;
   st.a_valid = false;
+  if (p.ref_start) {  // free-start first window: begin where the locate step found
+    const int32_t s0 = p.ref_start[pair];
+    const int32_t dl = p.locate_d[pair];
+    if (s0 < 0) {
+      st.status = kPairExceedsK;
+      finish_pair(p, st, writer);
+      return;
+    }
+    st.pos_t = static_cast<uint32_t>(s0);
+    if (dl >= 0) {
+      const uint64_t span_end = static_cast<uint64_t>(p.start_span[pair]) + static_cast<uint64_t>(p.W);
+      const uint64_t L = min(static_cast<uint64_t>(st.n), span_end);
+      st.cells = L * static_cast<uint64_t>(dl + 1);
+    }
+  }
   if (st.m == 0) finish_pair(p, st, writer);  // empty read: nothing to align
 }
 

@@ -214,13 +214,11 @@ __device__ __forceinline__ uint64_t rev64(uint64_t x) {
          __brev(static_cast<uint32_t>(x >> 32));
 }
 
-// Pattern masks PM[c] (bit j clear iff P[wp-1-j] == c), from the pattern
-// window's 2-bit codes split into their low and high bit planes, and this
-// lane's columns PM[T[c0 + x]] (all ones at c0 + x >= wt).
-template <int G>
-__device__ __forceinline__ void window_masks(int r, int wp, int wt, const uint32_t (&P)[4],
-                                             const uint32_t (&T)[4], uint64_t (&pm)[64 / G]) {
-  constexpr int C = 64 / G;
+// Pattern masks PM[c] (bit j clear iff P[wp-1-j] == c) of the pattern
+// window's 2-bit codes (base u at bits 2u%32.. of word u/16), from the codes'
+// low and high bit planes.
+__device__ __forceinline__ void pattern_masks(int wp, const uint32_t (&P)[4], uint64_t& pm0,
+                                              uint64_t& pm1, uint64_t& pm2, uint64_t& pm3) {
   uint32_t l16[4], h16[4];
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
@@ -236,10 +234,20 @@ __device__ __forceinline__ void window_masks(int r, int wp, int wt, const uint32
   const uint32_t sh = static_cast<uint32_t>(64 - wp);
   const uint64_t L = rev64(Lu) >> sh;
   const uint64_t H = rev64(Hu) >> sh;
-  const uint64_t pm0 = L | H;     // clear where code 0 (A)
-  const uint64_t pm1 = ~L | H;    // clear where code 1 (C)
-  const uint64_t pm2 = L | ~H;    // clear where code 2 (G)
-  const uint64_t pm3 = ~(L & H);  // clear where code 3 (T)
+  pm0 = L | H;     // clear where code 0 (A)
+  pm1 = ~L | H;    // clear where code 1 (C)
+  pm2 = L | ~H;    // clear where code 2 (G)
+  pm3 = ~(L & H);  // clear where code 3 (T)
+}
+
+// Pattern masks and this lane's columns PM[T[c0 + x]] (all ones at
+// c0 + x >= wt).
+template <int G>
+__device__ __forceinline__ void window_masks(int r, int wp, int wt, const uint32_t (&P)[4],
+                                             const uint32_t (&T)[4], uint64_t (&pm)[64 / G]) {
+  constexpr int C = 64 / G;
+  uint64_t pm0, pm1, pm2, pm3;
+  pattern_masks(wp, P, pm0, pm1, pm2, pm3);
   const int c0 = r * C;
   const int wi = (2 * c0) >> 5;
   uint32_t tw = T[0];

@@ -96,6 +96,27 @@ class DeviceBatch:
         else:
             ga_align_batch(*self._args(stats), self.workspace, self.ws_bytes, stream)
 
+    def set_start_span(self, start_span):
+        """Device copy of the free-start spans (an int for every pair, or one
+        value per pair) and the buffer for the alignment starts."""
+        n = max(self.n, 1)
+        spans = np.ascontiguousarray(np.broadcast_to(np.asarray(start_span, dtype=np.uint32),
+                                                     (self.n,)))
+        self.start_span = _u32(spans if self.n else np.zeros(1, np.uint32)).to(self.device)
+        if getattr(self, "ref_start", None) is None or self.ref_start.numel() < n:
+            self.ref_start = torch.empty(n, dtype=torch.int32, device=self.device)
+
+    def align_locate(self, start_span=None, stats: bool = True, stream=None):
+        """The batched alignment with a free-start first window (ga_align_batch_locate):
+        pair p may begin at any of its first start_span[p] reference bases (given
+        here or by set_start_span); the starts land in ref_start."""
+        from . import ga_align_batch_locate
+        if start_span is not None:
+            self.set_start_span(start_span)
+        a = self._args(stats)
+        ga_align_batch_locate(*a[:10], self.start_span, self.ref_start, *a[10:], self.workspace,
+                              self.ws_bytes, stream)
+
     def align_order(self, tb_order: str, stats: bool = True, stream=None):
         """The batched alignment with another traceback priority order ("MSID" is
         the default M > S > I > D); see ga_align_batch_order."""
@@ -162,6 +183,8 @@ class DeviceBatch:
             cells=self.cells[:n].cpu().numpy().view(np.uint64),
             cigar=self.cigar.cpu().numpy().view(np.uint32),
             cigar_off=self.h_cigar_off,
+            ref_start=(self.ref_start[:n].cpu().numpy() if getattr(self, "ref_start", None) is not None
+                       else np.zeros(n, np.int32)),
             n_invalid=int(self.n_invalid.item()))
 
 
