@@ -123,12 +123,17 @@ int ga_workspace_size(uint32_t n_pairs, int W, int O, int k, size_t* bytes_out);
  *                    workspace), otherwise 64-bit entries.
  *   lpt            : 1 = hand out pairs longest read first, -1 = in index
  *                    order (0 = default, longest first).
+ *   max_registers  : 0 = the kernel as compiled; 168 or 128 (with
+ *                    lanes_per_pair 8) = a variant capped at that many
+ *                    registers per thread, so that more blocks fit an SM
+ *                    when the tables are small.
  */
 typedef struct ga_tuning_s {
   int lanes_per_pair;
   int pairs_per_block;
   int table_rows;
   int lpt;
+  int max_registers;
 } ga_tuning;
 
 /*
@@ -386,8 +391,10 @@ int ga_align_batch(const uint8_t* d_reads, const uint64_t* d_read_off, const uin
  * [d_ref_start, d_ref_consumed). The distance counts the CIGAR's edits only.
  * d_cells adds the search's L * (its edit count + 1) DP entries. If no start
  * reaches the whole pattern within k edits the pair's status is
- * GA_PAIR_EXCEEDS_K. Workspace: ga_workspace_size(n_pairs, W, O, k) bytes.
- * W <= GA_MAX_W_ONCHIP. Asynchronous on `stream`.
+ * GA_PAIR_EXCEEDS_K. Tuning: the one ga_autotune_locate stored for this
+ * device and (W, O, k), else the library default (ga_align_batch_locate_tuned
+ * takes an explicit one). Workspace: ga_workspace_size_locate(n_pairs, W, O,
+ * k, tuning) bytes. W <= GA_MAX_W_ONCHIP. Asynchronous on `stream`.
  * Errors: GA_EINVAL (also W > GA_MAX_W_ONCHIP or NULL start spans / starts),
  * GA_ENOSPC, GA_ECUDA.
  */
@@ -400,6 +407,37 @@ int ga_align_batch_locate(const uint8_t* d_reads, const uint64_t* d_read_off,
                           uint32_t* d_cigar, const uint64_t* d_cigar_off, uint32_t* d_n_runs,
                           uint32_t* d_n_windows, uint64_t* d_cells,
                           void* d_workspace, size_t ws_bytes, ga_stream_t stream);
+int ga_align_batch_locate_tuned(const uint8_t* d_reads, const uint64_t* d_read_off,
+                                const uint32_t* d_read_len, const uint8_t* d_refs,
+                                const uint64_t* d_ref_off, const uint32_t* d_ref_len,
+                                uint32_t n_pairs, int W, int O, int k,
+                                const uint32_t* d_start_span, int32_t* d_ref_start,
+                                int32_t* d_dist, int32_t* d_status, int32_t* d_ref_consumed,
+                                uint32_t* d_cigar, const uint64_t* d_cigar_off, uint32_t* d_n_runs,
+                                uint32_t* d_n_windows, uint64_t* d_cells,
+                                void* d_workspace, size_t ws_bytes, const ga_tuning* tuning,
+                                ga_stream_t stream);
+/* Workspace bytes of ga_align_batch_locate(_tuned) with `tuning` (NULL = the
+ * stored free-start tuning or the default). Errors: GA_EINVAL. */
+int ga_workspace_size_locate(uint32_t n_pairs, int W, int O, int k, const ga_tuning* tuning,
+                             size_t* bytes_out);
+/*
+ * ga_autotune_locate - ga_autotune for the free-start form: the candidates
+ * are timed through ga_align_batch_locate_tuned on the caller's batch and
+ * start spans, and the fastest is stored as the device's free-start default
+ * for (W, O, k) (kept apart from ga_autotune's). Arguments as
+ * ga_align_batch_locate; workspace ga_autotune_workspace_size bytes.
+ * Errors: GA_EINVAL, GA_ENOSPC, GA_ECUDA.
+ */
+int ga_autotune_locate(const uint8_t* d_reads, const uint64_t* d_read_off,
+                       const uint32_t* d_read_len, const uint8_t* d_refs,
+                       const uint64_t* d_ref_off, const uint32_t* d_ref_len, uint32_t n_pairs,
+                       int W, int O, int k, const uint32_t* d_start_span, int32_t* d_ref_start,
+                       int32_t* d_dist, int32_t* d_status, int32_t* d_ref_consumed,
+                       uint32_t* d_cigar, const uint64_t* d_cigar_off, uint32_t* d_n_runs,
+                       uint32_t* d_n_windows, uint64_t* d_cells,
+                       void* d_workspace, size_t ws_bytes, ga_tuning* best, float* best_ms,
+                       ga_stream_t stream);
 
 /*
  * ga_align_batch_order - ga_align_batch with another traceback priority

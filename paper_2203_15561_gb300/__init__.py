@@ -54,7 +54,10 @@ class GenasmError(RuntimeError):
 class ga_tuning(ctypes.Structure):
     _fields_ = [("lanes_per_pair", ctypes.c_int),
                 ("pairs_per_block", ctypes.c_int), ("table_rows", ctypes.c_int),
-                ("lpt", ctypes.c_int)]
+                ("lpt", ctypes.c_int), ("max_registers", ctypes.c_int)]
+
+    def as_dict(self) -> dict:
+        return {name: int(getattr(self, name)) for name, _ in self._fields_}
 
 
 _lock = threading.Lock()
@@ -114,6 +117,15 @@ def lib():
             so.ga_align_batch_locate.restype = _i
             so.ga_align_batch_locate.argtypes = _ALIGN_ARGS[:10] + [_vp, _vp] + _ALIGN_ARGS[10:] + [
                 _vp, _sz, _vp]
+            so.ga_align_batch_locate_tuned.restype = _i
+            so.ga_align_batch_locate_tuned.argtypes = _ALIGN_ARGS[:10] + [_vp, _vp] + \
+                _ALIGN_ARGS[10:] + [_vp, _sz, ctypes.POINTER(ga_tuning), _vp]
+            so.ga_workspace_size_locate.restype = _i
+            so.ga_workspace_size_locate.argtypes = [_u32, _i, _i, _i, ctypes.POINTER(ga_tuning),
+                                                    ctypes.POINTER(_sz)]
+            so.ga_autotune_locate.restype = _i
+            so.ga_autotune_locate.argtypes = _ALIGN_ARGS[:10] + [_vp, _vp] + _ALIGN_ARGS[10:] + [
+                _vp, _sz, ctypes.POINTER(ga_tuning), ctypes.POINTER(ctypes.c_float), _vp]
             _lib = so
         return _lib
 
@@ -247,6 +259,43 @@ def ga_align_batch_locate(d_reads, d_read_off, d_read_len, d_refs, d_ref_off, d_
     a = a[:10] + [_ptr(d_start_span), _ptr(d_ref_start)] + a[10:]
     return _check(lib().ga_align_batch_locate(*a, _ptr(d_workspace), ws_bytes, _stream(stream)),
                   "ga_align_batch_locate")
+
+
+def ga_align_batch_locate_tuned(d_reads, d_read_off, d_read_len, d_refs, d_ref_off, d_ref_len,
+                                n_pairs, W, O, k, d_start_span, d_ref_start, d_dist, d_status,
+                                d_ref_consumed, d_cigar, d_cigar_off, d_n_runs, d_n_windows,
+                                d_cells, d_workspace, ws_bytes, tuning=None, stream=None) -> int:
+    a = _align_args(d_reads, d_read_off, d_read_len, d_refs, d_ref_off, d_ref_len, n_pairs, W, O, k,
+                    d_dist, d_status, d_ref_consumed, d_cigar, d_cigar_off, d_n_runs, d_n_windows,
+                    d_cells)
+    a = a[:10] + [_ptr(d_start_span), _ptr(d_ref_start)] + a[10:]
+    t = ctypes.byref(tuning) if tuning is not None else None
+    return _check(lib().ga_align_batch_locate_tuned(*a, _ptr(d_workspace), ws_bytes, t,
+                                                    _stream(stream)), "ga_align_batch_locate_tuned")
+
+
+def ga_workspace_size_locate(n_pairs: int, W: int, O: int, k: int, tuning=None) -> int:
+    out = _sz(0)
+    t = ctypes.byref(tuning) if tuning is not None else None
+    _check(lib().ga_workspace_size_locate(n_pairs, W, O, k, t, ctypes.byref(out)),
+           "ga_workspace_size_locate")
+    return int(out.value)
+
+
+def ga_autotune_locate(d_reads, d_read_off, d_read_len, d_refs, d_ref_off, d_ref_len, n_pairs, W, O,
+                       k, d_start_span, d_ref_start, d_dist, d_status, d_ref_consumed, d_cigar,
+                       d_cigar_off, d_n_runs, d_n_windows, d_cells, d_workspace, ws_bytes,
+                       stream=None) -> tuple[ga_tuning, float]:
+    """ga_autotune for the free-start form; stores the free-start default."""
+    best = ga_tuning()
+    ms = ctypes.c_float(0)
+    a = _align_args(d_reads, d_read_off, d_read_len, d_refs, d_ref_off, d_ref_len, n_pairs, W, O, k,
+                    d_dist, d_status, d_ref_consumed, d_cigar, d_cigar_off, d_n_runs, d_n_windows,
+                    d_cells)
+    a = a[:10] + [_ptr(d_start_span), _ptr(d_ref_start)] + a[10:]
+    _check(lib().ga_autotune_locate(*a, _ptr(d_workspace), ws_bytes, ctypes.byref(best),
+                                    ctypes.byref(ms), _stream(stream)), "ga_autotune_locate")
+    return best, float(ms.value)
 
 
 GA_TB_ORDER_DEFAULT = 0xE4

@@ -229,8 +229,11 @@ struct BatchArgs {
 
 constexpr int kSpillEntries = kMaxRows * kMaxStride;
 
-template <int G>
-__global__ void __launch_bounds__(256, 1) align_batched_kernel(const AlignParams p, const BatchArgs a) {
+// R caps the registers per thread (255: no cap beyond the architecture's):
+// fewer registers let more blocks share an SM when the tables are small.
+template <int G, int R>
+__global__ void __launch_bounds__(256) __maxnreg__(R)
+    align_batched_kernel(const AlignParams p, const BatchArgs a) {
   extern __shared__ __align__(16) uint64_t smem[];
   const int lane = threadIdx.x & 31;
   const int group_in_block = threadIdx.x / G;
@@ -303,24 +306,29 @@ __global__ void lpt_scatter_kernel(const uint32_t* __restrict__ read_len, uint32
   }
 }
 
-// The compiled variants of the batched kernel (lanes per pair G).
-#define GA_BATCH_VARIANTS(X) X(4) X(8) X(16) X(32)
+// The compiled variants of the batched kernel: lanes per pair G, register
+// cap R (255 = none). Eight-lane groups also come with 168 registers (six
+// 64-thread blocks per SM) and 128 (eight).
+#define GA_BATCH_VARIANTS(X) X(4, 255) X(8, 255) X(8, 168) X(8, 128) X(16, 255) X(32, 255)
 
-bool batch_variant_exists(int G) {
-#define GA_EXISTS(g) if (G == g) return true;
+static int cap_of(int max_registers) { return max_registers == 0 ? 255 : max_registers; }
+
+bool batch_variant_exists(int G, int max_registers) {
+  const int R = cap_of(max_registers);
+#define GA_EXISTS(g, r) if (G == g && R == r) return true;
   GA_BATCH_VARIANTS(GA_EXISTS)
 #undef GA_EXISTS
   return false;
 }
 
-static cudaError_t variant_setup(int G, int threads, size_t smem, int* per_sm) {
-#define GA_SETUP(g)                                                                             \
-  if (G == g) {                                                                                 \
-    cudaError_t e = cudaFuncSetAttribute(align_batched_kernel<g>,                               \
+static cudaError_t variant_setup(int G, int R, int threads, size_t smem, int* per_sm) {
+#define GA_SETUP(g, r)                                                                          \
+  if (G == g && R == r) {                                                                       \
+    cudaError_t e = cudaFuncSetAttribute(align_batched_kernel<g, r>,                            \
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,           \
                                          static_cast<int>(smem));                               \
     if (e != cudaSuccess) return e;                                                             \
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, align_batched_kernel<g>,       \
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, align_batched_kernel<g, r>,    \
                                                          threads, smem);                        \
   }
   GA_BATCH_VARIANTS(GA_SETUP)
@@ -328,10 +336,10 @@ static cudaError_t variant_setup(int G, int threads, size_t smem, int* per_sm) {
   return cudaErrorInvalidValue;
 }
 
-static void variant_launch(int G, int blocks, int threads, size_t smem, cudaStream_t s,
+static void variant_launch(int G, int R, int blocks, int threads, size_t smem, cudaStream_t s,
                            const AlignParams& p, const BatchArgs& a) {
-#define GA_LAUNCH(g) \
-  if (G == g) align_batched_kernel<g><<<blocks, threads, smem, s>>>(p, a);
+#define GA_LAUNCH(g, r) \
+  if (G == g && R == r) align_batched_kernel<g, r><<<blocks, threads, smem, s>>>(p, a);
   GA_BATCH_VARIANTS(GA_LAUNCH)
 #undef GA_LAUNCH
 }
@@ -349,14 +357,16 @@ int table_rows_for(int G, int W, int O, int entries, bool band) {
   return band ? 2 * entries / band_stride(G, ncols) : (entries - kPmCols) / table_stride(ncols);
 }
 
-cudaError_t default_tuning(int W, int O, int k, int* G, int* ppb, int* table_entries, int* lpt) {
+cudaError_t default_tuning(int W, int O, int k, int* G, int* ppb, int* table_entries, int* lpt,
+                           int* max_registers, int mode) {
   const bool band = band_top_for(O) >= 0;
   ga_tuning t;
-  if (stored_tuning(W, O, k, &t)) {  // chosen by ga_autotune or set by ga_tuning_set
+  if (stored_tuning(W, O, k, &t, mode)) {  // chosen by an autotuner or set by ga_tuning_set
     *G = t.lanes_per_pair;
     *ppb = t.pairs_per_block;
     *table_entries = table_entries_for(*G, W, O, t.table_rows, band);
     *lpt = t.lpt >= 0 ? 1 : 0;
+    *max_registers = t.max_registers;
     return cudaSuccess;
   }
   *G = 8;
@@ -364,14 +374,15 @@ cudaError_t default_tuning(int W, int O, int k, int* G, int* ppb, int* table_ent
   // Rows 0..38 of a window that is not the last (W-O+1 stored columns).
   *table_entries = table_entries_for(*G, W, O, 39, band);
   *lpt = 1;
+  *max_registers = 0;
   return cudaSuccess;
 }
 
 cudaError_t resolve_plan(int W, int O, int k, int G, int ppb, int table_entries, int lpt,
-                         bool band, BatchPlan* plan) {
+                         bool band, BatchPlan* plan, int max_registers) {
   (void)W;
   (void)k;
-  if (!batch_variant_exists(G)) return cudaErrorInvalidValue;
+  if (!batch_variant_exists(G, max_registers)) return cudaErrorInvalidValue;
   if (ppb < 1 || ppb * G > 256 || (ppb * G) % 32 != 0) return cudaErrorInvalidValue;  // whole warps
   // The area holds the table rows and the 64 words of 64-bit PM columns.
   table_entries =
@@ -389,8 +400,9 @@ cudaError_t resolve_plan(int W, int O, int k, int G, int ppb, int table_entries,
   if (smem > static_cast<size_t>(smem_optin)) return cudaErrorInvalidValue;
   const int threads = ppb * G;
   int per_sm = 0;
-  if ((e = variant_setup(G, threads, smem, &per_sm)) != cudaSuccess) return e;
+  if ((e = variant_setup(G, cap_of(max_registers), threads, smem, &per_sm)) != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  plan->max_registers = max_registers;
   plan->lanes_per_pair = G;
   plan->pairs_per_block = ppb;
   plan->table_entries = table_entries;
@@ -441,7 +453,8 @@ cudaError_t launch_batched(const AlignParams& p, const BatchPlan& plan, void* ws
   const int threads = plan.pairs_per_block * plan.lanes_per_pair;
   AlignParams q = p;
   q.band_top = plan.band_top;
-  variant_launch(plan.lanes_per_pair, plan.blocks, threads, plan.smem_bytes, s, q, a);
+  variant_launch(plan.lanes_per_pair, cap_of(plan.max_registers), plan.blocks, threads,
+                 plan.smem_bytes, s, q, a);
   count_launches(1);
   return cudaGetLastError();
 }

@@ -64,20 +64,21 @@ int fill_params(const uint8_t* d_reads, const uint64_t* d_read_off, const uint32
   return GA_OK;
 }
 
-int resolve(int W, int O, int k, const ga_tuning* t, ga::BatchPlan* plan) {
-  int G = 0, ppb = 0, entries = 0, lpt = 1;
-  cudaError_t e = ga::default_tuning(W, O, k, &G, &ppb, &entries, &lpt);
+int resolve(int W, int O, int k, const ga_tuning* t, ga::BatchPlan* plan, int mode = 0) {
+  int G = 0, ppb = 0, entries = 0, lpt = 1, regs = 0;
+  cudaError_t e = ga::default_tuning(W, O, k, &G, &ppb, &entries, &lpt, &regs, mode);
   if (e != cudaSuccess) return cuda_fail(e);
   if (t) {
     if (t->lanes_per_pair) G = t->lanes_per_pair;
     if (t->pairs_per_block) ppb = t->pairs_per_block;
     if (t->table_rows) entries = ga::table_entries_for(G, W, O, t->table_rows, ga::band_top_for(O) >= 0);
     if (t->lpt) lpt = t->lpt > 0 ? 1 : 0;
-    if (!ga::batch_variant_exists(G) || ppb < 1 || ppb * G > 256 || (ppb * G) % 32 != 0 ||
+    regs = t->max_registers;
+    if (!ga::batch_variant_exists(G, regs) || ppb < 1 || ppb * G > 256 || (ppb * G) % 32 != 0 ||
         t->table_rows < 0)
       return GA_EINVAL;
   }
-  e = ga::resolve_plan(W, O, k, G, ppb, entries, lpt, true, plan);
+  e = ga::resolve_plan(W, O, k, G, ppb, entries, lpt, true, plan, regs);
   if (e == cudaErrorInvalidValue || e == cudaErrorInvalidConfiguration) {
     cudaGetLastError();
     return GA_EINVAL;
@@ -222,14 +223,25 @@ int ga_align_batch_order(const uint8_t* d_reads, const uint64_t* d_read_off,
   return cuda_fail(ga::launch_batched(p, plan, d_workspace, reinterpret_cast<cudaStream_t>(stream)));
 }
 
-int ga_align_batch_locate(const uint8_t* d_reads, const uint64_t* d_read_off,
-                          const uint32_t* d_read_len, const uint8_t* d_refs,
-                          const uint64_t* d_ref_off, const uint32_t* d_ref_len, uint32_t n_pairs,
-                          int W, int O, int k, const uint32_t* d_start_span, int32_t* d_ref_start,
-                          int32_t* d_dist, int32_t* d_status, int32_t* d_ref_consumed,
-                          uint32_t* d_cigar, const uint64_t* d_cigar_off, uint32_t* d_n_runs,
-                          uint32_t* d_n_windows, uint64_t* d_cells, void* d_workspace,
-                          size_t ws_bytes, ga_stream_t stream) {
+int ga_workspace_size_locate(uint32_t n_pairs, int W, int O, int k, const ga_tuning* tuning,
+                             size_t* bytes_out) {
+  if (!bytes_out || bad_wok(W, O, k) || wide_window(W)) return GA_EINVAL;
+  ga::BatchPlan plan{};
+  const int rc = resolve(W, O, k, tuning, &plan, 1);
+  if (rc != GA_OK) return rc;
+  *bytes_out = ga::workspace_layout(n_pairs, plan).total;
+  return GA_OK;
+}
+
+int ga_align_batch_locate_tuned(const uint8_t* d_reads, const uint64_t* d_read_off,
+                                const uint32_t* d_read_len, const uint8_t* d_refs,
+                                const uint64_t* d_ref_off, const uint32_t* d_ref_len,
+                                uint32_t n_pairs, int W, int O, int k,
+                                const uint32_t* d_start_span, int32_t* d_ref_start,
+                                int32_t* d_dist, int32_t* d_status, int32_t* d_ref_consumed,
+                                uint32_t* d_cigar, const uint64_t* d_cigar_off, uint32_t* d_n_runs,
+                                uint32_t* d_n_windows, uint64_t* d_cells, void* d_workspace,
+                                size_t ws_bytes, const ga_tuning* tuning, ga_stream_t stream) {
   ga::AlignParams p{};
   int rc = fill_params(d_reads, d_read_off, d_read_len, d_refs, d_ref_off, d_ref_len, n_pairs, W,
                        O, k, d_dist, d_status, d_ref_consumed, d_cigar, d_cigar_off, d_n_runs,
@@ -239,12 +251,27 @@ int ga_align_batch_locate(const uint8_t* d_reads, const uint64_t* d_read_off,
   if (n_pairs > 0 && (!d_start_span || !d_ref_start)) return GA_EINVAL;
   if (n_pairs == 0) return GA_OK;
   ga::BatchPlan plan{};
-  rc = resolve(W, O, k, nullptr, &plan);
+  rc = resolve(W, O, k, tuning, &plan, 1);
   if (rc != GA_OK) return rc;
   const ga::WorkspaceLayout L = ga::workspace_layout(n_pairs, plan);
   if (!d_workspace || ws_bytes < L.total) return GA_ENOSPC;
   return cuda_fail(ga::launch_batched_locate(p, plan, d_start_span, d_ref_start, d_workspace,
                                              reinterpret_cast<cudaStream_t>(stream)));
+}
+
+int ga_align_batch_locate(const uint8_t* d_reads, const uint64_t* d_read_off,
+                          const uint32_t* d_read_len, const uint8_t* d_refs,
+                          const uint64_t* d_ref_off, const uint32_t* d_ref_len, uint32_t n_pairs,
+                          int W, int O, int k, const uint32_t* d_start_span, int32_t* d_ref_start,
+                          int32_t* d_dist, int32_t* d_status, int32_t* d_ref_consumed,
+                          uint32_t* d_cigar, const uint64_t* d_cigar_off, uint32_t* d_n_runs,
+                          uint32_t* d_n_windows, uint64_t* d_cells, void* d_workspace,
+                          size_t ws_bytes, ga_stream_t stream) {
+  return ga_align_batch_locate_tuned(d_reads, d_read_off, d_read_len, d_refs, d_ref_off,
+                                     d_ref_len, n_pairs, W, O, k, d_start_span, d_ref_start,
+                                     d_dist, d_status, d_ref_consumed, d_cigar, d_cigar_off,
+                                     d_n_runs, d_n_windows, d_cells, d_workspace, ws_bytes,
+                                     nullptr, stream);
 }
 
 int ga_align_batch(const uint8_t* d_reads, const uint64_t* d_read_off, const uint32_t* d_read_len,

@@ -53,6 +53,7 @@ struct BatchPlan {
   int band_top;         // band table offset A, or -1 (wide tables only)
   int blocks;           // persistent grid size
   size_t smem_bytes;    // dynamic shared memory per block
+  int max_registers;    // register cap of the kernel variant (0: none)
 };
 
 // Workspace layout of the batched kernel (byte offsets).
@@ -111,9 +112,12 @@ uint64_t launch_count();
 void count_launches(uint64_t n);
 void uncount_launches(uint64_t n);  // kernels that were captured into a graph, not run
 
-// Per-device tuning chosen by the autotuner (or set by the caller).
-bool stored_tuning(int W, int O, int k, struct ga_tuning_s* out);
-void store_tuning(int W, int O, int k, const struct ga_tuning_s* t);
+// Per-device tuning chosen by the autotuner (or set by the caller), kept
+// apart for the two forms of the batched alignment: mode 0 anchored first
+// windows (ga_align_batch), mode 1 free-start first windows
+// (ga_align_batch_locate).
+bool stored_tuning(int W, int O, int k, struct ga_tuning_s* out, int mode = 0);
+void store_tuning(int W, int O, int k, const struct ga_tuning_s* t, int mode = 0);
 
 cudaError_t measure_int_peak(double out[3], cudaStream_t s);
 cudaError_t measure_smem_peak(double out[2], cudaStream_t s);
@@ -140,12 +144,14 @@ cudaError_t launch_batched_locate(const AlignParams& p, const BatchPlan& plan,
                                   const uint32_t* start_span, int32_t* ref_start, void* ws,
                                   cudaStream_t s);
 
-// Default tuning for (W, O, k) on the current device; fills G / pairs per
-// block / table entries / lpt. Returns cudaSuccess or the device query error.
-cudaError_t default_tuning(int W, int O, int k, int* G, int* ppb, int* table_entries, int* lpt);
-bool batch_variant_exists(int G);
+// Default tuning for (W, O, k) on the current device (the stored one of
+// `mode`, else the library's); fills G / pairs per block / table entries /
+// lpt / register cap. Returns cudaSuccess or the device query error.
+cudaError_t default_tuning(int W, int O, int k, int* G, int* ppb, int* table_entries, int* lpt,
+                           int* max_registers, int mode = 0);
+bool batch_variant_exists(int G, int max_registers = 0);
 cudaError_t resolve_plan(int W, int O, int k, int G, int ppb, int table_entries, int lpt,
-                         bool band, BatchPlan* plan);
+                         bool band, BatchPlan* plan, int max_registers = 0);
 
 // Band tables (32-bit entries around the diagonal) are used for windows that
 // are not the last when O >= 16, with offset A = min(22, O - 1). Table sizes

@@ -228,7 +228,8 @@ extern "C" int ga_server_create(size_t budget_bytes, int W, int O, int k, ga_ser
   // Step kernel tuning: the stored/default tuning when it has a step variant.
   ga_tuning t{};
   int G = 8, ppb = 8, rows = 39;
-  if (ga_tuning_get(W, O, k, &t) == GA_OK && ga::step_variant_exists(t.lanes_per_pair)) {
+  if (ga_tuning_get(W, O, k, &t) == GA_OK && ga::step_variant_exists(t.lanes_per_pair) &&
+      t.max_registers == 0) {
     G = t.lanes_per_pair;
     ppb = t.pairs_per_block;
     rows = t.table_rows;

@@ -30,9 +30,9 @@ namespace ga {
 namespace {
 
 struct TuneKey {
-  int dev, W, O, k;
+  int dev, W, O, k, mode;
   bool operator<(const TuneKey& o) const {
-    return std::tie(dev, W, O, k) < std::tie(o.dev, o.W, o.O, o.k);
+    return std::tie(dev, W, O, k, mode) < std::tie(o.dev, o.W, o.O, o.k, o.mode);
   }
 };
 
@@ -41,22 +41,22 @@ std::map<TuneKey, ga_tuning> g_tuned;
 
 }  // namespace
 
-bool stored_tuning(int W, int O, int k, ga_tuning* out) {
+bool stored_tuning(int W, int O, int k, ga_tuning* out, int mode) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return false;
   std::lock_guard<std::mutex> lock(g_tune_mutex);
-  auto it = g_tuned.find(TuneKey{dev, W, O, k});
+  auto it = g_tuned.find(TuneKey{dev, W, O, k, mode});
   if (it == g_tuned.end()) return false;
   *out = it->second;
   return true;
 }
 
-void store_tuning(int W, int O, int k, const ga_tuning* t) {
+void store_tuning(int W, int O, int k, const ga_tuning* t, int mode) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return;
   std::lock_guard<std::mutex> lock(g_tune_mutex);
-  if (t) g_tuned[TuneKey{dev, W, O, k}] = *t;
-  else g_tuned.erase(TuneKey{dev, W, O, k});
+  if (t) g_tuned[TuneKey{dev, W, O, k, mode}] = *t;
+  else g_tuned.erase(TuneKey{dev, W, O, k, mode});
 }
 
 }  // namespace ga
@@ -67,14 +67,20 @@ int bad_wok(int W, int O, int k) {
   return W < 1 || W > GA_MAX_W_ONCHIP || O < 0 || O >= W || k < 0;
 }
 
-// Candidate tunings for a workload whose windows keep about `rows` rows.
+// Candidate tunings for a workload whose windows keep about `rows` rows:
+// lanes per pair, pairs per block, two table sizes, and for eight-lane groups
+// the register-capped variants (which pay off when small tables leave room
+// for more blocks per SM).
 std::vector<ga_tuning> candidates(int rows) {
   const int lo = std::min(65, std::max(4, rows + 5));
   const int hi = std::min(65, std::max(6, rows + 8));
   std::vector<ga_tuning> c;
   const int shapes[][2] = {{4, 8}, {4, 16}, {8, 4}, {8, 8}, {16, 2}, {16, 4}, {32, 1}, {32, 2}};
   for (const auto& s : shapes)
-    for (int r : {lo, hi}) c.push_back(ga_tuning{s[0], s[1], r, 1});
+    for (int r : {lo, hi}) c.push_back(ga_tuning{s[0], s[1], r, 1, 0});
+  for (int regs : {168, 128})
+    for (int ppb : {4, 8})
+      for (int r : {lo, hi}) c.push_back(ga_tuning{8, ppb, r, 1, regs});
   return c;
 }
 
@@ -83,10 +89,10 @@ std::vector<ga_tuning> candidates(int rows) {
 extern "C" int ga_tuning_get(int W, int O, int k, ga_tuning* out) {
   if (!out || bad_wok(W, O, k)) return GA_EINVAL;
   if (ga::stored_tuning(W, O, k, out)) return GA_OK;
-  int G, ppb, entries, lpt;
-  if (ga::default_tuning(W, O, k, &G, &ppb, &entries, &lpt) != cudaSuccess) return GA_ECUDA;
+  int G, ppb, entries, lpt, regs;
+  if (ga::default_tuning(W, O, k, &G, &ppb, &entries, &lpt, &regs) != cudaSuccess) return GA_ECUDA;
   *out = ga_tuning{G, ppb, ga::table_rows_for(G, W, O, entries, ga::band_top_for(O) >= 0),
-                   lpt ? 1 : -1};
+                   lpt ? 1 : -1, regs};
   return GA_OK;
 }
 
@@ -117,20 +123,51 @@ extern "C" int ga_autotune_workspace_size(uint32_t n_pairs, int W, int O, int k,
   return GA_OK;
 }
 
-extern "C" int ga_autotune(const uint8_t* d_reads, const uint64_t* d_read_off,
-                           const uint32_t* d_read_len, const uint8_t* d_refs,
-                           const uint64_t* d_ref_off, const uint32_t* d_ref_len, uint32_t n_pairs,
-                           int W, int O, int k, int32_t* d_dist, int32_t* d_status,
-                           int32_t* d_ref_consumed, uint32_t* d_cigar, const uint64_t* d_cigar_off,
-                           uint32_t* d_n_runs, uint32_t* d_n_windows, uint64_t* d_cells,
-                           void* d_workspace, size_t ws_bytes, ga_tuning* best, float* best_ms,
-                           ga_stream_t stream) {
+namespace {
+
+// One alignment of the batch: the anchored form (start_span == nullptr) or
+// the free-start form, with an explicit tuning (nullptr: the stored one).
+int align_once(const uint8_t* d_reads, const uint64_t* d_read_off, const uint32_t* d_read_len,
+               const uint8_t* d_refs, const uint64_t* d_ref_off, const uint32_t* d_ref_len,
+               uint32_t n_pairs, int W, int O, int k, const uint32_t* d_start_span,
+               int32_t* d_ref_start, int32_t* d_dist, int32_t* d_status, int32_t* d_ref_consumed,
+               uint32_t* d_cigar, const uint64_t* d_cigar_off, uint32_t* d_n_runs,
+               uint32_t* d_n_windows, uint64_t* d_cells, void* d_workspace, size_t ws_bytes,
+               const ga_tuning* t, ga_stream_t stream) {
+  if (d_start_span)
+    return ga_align_batch_locate_tuned(d_reads, d_read_off, d_read_len, d_refs, d_ref_off,
+                                       d_ref_len, n_pairs, W, O, k, d_start_span, d_ref_start,
+                                       d_dist, d_status, d_ref_consumed, d_cigar, d_cigar_off,
+                                       d_n_runs, d_n_windows, d_cells, d_workspace, ws_bytes, t,
+                                       stream);
+  return ga_align_batch_tuned(d_reads, d_read_off, d_read_len, d_refs, d_ref_off, d_ref_len,
+                              n_pairs, W, O, k, d_dist, d_status, d_ref_consumed, d_cigar,
+                              d_cigar_off, d_n_runs, d_n_windows, d_cells, d_workspace, ws_bytes, t,
+                              stream);
+}
+
+int workspace_for(uint32_t n_pairs, int W, int O, int k, const ga_tuning* t, bool locate,
+                  size_t* need) {
+  return locate ? ga_workspace_size_locate(n_pairs, W, O, k, t, need)
+                : ga_workspace_size_tuned(n_pairs, W, O, k, t, need);
+}
+
+int autotune(const uint8_t* d_reads, const uint64_t* d_read_off, const uint32_t* d_read_len,
+             const uint8_t* d_refs, const uint64_t* d_ref_off, const uint32_t* d_ref_len,
+             uint32_t n_pairs, int W, int O, int k, const uint32_t* d_start_span,
+             int32_t* d_ref_start, int32_t* d_dist, int32_t* d_status, int32_t* d_ref_consumed,
+             uint32_t* d_cigar, const uint64_t* d_cigar_off, uint32_t* d_n_runs,
+             uint32_t* d_n_windows, uint64_t* d_cells, void* d_workspace, size_t ws_bytes,
+             ga_tuning* best, float* best_ms, ga_stream_t stream) {
   if (bad_wok(W, O, k) || n_pairs == 0 || !d_n_windows || !d_cells) return GA_EINVAL;
+  const bool locate = d_start_span != nullptr;
+  const int mode = locate ? 1 : 0;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   // 1. d_min estimate: run the current default once with statistics.
-  int rc = ga_align_batch(d_reads, d_read_off, d_read_len, d_refs, d_ref_off, d_ref_len, n_pairs, W,
-                          O, k, d_dist, d_status, d_ref_consumed, d_cigar, d_cigar_off, d_n_runs,
-                          d_n_windows, d_cells, d_workspace, ws_bytes, stream);
+  int rc = align_once(d_reads, d_read_off, d_read_len, d_refs, d_ref_off, d_ref_len, n_pairs, W, O,
+                      k, d_start_span, d_ref_start, d_dist, d_status, d_ref_consumed, d_cigar,
+                      d_cigar_off, d_n_runs, d_n_windows, d_cells, d_workspace, ws_bytes, nullptr,
+                      stream);
   if (rc != GA_OK) return rc;
   const uint32_t n_probe = std::min<uint32_t>(n_pairs, 4096);
   std::vector<uint32_t> nw(n_probe);
@@ -160,17 +197,16 @@ extern "C" int ga_autotune(const uint8_t* d_reads, const uint64_t* d_read_off,
   rc = GA_OK;
   for (const ga_tuning& c : candidates(rows)) {
     size_t need = 0;
-    if (ga_workspace_size_tuned(n_pairs, W, O, k, &c, &need) != GA_OK || need > ws_bytes) continue;
-    int r1 = ga_align_batch_tuned(d_reads, d_read_off, d_read_len, d_refs, d_ref_off, d_ref_len,
-                                  n_pairs, W, O, k, d_dist, d_status, d_ref_consumed, d_cigar,
-                                  d_cigar_off, d_n_runs, nullptr, nullptr, d_workspace, ws_bytes,
-                                  &c, stream);
+    if (workspace_for(n_pairs, W, O, k, &c, locate, &need) != GA_OK || need > ws_bytes) continue;
+    int r1 = align_once(d_reads, d_read_off, d_read_len, d_refs, d_ref_off, d_ref_len, n_pairs, W,
+                        O, k, d_start_span, d_ref_start, d_dist, d_status, d_ref_consumed, d_cigar,
+                        d_cigar_off, d_n_runs, nullptr, nullptr, d_workspace, ws_bytes, &c,
+                        stream);
     if (r1 != GA_OK) continue;
     cudaEventRecord(e0, s);
-    r1 = ga_align_batch_tuned(d_reads, d_read_off, d_read_len, d_refs, d_ref_off, d_ref_len,
-                              n_pairs, W, O, k, d_dist, d_status, d_ref_consumed, d_cigar,
-                              d_cigar_off, d_n_runs, nullptr, nullptr, d_workspace, ws_bytes, &c,
-                              stream);
+    r1 = align_once(d_reads, d_read_off, d_read_len, d_refs, d_ref_off, d_ref_len, n_pairs, W, O,
+                    k, d_start_span, d_ref_start, d_dist, d_status, d_ref_consumed, d_cigar,
+                    d_cigar_off, d_n_runs, nullptr, nullptr, d_workspace, ws_bytes, &c, stream);
     cudaEventRecord(e1, s);
     if (r1 != GA_OK || cudaEventSynchronize(e1) != cudaSuccess) {
       rc = GA_ECUDA;
@@ -187,10 +223,42 @@ extern "C" int ga_autotune(const uint8_t* d_reads, const uint64_t* d_read_off,
   cudaEventDestroy(e1);
   if (rc != GA_OK) return rc;
   if (best_t >= 1e30f) return GA_ENOSPC;  // no candidate fitted the workspace
-  ga::store_tuning(W, O, k, &best_c);
+  ga::store_tuning(W, O, k, &best_c, mode);
   if (best) *best = best_c;
   if (best_ms) *best_ms = best_t;
   return GA_OK;
+}
+
+}  // namespace
+
+extern "C" int ga_autotune(const uint8_t* d_reads, const uint64_t* d_read_off,
+                           const uint32_t* d_read_len, const uint8_t* d_refs,
+                           const uint64_t* d_ref_off, const uint32_t* d_ref_len, uint32_t n_pairs,
+                           int W, int O, int k, int32_t* d_dist, int32_t* d_status,
+                           int32_t* d_ref_consumed, uint32_t* d_cigar, const uint64_t* d_cigar_off,
+                           uint32_t* d_n_runs, uint32_t* d_n_windows, uint64_t* d_cells,
+                           void* d_workspace, size_t ws_bytes, ga_tuning* best, float* best_ms,
+                           ga_stream_t stream) {
+  return autotune(d_reads, d_read_off, d_read_len, d_refs, d_ref_off, d_ref_len, n_pairs, W, O, k,
+                  nullptr, nullptr, d_dist, d_status, d_ref_consumed, d_cigar, d_cigar_off,
+                  d_n_runs, d_n_windows, d_cells, d_workspace, ws_bytes, best, best_ms, stream);
+}
+
+extern "C" int ga_autotune_locate(const uint8_t* d_reads, const uint64_t* d_read_off,
+                                  const uint32_t* d_read_len, const uint8_t* d_refs,
+                                  const uint64_t* d_ref_off, const uint32_t* d_ref_len,
+                                  uint32_t n_pairs, int W, int O, int k,
+                                  const uint32_t* d_start_span, int32_t* d_ref_start,
+                                  int32_t* d_dist, int32_t* d_status, int32_t* d_ref_consumed,
+                                  uint32_t* d_cigar, const uint64_t* d_cigar_off,
+                                  uint32_t* d_n_runs, uint32_t* d_n_windows, uint64_t* d_cells,
+                                  void* d_workspace, size_t ws_bytes, ga_tuning* best,
+                                  float* best_ms, ga_stream_t stream) {
+  if (!d_start_span || !d_ref_start) return GA_EINVAL;
+  return autotune(d_reads, d_read_off, d_read_len, d_refs, d_ref_off, d_ref_len, n_pairs, W, O, k,
+                  d_start_span, d_ref_start, d_dist, d_status, d_ref_consumed, d_cigar,
+                  d_cigar_off, d_n_runs, d_n_windows, d_cells, d_workspace, ws_bytes, best,
+                  best_ms, stream);
 }
 
 // ---------------------------------------------------------------------------

@@ -106,16 +106,34 @@ class DeviceBatch:
         if getattr(self, "ref_start", None) is None or self.ref_start.numel() < n:
             self.ref_start = torch.empty(n, dtype=torch.int32, device=self.device)
 
-    def align_locate(self, start_span=None, stats: bool = True, stream=None):
+    def _grow_workspace(self, need: int):
+        if need > self.ws_bytes:
+            self.workspace = torch.empty(need, dtype=torch.uint8, device=self.device)
+            self.ws_bytes = need
+
+    def align_locate(self, start_span=None, stats: bool = True, stream=None, tuning=None):
         """The batched alignment with a free-start first window (ga_align_batch_locate):
         pair p may begin at any of its first start_span[p] reference bases (given
         here or by set_start_span); the starts land in ref_start."""
-        from . import ga_align_batch_locate
+        from . import ga_align_batch_locate_tuned, ga_workspace_size_locate
         if start_span is not None:
             self.set_start_span(start_span)
+        self._grow_workspace(ga_workspace_size_locate(self.n, self.W, self.O, self.k, tuning))
         a = self._args(stats)
-        ga_align_batch_locate(*a[:10], self.start_span, self.ref_start, *a[10:], self.workspace,
-                              self.ws_bytes, stream)
+        ga_align_batch_locate_tuned(*a[:10], self.start_span, self.ref_start, *a[10:],
+                                    self.workspace, self.ws_bytes, tuning, stream)
+
+    def autotune_locate(self, start_span=None, stream=None):
+        """ga_autotune_locate on this batch (packed first); its choice becomes the
+        free-start default. Returns (tuning, ms)."""
+        from . import ga_autotune_locate, ga_autotune_workspace_size
+        if start_span is not None:
+            self.set_start_span(start_span)
+        self._grow_workspace(ga_autotune_workspace_size(self.n, self.W, self.O, self.k))
+        self.pack(stream)
+        a = self._args(True)
+        return ga_autotune_locate(*a[:10], self.start_span, self.ref_start, *a[10:],
+                                  self.workspace, self.ws_bytes, stream)
 
     def align_order(self, tb_order: str, stats: bool = True, stream=None):
         """The batched alignment with another traceback priority order ("MSID" is
@@ -166,9 +184,14 @@ class DeviceBatch:
             self.workspace = torch.empty(need, dtype=torch.uint8, device=self.device)
             self.ws_bytes = need
         a = self._args(stats)
-        return ga_graph_create(self.ascii_reads if pack else None, self.ascii_reads.numel(),
-                               self.ascii_refs if pack else None, self.ascii_refs.numel(),
-                               *a, self.workspace, self.ws_bytes, tuning)
+        g = ga_graph_create(self.ascii_reads if pack else None, self.ascii_reads.numel(),
+                            self.ascii_refs if pack else None, self.ascii_refs.numel(),
+                            *a, self.workspace, self.ws_bytes, tuning)
+        # The graph holds raw addresses: keep every buffer it captured alive, even
+        # if this batch later replaces its workspace with a larger one.
+        g.buffers = (self.ascii_reads, self.ascii_refs, *[x for x in a if torch.is_tensor(x)],
+                     self.workspace)
+        return g
 
     # -- results ------------------------------------------------------------
     def results(self) -> "HostResult":

@@ -31,7 +31,7 @@ def oracle_dense(res) -> np.ndarray:
     return res.cigar[idx]
 
 
-def gpu_dense(db, a: int, b: int, torch, ga):
+def gpu_dense(db, a: int, b: int, torch, ga, with_start: bool = False):
     """Pairs a..b-1 of a DeviceBatch: per-pair fields and the compacted runs."""
     m = b - a
     dev = db.device
@@ -54,12 +54,14 @@ def gpu_dense(db, a: int, b: int, torch, ga):
         "runs": dense[:total].cpu().numpy().view(np.uint32),
         "run_off": doff.cpu().numpy(),
     }
+    if with_start:
+        out["ref_start"] = db.ref_start[a:b].cpu().numpy()
     return out
 
 
 def compare(got: dict, ref, a: int, label: str) -> None:
     """Element by element; the message names the first differing pairs."""
-    for name in FIELDS:
+    for name in FIELDS + (("ref_start",) if "ref_start" in got else ()):
         x = np.asarray(got[name]).astype(np.int64)
         y = np.asarray(getattr(ref, name)).astype(np.int64)
         bad = np.nonzero(x != y)[0]
@@ -84,12 +86,15 @@ def compare(got: dict, ref, a: int, label: str) -> None:
 
 
 def compare_batch(batch, db, torch, ga, W=64, O=24, k=64, chunk=25_000, label="",
-                  tb_order: str = "MSID") -> int:
+                  tb_order: str = "MSID", start_span=None) -> int:
     """Every pair of `batch` (aligned on the GPU into DeviceBatch `db`) against
-    the oracle. Returns the number of pairs compared."""
+    the oracle (with per-pair start spans for the free-start form). Returns the
+    number of pairs compared."""
     n = batch.n_pairs
     for a in range(0, n, chunk):
         b = min(n, a + chunk)
-        ref = oracle.align(batch.slice(a, b), W=W, O=O, k=k, tb_order=tb_order)
-        compare(gpu_dense(db, a, b, torch, ga), ref, a, f"{label} pairs {a}..{b - 1}")
+        spans = None if start_span is None else np.asarray(start_span)[a:b]
+        ref = oracle.align(batch.slice(a, b), W=W, O=O, k=k, tb_order=tb_order, start_span=spans)
+        compare(gpu_dense(db, a, b, torch, ga, with_start=spans is not None), ref, a,
+                f"{label} pairs {a}..{b - 1}")
     return n

@@ -32,7 +32,7 @@ from paper_2203_15561_gb300.pipeline import DeviceBatch  # noqa: E402
 WORKERS = min(16, len(os.sched_getaffinity(0)))
 
 
-def check_all_pairs(db, chunk=4096):
+def check_all_pairs(db, chunk=4096, with_start=False):
     n = db.n
     dev = db.device
     status = db.status[:n]
@@ -63,7 +63,10 @@ def check_all_pairs(db, chunk=4096):
         eq, x, ins, dl = sums[:, 7], sums[:, 8], sums[:, 1], sums[:, 2]
         read_len = db.read_len[a:b].to(torch.int64)
         torch.testing.assert_close(eq + x + ins, read_len)
-        torch.testing.assert_close(eq + x + dl, db.ref_consumed[a:b].to(torch.int64))
+        span = db.ref_consumed[a:b].to(torch.int64)
+        if with_start:  # the CIGAR spans ref_start .. ref_consumed
+            span = span - db.ref_start[a:b].to(torch.int64)
+        torch.testing.assert_close(eq + x + dl, span)
         torch.testing.assert_close(x + ins + dl, db.dist[a:b].to(torch.int64))
 
 
@@ -94,3 +97,20 @@ def test_full_workload_wide_windows():
     torch.cuda.synchronize()
     check_all_pairs(db)
     compare_batch(batch, db, torch, ga, W=128, O=48, k=128, label="workload 2, W = 128")
+
+
+@pytest.mark.parametrize("config", [2, 4])
+def test_full_workload_free_start(config):
+    # The free-start form as bench.py times it (start span ceil(n / 20), tuned by
+    # ga_autotune_locate), every pair against the oracle, the start included.
+    import numpy as np
+    batch = datagen.make_batch(config, workers=WORKERS)
+    spans = (batch.ref_len.astype(np.int64) + 19) // 20
+    db = DeviceBatch(batch)
+    db.autotune_locate(spans)
+    for t in (db.dist, db.status, db.ref_consumed, db.n_runs, db.n_windows, db.cells, db.ref_start):
+        t.fill_(-9)
+    db.align_locate(stats=True)
+    torch.cuda.synchronize()
+    check_all_pairs(db, with_start=True)
+    compare_batch(batch, db, torch, ga, label=f"workload {config}, free start", start_span=spans)

@@ -149,25 +149,33 @@ def test_error_cap(k):
         assert_same(b, run_gpu(b, kernel, k=k), ref, f"k{k}/{kernel}")
 
 
-TUNINGS = [(4, 8, 38, 1), (4, 8, 1, 1), (8, 4, 20, -1), (8, 4, 65, 1), (16, 4, 30, 1),
-           (32, 2, 36, -1), (8, 8, 2, 1), (32, 1, 65, 1), (32, 3, 10, 1), (16, 2, 3, 1),
-           (4, 16, 40, 1), (16, 16, 12, 1)]
+TUNINGS = [(4, 8, 38, 1, 0), (4, 8, 1, 1, 0), (8, 4, 20, -1, 0), (8, 4, 65, 1, 0),
+           (16, 4, 30, 1, 0), (32, 2, 36, -1, 0), (8, 8, 2, 1, 0), (32, 1, 65, 1, 0),
+           (32, 3, 10, 1, 0), (16, 2, 3, 1, 0), (4, 16, 40, 1, 0), (16, 16, 12, 1, 0),
+           (8, 8, 16, 1, 168), (8, 4, 39, 1, 128), (8, 8, 3, -1, 128)]
 
 
-@pytest.mark.parametrize("G,ppb,rows,lpt", TUNINGS)
-def test_tunings_identical(G, ppb, rows, lpt):
+@pytest.mark.parametrize("G,ppb,rows,lpt,regs", TUNINGS)
+def test_tunings_identical(G, ppb, rows, lpt, regs):
     b = datagen.make_batch(4, pair_ids=range(40))
     ref = oracle.align(b)
-    t = ga.ga_tuning(G, ppb, rows, lpt)
-    assert_same(b, run_gpu(b, "batched", tuning=t), ref, f"G{G}/ppb{ppb}/rows{rows}")
+    t = ga.ga_tuning(G, ppb, rows, lpt, regs)
+    assert_same(b, run_gpu(b, "batched", tuning=t), ref, f"G{G}/ppb{ppb}/rows{rows}/regs{regs}")
 
 
-@pytest.mark.parametrize("G,ppb,rows,lpt", TUNINGS[:6])
-def test_tunings_edge_cases(G, ppb, rows, lpt):
+@pytest.mark.parametrize("G,ppb,rows,lpt,regs", TUNINGS[:6] + TUNINGS[-3:])
+def test_tunings_edge_cases(G, ppb, rows, lpt, regs):
     b = datagen.from_pairs(edge_pairs(seed=G * 10 + ppb, n_random=100))
     ref = oracle.align(b, k=40)
-    t = ga.ga_tuning(G, ppb, rows, lpt)
+    t = ga.ga_tuning(G, ppb, rows, lpt, regs)
     assert_same(b, run_gpu(b, "batched", k=40, tuning=t), ref, f"edge G{G}/ppb{ppb}/rows{rows}")
+
+
+def test_register_capped_tuning_rejected_for_other_lane_counts():
+    b = datagen.make_batch(1, pair_ids=range(4))
+    with pytest.raises(ga.GenasmError) as e:
+        run_gpu(b, "batched", tuning=ga.ga_tuning(16, 4, 20, 1, 168))
+    assert e.value.code == ga.GA_EINVAL
 
 
 @pytest.mark.parametrize("config,ids", [(2, range(0, 24)), (3, range(100, 130)), (4, range(1000, 1060))])
