@@ -127,6 +127,12 @@ int ga_workspace_size(uint32_t n_pairs, int W, int O, int k, size_t* bytes_out);
  *                    lanes_per_pair 8) = a variant capped at that many
  *                    registers per thread, so that more blocks fit an SM
  *                    when the tables are small.
+ *   slice_windows  : pairs take turns of this many windows through a FIFO
+ *                    queue (their window state is saved between turns), so
+ *                    that all pairs finish together instead of the last
+ *                    ones running alone; -1 = off (a pair runs to its end);
+ *                    0 = automatic (turns of 32 windows when the pairs
+ *                    outnumber the resident groups, but less than 16 times).
  */
 typedef struct ga_tuning_s {
   int lanes_per_pair;
@@ -134,6 +140,7 @@ typedef struct ga_tuning_s {
   int table_rows;
   int lpt;
   int max_registers;
+  int slice_windows;
 } ga_tuning;
 
 /*

@@ -54,7 +54,8 @@ class GenasmError(RuntimeError):
 class ga_tuning(ctypes.Structure):
     _fields_ = [("lanes_per_pair", ctypes.c_int),
                 ("pairs_per_block", ctypes.c_int), ("table_rows", ctypes.c_int),
-                ("lpt", ctypes.c_int), ("max_registers", ctypes.c_int)]
+                ("lpt", ctypes.c_int), ("max_registers", ctypes.c_int),
+                ("slice_windows", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         return {name: int(getattr(self, name)) for name, _ in self._fields_}

@@ -216,16 +216,68 @@ cudaError_t launch_plain(const AlignParams& p, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 // Batched: persistent blocks of `pairs_per_block` groups of G lanes (each
 // lane a strip of 64/G text columns). Each group pulls pairs from a device
-// counter; with LPT the counter indexes a longest-read-first permutation
-// built by a counting sort.
+// queue; with LPT the queue starts in longest-read-first order (a counting
+// sort).
+//
+// Sliced form (slice > 0): the queue is a FIFO of pairs, and a group runs a
+// pair for at most `slice` windows, saves its window state (positions, edit
+// count, statistics, open CIGAR run) and puts it back at the tail. Every
+// pair then moves forward at the same pace, and the pairs finish within about
+// one slice of each other: a batch whose pairs outnumber the resident groups
+// but not by a whole multiple no longer ends with a round in which a few
+// groups run alone (10,000 equal pairs on 4,864 groups: three pair lengths
+// without slices, about 2.06 with them). Pushing is lock-free: a producer
+// takes a tail position with atomicAdd, writes the pair into the ring slot
+// and then publishes the slot with its sequence number (position + 1); a
+// consumer claims the head position with atomicCAS once its slot carries the
+// head's sequence number. A group that finds the head unpublished stops
+// (the queue is empty: every pair still unfinished is held by a group, which
+// takes it back itself), so no group ever waits.
 // ---------------------------------------------------------------------------
 
 struct BatchArgs {
-  uint32_t* queue;
-  const uint32_t* order;  // nullptr: index order
+  uint32_t* queue;        // [0] hand-out counter (unsliced), [1] ring head, [2] ring tail
+  uint32_t* order;        // hand-out order / the ring's slots (nullptr: index order, unsliced)
   uint64_t* spill;        // [groups][kMaxRows * kMaxStride]
   int table_entries;
+  uint32_t slice;         // windows per turn (0: a pair runs to its end)
+  uint32_t* ring_seq;     // per ring slot: the position it holds + 1
+  SlotState* state;       // per pair: saved window state (all zero: not started)
 };
+
+constexpr uint32_t kNoPair = 0xffffffffu;
+
+// Takes the pair at the ring's head, or kNoPair when the head slot is not
+// published (nothing waiting) or the claim keeps losing races.
+__device__ __forceinline__ uint32_t ring_pop(const BatchArgs& a, uint32_t n) {
+  volatile uint32_t* head = a.queue + 1;
+  volatile uint32_t* seq = a.ring_seq;
+  volatile uint32_t* slot = a.order;
+  for (int tries = 0; tries < 1024; ++tries) {
+    const uint32_t h = *head;
+    const uint32_t x = h % n;
+    if (seq[x] != h + 1u) return kNoPair;
+    __threadfence();
+    const uint32_t pair = slot[x];
+    if (atomicCAS(a.queue + 1, h, h + 1u) == h) {
+      __threadfence();
+      return pair;
+    }
+  }
+  return kNoPair;
+}
+
+// Puts a pair (its state already saved) at the ring's tail.
+__device__ __forceinline__ void ring_push(const BatchArgs& a, uint32_t n, uint32_t pair) {
+  __threadfence();  // the saved state before the publication
+  const uint32_t t = atomicAdd(a.queue + 2, 1u);
+  const uint32_t x = t % n;
+  volatile uint32_t* slot = a.order;
+  volatile uint32_t* seq = a.ring_seq;
+  slot[x] = pair;
+  __threadfence();
+  seq[x] = t + 1u;
+}
 
 constexpr int kSpillEntries = kMaxRows * kMaxStride;
 
@@ -248,18 +300,52 @@ __global__ void __launch_bounds__(256) __maxnreg__(R)
   PairState st;
   st.busy = false;
   bool drained = false;
+  uint32_t budget = 0;
   for (;;) {
     // Groups without a pair take the next one from the queue.
     const bool want = !st.busy && !drained;
-    uint32_t idx = 0xffffffffu;
-    if (want && r == 0) idx = atomicAdd(a.queue, 1u);
-    idx = __shfl_sync(kFull, idx, gbase);
+    uint32_t pair = kNoPair;
+    if (want && r == 0) {
+      if (a.slice) {
+        pair = ring_pop(a, p.n_pairs);
+      } else {
+        const uint32_t idx = atomicAdd(a.queue, 1u);
+        if (idx < p.n_pairs) pair = a.order ? a.order[idx] : idx;
+      }
+    }
+    pair = __shfl_sync(kFull, pair, gbase);
     if (want) {
-      if (idx < p.n_pairs) begin_pair(p, a.order ? a.order[idx] : idx, st, r == 0);
-      else drained = true;
+      if (pair != kNoPair) {
+        begin_pair(p, pair, st, r == 0);
+        if (a.slice) {
+          // Another SM may have saved this state: read it from L2, not L1.
+          const SlotState* sp = a.state + pair;
+          SlotState s;
+          s.pos_p = __ldcg(&sp->pos_p);
+          s.pos_t = __ldcg(&sp->pos_t);
+          s.edits = __ldcg(&sp->edits);
+          s.windows = __ldcg(&sp->windows);
+          s.cells = __ldcg(reinterpret_cast<const unsigned long long*>(&sp->cells));
+          s.runs = __ldcg(&sp->runs);
+          s.run_op = __ldcg(&sp->run_op);
+          s.run_len = __ldcg(&sp->run_len);
+          if (s.windows > 0) resume_pair(s, st);  // a pair that had turns already
+          budget = a.slice;
+        }
+      } else {
+        drained = true;
+      }
     }
     if (!__any_sync(kFull, st.busy || !drained)) break;
     if (__any_sync(kFull, st.busy)) step_window<G>(p, r, gbase, st, gs, table, a.table_entries, spill);
+    // End of a turn: the pair goes back to the queue's tail.
+    if (a.slice && st.busy && --budget == 0) {
+      if (r == 0) {
+        save_pair(st, a.state[st.pair]);
+        ring_push(a, p.n_pairs, st.pair);
+      }
+      st.busy = false;
+    }
   }
 }
 
@@ -346,6 +432,16 @@ static void variant_launch(int G, int R, int blocks, int threads, size_t smem, c
 
 int band_top_for(int O) { return O >= 16 ? std::min(22, O - 1) : -1; }
 
+// Windows per turn of the sliced queue: the plan's choice, else slices of 32
+// windows when the pairs outnumber the resident groups less than 16 times
+// over (more pairs than that leave a tail of under a sixteenth of a round).
+uint32_t slice_for(uint32_t n_pairs, const BatchPlan& plan) {
+  if (plan.slice_windows < 0) return 0u;
+  if (plan.slice_windows > 0) return static_cast<uint32_t>(plan.slice_windows);
+  const uint64_t groups = static_cast<uint64_t>(plan.blocks) * plan.pairs_per_block;
+  return n_pairs > groups && n_pairs < 16 * groups ? 32u : 0u;
+}
+
 int table_entries_for(int G, int W, int O, int rows, bool band) {
   const int ncols = W - O + 1;
   return band ? std::max((rows * band_stride(G, ncols) + 1) / 2, kPmCols)
@@ -358,7 +454,7 @@ int table_rows_for(int G, int W, int O, int entries, bool band) {
 }
 
 cudaError_t default_tuning(int W, int O, int k, int* G, int* ppb, int* table_entries, int* lpt,
-                           int* max_registers, int mode) {
+                           int* max_registers, int* slice_windows, int mode) {
   const bool band = band_top_for(O) >= 0;
   ga_tuning t;
   if (stored_tuning(W, O, k, &t, mode)) {  // chosen by an autotuner or set by ga_tuning_set
@@ -367,6 +463,7 @@ cudaError_t default_tuning(int W, int O, int k, int* G, int* ppb, int* table_ent
     *table_entries = table_entries_for(*G, W, O, t.table_rows, band);
     *lpt = t.lpt >= 0 ? 1 : 0;
     *max_registers = t.max_registers;
+    *slice_windows = t.slice_windows;
     return cudaSuccess;
   }
   *G = 8;
@@ -375,11 +472,12 @@ cudaError_t default_tuning(int W, int O, int k, int* G, int* ppb, int* table_ent
   *table_entries = table_entries_for(*G, W, O, 39, band);
   *lpt = 1;
   *max_registers = 0;
+  *slice_windows = 0;
   return cudaSuccess;
 }
 
 cudaError_t resolve_plan(int W, int O, int k, int G, int ppb, int table_entries, int lpt,
-                         bool band, BatchPlan* plan, int max_registers) {
+                         bool band, BatchPlan* plan, int max_registers, int slice_windows) {
   (void)W;
   (void)k;
   if (!batch_variant_exists(G, max_registers)) return cudaErrorInvalidValue;
@@ -403,6 +501,7 @@ cudaError_t resolve_plan(int W, int O, int k, int G, int ppb, int table_entries,
   if ((e = variant_setup(G, cap_of(max_registers), threads, smem, &per_sm)) != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   plan->max_registers = max_registers;
+  plan->slice_windows = slice_windows;
   plan->lanes_per_pair = G;
   plan->pairs_per_block = ppb;
   plan->table_entries = table_entries;
@@ -423,6 +522,17 @@ cudaError_t launch_lpt_order(const uint32_t* read_len, uint32_t n, uint32_t* his
   return cudaGetLastError();
 }
 
+// The ring of the sliced queue starts full: slot x holds hand-out position x
+// (the LPT order, or pair x), published with sequence number x + 1.
+__global__ void ring_init_kernel(uint32_t n, bool identity, uint32_t* __restrict__ slot,
+                                 uint32_t* __restrict__ seq, uint32_t* __restrict__ tail) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) *tail = n;  // the ring starts full
+  for (uint32_t x = blockIdx.x * blockDim.x + threadIdx.x; x < n; x += gridDim.x * blockDim.x) {
+    if (identity) slot[x] = x;
+    seq[x] = x + 1u;
+  }
+}
+
 WorkspaceLayout workspace_layout(uint32_t n_pairs, const BatchPlan& plan) {
   auto up = [](size_t x) { return (x + 255) & ~static_cast<size_t>(255); };
   WorkspaceLayout L{};
@@ -430,7 +540,9 @@ WorkspaceLayout workspace_layout(uint32_t n_pairs, const BatchPlan& plan) {
   L.hist = up(L.queue + 256);
   L.order = up(L.hist + sizeof(uint32_t) * kLptBuckets);
   L.locate = up(L.order + sizeof(uint32_t) * static_cast<size_t>(n_pairs));
-  L.spill = up(L.locate + sizeof(int32_t) * static_cast<size_t>(n_pairs));
+  L.ring_seq = up(L.locate + sizeof(int32_t) * static_cast<size_t>(n_pairs));
+  L.state = up(L.ring_seq + sizeof(uint32_t) * static_cast<size_t>(n_pairs));
+  L.spill = up(L.state + sizeof(SlotState) * static_cast<size_t>(n_pairs));
   const size_t groups = static_cast<size_t>(plan.blocks) * plan.pairs_per_block;
   L.total = up(L.spill + groups * sizeof(uint64_t) * kSpillEntries);
   return L;
@@ -448,8 +560,18 @@ cudaError_t launch_batched(const AlignParams& p, const BatchPlan& plan, void* ws
   if (e != cudaSuccess) return e;
   if (plan.lpt && (e = launch_lpt_order(p.read_len, p.n_pairs, hist, order, s)) != cudaSuccess)
     return e;
-  BatchArgs a{queue, plan.lpt ? order : nullptr,
-              spill_area ? reinterpret_cast<uint64_t*>(w + L.spill) : nullptr, plan.table_entries};
+  const uint32_t slice = spill_area ? slice_for(p.n_pairs, plan) : 0u;
+  uint32_t* ring_seq = reinterpret_cast<uint32_t*>(w + L.ring_seq);
+  SlotState* state = reinterpret_cast<SlotState*>(w + L.state);
+  if (slice) {
+    if ((e = cudaMemsetAsync(state, 0, sizeof(SlotState) * p.n_pairs, s)) != cudaSuccess) return e;
+    const int blocks = static_cast<int>(std::min<uint32_t>((p.n_pairs + 255) / 256, 1024u));
+    ring_init_kernel<<<blocks, 256, 0, s>>>(p.n_pairs, !plan.lpt, order, ring_seq, queue + 2);
+    count_launches(1);
+  }
+  BatchArgs a{queue, (plan.lpt || slice) ? order : nullptr,
+              spill_area ? reinterpret_cast<uint64_t*>(w + L.spill) : nullptr, plan.table_entries,
+              slice, ring_seq, state};
   const int threads = plan.pairs_per_block * plan.lanes_per_pair;
   AlignParams q = p;
   q.band_top = plan.band_top;
@@ -668,31 +790,6 @@ cudaError_t launch_batched_locate(const AlignParams& p, const BatchPlan& plan,
 
 namespace ga {
 
-__device__ __forceinline__ void resume_pair(const AlignParams& p, uint32_t slot,
-                                            const SlotState& s, PairState& st, bool writer) {
-  begin_pair(p, slot, st, writer);  // a fresh slot (all zero) starts here
-  if (!st.busy) return;             // empty read: already finished
-  st.pos_p = s.pos_p;
-  st.pos_t = s.pos_t;
-  st.edits = s.edits;
-  st.windows = s.windows;
-  st.cells = s.cells;
-  st.rw.n = s.runs;
-  st.rw.op = s.run_op;
-  st.rw.len = s.run_len;
-}
-
-__device__ __forceinline__ void save_pair(const PairState& st, SlotState& s) {
-  s.pos_p = st.pos_p;
-  s.pos_t = st.pos_t;
-  s.edits = st.edits;
-  s.windows = st.windows;
-  s.cells = st.cells;
-  s.runs = st.rw.n;
-  s.run_op = st.rw.op;
-  s.run_len = st.rw.len;
-}
-
 template <int G>
 __global__ void __launch_bounds__(256, 1) align_step_kernel(const AlignParams p, const StepArgs a) {
   extern __shared__ __align__(16) uint64_t smem[];
@@ -719,7 +816,8 @@ __global__ void __launch_bounds__(256, 1) align_step_kernel(const AlignParams p,
     if (want) {
       if (idx < a.n_active) {
         slot = a.active[idx];
-        resume_pair(p, slot, a.state[slot], st, r == 0);
+        begin_pair(p, slot, st, r == 0);  // a fresh slot (all zero) starts here
+        if (st.busy) resume_pair(a.state[slot], st);
         budget = a.max_windows;
         finished = !st.busy;
       } else {

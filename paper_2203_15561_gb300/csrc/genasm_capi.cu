@@ -65,8 +65,8 @@ int fill_params(const uint8_t* d_reads, const uint64_t* d_read_off, const uint32
 }
 
 int resolve(int W, int O, int k, const ga_tuning* t, ga::BatchPlan* plan, int mode = 0) {
-  int G = 0, ppb = 0, entries = 0, lpt = 1, regs = 0;
-  cudaError_t e = ga::default_tuning(W, O, k, &G, &ppb, &entries, &lpt, &regs, mode);
+  int G = 0, ppb = 0, entries = 0, lpt = 1, regs = 0, slice = 0;
+  cudaError_t e = ga::default_tuning(W, O, k, &G, &ppb, &entries, &lpt, &regs, &slice, mode);
   if (e != cudaSuccess) return cuda_fail(e);
   if (t) {
     if (t->lanes_per_pair) G = t->lanes_per_pair;
@@ -74,11 +74,12 @@ int resolve(int W, int O, int k, const ga_tuning* t, ga::BatchPlan* plan, int mo
     if (t->table_rows) entries = ga::table_entries_for(G, W, O, t->table_rows, ga::band_top_for(O) >= 0);
     if (t->lpt) lpt = t->lpt > 0 ? 1 : 0;
     regs = t->max_registers;
+    slice = t->slice_windows;
     if (!ga::batch_variant_exists(G, regs) || ppb < 1 || ppb * G > 256 || (ppb * G) % 32 != 0 ||
-        t->table_rows < 0)
+        t->table_rows < 0 || slice < -1)
       return GA_EINVAL;
   }
-  e = ga::resolve_plan(W, O, k, G, ppb, entries, lpt, true, plan, regs);
+  e = ga::resolve_plan(W, O, k, G, ppb, entries, lpt, true, plan, regs, slice);
   if (e == cudaErrorInvalidValue || e == cudaErrorInvalidConfiguration) {
     cudaGetLastError();
     return GA_EINVAL;

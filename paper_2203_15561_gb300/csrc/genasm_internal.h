@@ -54,6 +54,7 @@ struct BatchPlan {
   int blocks;           // persistent grid size
   size_t smem_bytes;    // dynamic shared memory per block
   int max_registers;    // register cap of the kernel variant (0: none)
+  int slice_windows;    // windows per turn of the sliced queue (0: automatic, -1: off)
 };
 
 // Workspace layout of the batched kernel (byte offsets).
@@ -62,6 +63,8 @@ struct WorkspaceLayout {
   size_t hist;    // uint32[kLptBuckets]
   size_t order;   // uint32[n_pairs]
   size_t locate;  // int32[n_pairs]: the locate step's edit counts
+  size_t ring_seq;  // uint32[n_pairs]: sequence numbers of the sliced queue's ring
+  size_t state;   // SlotState[n_pairs]: window state of pairs between turns
   size_t spill;   // uint64[groups][kMaxRows * kMaxCols]
   size_t total;
 };
@@ -148,10 +151,11 @@ cudaError_t launch_batched_locate(const AlignParams& p, const BatchPlan& plan,
 // `mode`, else the library's); fills G / pairs per block / table entries /
 // lpt / register cap. Returns cudaSuccess or the device query error.
 cudaError_t default_tuning(int W, int O, int k, int* G, int* ppb, int* table_entries, int* lpt,
-                           int* max_registers, int mode = 0);
+                           int* max_registers, int* slice_windows, int mode = 0);
 bool batch_variant_exists(int G, int max_registers = 0);
 cudaError_t resolve_plan(int W, int O, int k, int G, int ppb, int table_entries, int lpt,
-                         bool band, BatchPlan* plan, int max_registers = 0);
+                         bool band, BatchPlan* plan, int max_registers = 0, int slice_windows = 0);
+uint32_t slice_for(uint32_t n_pairs, const BatchPlan& plan);
 
 // Band tables (32-bit entries around the diagonal) are used for windows that
 // are not the last when O >= 16, with offset A = min(22, O - 1). Table sizes

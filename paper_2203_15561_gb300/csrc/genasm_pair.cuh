@@ -76,4 +76,28 @@ __device__ __forceinline__ void begin_pair(const AlignParams& p, uint32_t pair, 
   if (st.m == 0) finish_pair(p, st, writer);  // empty read: nothing to align
 }
 
+// Restores a pair's saved window state (a pair resumed by the sliced queue
+// or the serving step), after begin_pair.
+__device__ __forceinline__ void resume_pair(const SlotState& s, PairState& st) {
+  st.pos_p = s.pos_p;
+  st.pos_t = s.pos_t;
+  st.edits = s.edits;
+  st.windows = s.windows;
+  st.cells = s.cells;
+  st.rw.n = s.runs;
+  st.rw.op = s.run_op;
+  st.rw.len = s.run_len;
+}
+
+__device__ __forceinline__ void save_pair(const PairState& st, SlotState& s) {
+  s.pos_p = st.pos_p;
+  s.pos_t = st.pos_t;
+  s.edits = st.edits;
+  s.windows = st.windows;
+  s.cells = st.cells;
+  s.runs = st.rw.n;
+  s.run_op = st.rw.op;
+  s.run_len = st.rw.len;
+}
+
 }  // namespace ga

@@ -72,15 +72,18 @@ int bad_wok(int W, int O, int k) {
 // the register-capped variants (which pay off when small tables leave room
 // for more blocks per SM).
 std::vector<ga_tuning> candidates(int rows) {
+  // `rows` is the mean d_min + 1; windows whose d_min does not fit are redone in
+  // global memory, so larger tables that cover the tail of d_min are tried too.
   const int lo = std::min(65, std::max(4, rows + 5));
   const int hi = std::min(65, std::max(6, rows + 8));
+  const int tail = std::min(65, std::max(8, rows + 16));
   std::vector<ga_tuning> c;
   const int shapes[][2] = {{4, 8}, {4, 16}, {8, 4}, {8, 8}, {16, 2}, {16, 4}, {32, 1}, {32, 2}};
   for (const auto& s : shapes)
-    for (int r : {lo, hi}) c.push_back(ga_tuning{s[0], s[1], r, 1, 0});
+    for (int r : {lo, hi, tail}) c.push_back(ga_tuning{s[0], s[1], r, 1, 0, 0});
   for (int regs : {168, 128})
     for (int ppb : {4, 8})
-      for (int r : {lo, hi}) c.push_back(ga_tuning{8, ppb, r, 1, regs});
+      for (int r : {lo, hi, tail}) c.push_back(ga_tuning{8, ppb, r, 1, regs, 0});
   return c;
 }
 
@@ -89,10 +92,11 @@ std::vector<ga_tuning> candidates(int rows) {
 extern "C" int ga_tuning_get(int W, int O, int k, ga_tuning* out) {
   if (!out || bad_wok(W, O, k)) return GA_EINVAL;
   if (ga::stored_tuning(W, O, k, out)) return GA_OK;
-  int G, ppb, entries, lpt, regs;
-  if (ga::default_tuning(W, O, k, &G, &ppb, &entries, &lpt, &regs) != cudaSuccess) return GA_ECUDA;
+  int G, ppb, entries, lpt, regs, slice;
+  if (ga::default_tuning(W, O, k, &G, &ppb, &entries, &lpt, &regs, &slice) != cudaSuccess)
+    return GA_ECUDA;
   *out = ga_tuning{G, ppb, ga::table_rows_for(G, W, O, entries, ga::band_top_for(O) >= 0),
-                   lpt ? 1 : -1, regs};
+                   lpt ? 1 : -1, regs, slice};
   return GA_OK;
 }
 

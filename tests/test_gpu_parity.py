@@ -153,22 +153,42 @@ TUNINGS = [(4, 8, 38, 1, 0), (4, 8, 1, 1, 0), (8, 4, 20, -1, 0), (8, 4, 65, 1, 0
            (16, 4, 30, 1, 0), (32, 2, 36, -1, 0), (8, 8, 2, 1, 0), (32, 1, 65, 1, 0),
            (32, 3, 10, 1, 0), (16, 2, 3, 1, 0), (4, 16, 40, 1, 0), (16, 16, 12, 1, 0),
            (8, 8, 16, 1, 168), (8, 4, 39, 1, 128), (8, 8, 3, -1, 128)]
+TUNINGS = [t + (0,) for t in TUNINGS]
+# The sliced queue: turns of 1, 2 or 3 windows (many pushes and pops), forced
+# off, with and without the longest-first order.
+SLICED = [(8, 8, 39, 1, 0, 1), (8, 8, 39, -1, 0, 2), (4, 8, 38, 1, 0, 3), (16, 4, 30, 1, 0, 1),
+          (32, 2, 36, -1, 0, 2), (8, 4, 20, 1, 168, 1), (8, 8, 39, 1, 0, -1)]
 
 
-@pytest.mark.parametrize("G,ppb,rows,lpt,regs", TUNINGS)
-def test_tunings_identical(G, ppb, rows, lpt, regs):
+@pytest.mark.parametrize("G,ppb,rows,lpt,regs,slice_", TUNINGS + SLICED)
+def test_tunings_identical(G, ppb, rows, lpt, regs, slice_):
     b = datagen.make_batch(4, pair_ids=range(40))
     ref = oracle.align(b)
-    t = ga.ga_tuning(G, ppb, rows, lpt, regs)
-    assert_same(b, run_gpu(b, "batched", tuning=t), ref, f"G{G}/ppb{ppb}/rows{rows}/regs{regs}")
+    t = ga.ga_tuning(G, ppb, rows, lpt, regs, slice_)
+    assert_same(b, run_gpu(b, "batched", tuning=t), ref,
+                f"G{G}/ppb{ppb}/rows{rows}/regs{regs}/slice{slice_}")
 
 
-@pytest.mark.parametrize("G,ppb,rows,lpt,regs", TUNINGS[:6] + TUNINGS[-3:])
-def test_tunings_edge_cases(G, ppb, rows, lpt, regs):
+@pytest.mark.parametrize("G,ppb,rows,lpt,regs,slice_", TUNINGS[:6] + TUNINGS[-3:] + SLICED)
+def test_tunings_edge_cases(G, ppb, rows, lpt, regs, slice_):
     b = datagen.from_pairs(edge_pairs(seed=G * 10 + ppb, n_random=100))
     ref = oracle.align(b, k=40)
-    t = ga.ga_tuning(G, ppb, rows, lpt, regs)
+    t = ga.ga_tuning(G, ppb, rows, lpt, regs, slice_)
     assert_same(b, run_gpu(b, "batched", k=40, tuning=t), ref, f"edge G{G}/ppb{ppb}/rows{rows}")
+
+
+@pytest.mark.parametrize("slice_", [0, 1, 2])
+def test_sliced_queue_more_pairs_than_groups(slice_):
+    # 12,000 short pairs (about three windows each) and 400 mixed-length ones:
+    # more pairs than resident groups, so the ring wraps around and cycles through
+    # pushes and pops at every turn length (0: the automatic choice).
+    b = datagen.make_batch(1, n_pairs=12_000)
+    mixed = datagen.make_batch(4, pair_ids=range(300, 700))
+    b = datagen.from_pairs([(b.read(p), b.ref(p)) for p in range(b.n_pairs)] +
+                           [(mixed.read(p), mixed.ref(p)) for p in range(mixed.n_pairs)])
+    ref = oracle.align(b)
+    t = ga.ga_tuning(8, 8, 39, 1, 0, slice_)
+    assert_same(b, run_gpu(b, "batched", tuning=t), ref, f"mixed / slice {slice_}")
 
 
 def test_register_capped_tuning_rejected_for_other_lane_counts():
