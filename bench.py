@@ -60,8 +60,10 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     ap.add_argument("--workers", type=int, default=0, help="processes for input generation")
-    ap.add_argument("--serve-seconds", type=float, default=10.0,
-                    help="seconds of Poisson arrivals for the serving leg (workload 5 runs 60)")
+    ap.add_argument("--serve-seconds", type=float, default=60.0,
+                    help="seconds of Poisson arrivals for the serving leg (workload 5: 60)")
+    ap.add_argument("--saturate-seconds", type=float, default=2.0,
+                    help="seconds of arrivals at ten times the rate (the server's capacity)")
     ap.add_argument("--plain-serve-seconds", type=float, default=1.0,
                     help="seconds of arrivals replayed through the plain per-request launch")
     ap.add_argument("--no-serve", action="store_true")
@@ -472,90 +474,126 @@ def _percentiles(lat_ms):
             "max_ms": float(a[-1])}
 
 
+POOL_PAIRS = 1 << 16
+
+
 def run_serving(args, dev):
     """Workload 5: open-loop Poisson arrivals at 2,000 requests/s, each 1-64
-    pairs of the workload-4 distribution (seed 5). The pairs come from a pool
-    of distinct pairs (request pair j is pool pair j mod P); every request is
-    copied into the server at submission, so reuse does not share work.
-    Latency = arrival -> result visible on the host."""
+    pairs of the workload-4 distribution (seed 5). Request pair j is pool pair
+    j mod 65,536 (the pool: 65,536 distinct pairs, about one second of
+    arrivals; drawing fresh pairs for all 60 s, about 3.9 M pairs and 31
+    Gbases, would take the input generator tens of minutes). Every request is
+    copied into the server at submission, so reuse shares no work. Latency =
+    arrival -> result visible on the host. Every served request is checked
+    against the oracle's result for its pool pairs (after the timed span).
+    A second span offers ten times the load (20,000 requests/s) to find the
+    server's capacity and its latency when saturated."""
     import ctypes
     import torch
+    import oracle
     import paper_2203_15561_gb300 as ga
     from paper_2203_15561_gb300 import datagen
 
-    pool_n = 8192
-    pool = datagen.make_batch(4, pair_ids=range(pool_n), seed=5,
+    pool = datagen.make_batch(4, pair_ids=range(POOL_PAIRS), seed=5,
                               workers=args.workers or min(16, host_cores()))
-    reqs = datagen.make_requests(2000.0, max(args.serve_seconds, args.plain_serve_seconds), seed=5)
-    arrivals = np.array([r.arrival_s for r in reqs])
-    ids = [np.asarray(r.pair_ids, dtype=np.int64) % pool_n for r in reqs]
-    meta = []
-    for q in ids:
-        meta.append([np.ascontiguousarray(pool.read_off[q]), np.ascontiguousarray(pool.read_len[q]),
-                     np.ascontiguousarray(pool.ref_off[q]), np.ascontiguousarray(pool.ref_len[q])])
     reads_p, refs_p = pool.reads.ctypes.data, pool.refs.ctypes.data
-
-    def request(i):
-        ro, rl, fo, fl = meta[i]
-        return ga.ga_request(len(ro), reads_p, ro.ctypes.data, rl.ctypes.data, refs_p,
-                             fo.ctypes.data, fl.ctypes.data, i)
-
-    # -- served (continuous batching) --
-    free, _ = torch.cuda.mem_get_info(dev)
-    budget = int(min(40 << 30, 0.6 * free))
-    srv = ga.ga_server_create(budget, W, O, K)
-    ga.ga_server_set_step_windows(srv, 48)
-    n_req = int(np.searchsorted(arrivals, args.serve_seconds))
-    lat, pairs, bases, steps = [], 0, 0, 0
-    launches0 = ga.ga_launch_count()
-    t0 = time.perf_counter()
-    nxt, done, inflight = 0, 0, 0
     f_poll = ga._typed("ga_server_poll", ga._i, [ga._vp, ctypes.POINTER(ga.ga_result), ga._i,
                                                  ctypes.POINTER(ga._i)])
-    buf = (ga.ga_result * 1024)()
-    nres = ga._i(0)
-    while done < n_req:
-        now = time.perf_counter() - t0
-        while nxt < n_req and arrivals[nxt] <= now:
-            ga.ga_server_submit(srv, request(nxt))
-            nxt += 1
-            inflight += 1
-        if inflight == 0:
-            time.sleep(max(0.0, arrivals[nxt] - (time.perf_counter() - t0)))
-            continue
-        ga.ga_server_step(srv)
-        steps += 1
-        while True:
-            f_poll(srv, buf, 1024, ctypes.byref(nres))
-            if nres.value == 0:
-                break
-            t = time.perf_counter() - t0
-            for q in range(nres.value):
-                r = buf[q]
-                lat.append(1e3 * (t - arrivals[r.tag]))
-                pairs += r.n_pairs
-                bases += int(meta[r.tag][1].sum())
-                ga.ga_server_release(srv, r.ticket)
-            done += nres.value
-            inflight -= nres.value
-    wall = time.perf_counter() - t0
-    server_launches = ga.ga_launch_count() - launches0
-    ga.ga_server_destroy(srv)
-    served = {"requests": n_req, "pairs": pairs, "read_bases": bases, "wall_s": wall,
-              "pairs_per_s": pairs / wall, "gbases_per_s": bases / wall / 1e9, "steps": steps,
-              "step_windows": 48, "budget_bytes": budget, "kernel_launches": server_launches,
-              **_percentiles(lat)}
+
+    def serve(rate, seconds, seed, check):
+        reqs = datagen.make_requests(rate, seconds, seed=seed)
+        arrivals = np.array([r.arrival_s for r in reqs])
+        ids = [np.asarray(r.pair_ids, dtype=np.int64) % POOL_PAIRS for r in reqs]
+        meta = [[np.ascontiguousarray(pool.read_off[q]), np.ascontiguousarray(pool.read_len[q]),
+                 np.ascontiguousarray(pool.ref_off[q]), np.ascontiguousarray(pool.ref_len[q])]
+                for q in ids]
+        free, _ = torch.cuda.mem_get_info(dev)
+        budget = int(min(40 << 30, 0.6 * free))
+        srv = ga.ga_server_create(budget, W, O, K)
+        ga.ga_server_set_step_windows(srv, 48)
+        n_req = len(reqs)
+        lat = np.zeros(n_req)
+        got = [None] * n_req if check else None
+        pairs = bases = steps = 0
+        buf = (ga.ga_result * 1024)()
+        nres = ga._i(0)
+        launches0 = ga.ga_launch_count()
+        t0 = time.perf_counter()
+        nxt = done = inflight = 0
+        while done < n_req:
+            now = time.perf_counter() - t0
+            while nxt < n_req and arrivals[nxt] <= now:
+                ro, rl, fo, fl = meta[nxt]
+                ga.ga_server_submit(srv, ga.ga_request(len(ro), reads_p, ro.ctypes.data,
+                                                       rl.ctypes.data, refs_p, fo.ctypes.data,
+                                                       fl.ctypes.data, nxt))
+                nxt += 1
+                inflight += 1
+            if inflight == 0:
+                time.sleep(max(0.0, arrivals[nxt] - (time.perf_counter() - t0)))
+                continue
+            ga.ga_server_step(srv)
+            steps += 1
+            while True:
+                f_poll(srv, buf, 1024, ctypes.byref(nres))
+                if nres.value == 0:
+                    break
+                t = time.perf_counter() - t0
+                for q in range(nres.value):
+                    r = buf[q]
+                    i = int(r.tag)
+                    lat[i] = 1e3 * (t - arrivals[i])
+                    n = int(r.n_pairs)
+                    pairs += n
+                    bases += int(meta[i][1].sum())
+                    if check:
+                        off = np.ctypeslib.as_array(r.cigar_off, shape=(n + 1,)).copy()
+                        got[i] = (np.ctypeslib.as_array(r.dist, shape=(n,)).copy(),
+                                  np.ctypeslib.as_array(r.status, shape=(n,)).copy(),
+                                  np.ctypeslib.as_array(r.ref_consumed, shape=(n,)).copy(), off,
+                                  np.ctypeslib.as_array(r.cigar, shape=(int(off[-1]),)).copy()
+                                  if off[-1] else np.zeros(0, np.uint32))
+                    ga.ga_server_release(srv, r.ticket)
+                done += nres.value
+                inflight -= nres.value
+        wall = time.perf_counter() - t0
+        launches = ga.ga_launch_count() - launches0
+        ga.ga_server_destroy(srv)
+        out = {"offered_requests_per_s": rate, "seconds_of_arrivals": seconds, "requests": n_req,
+               "pairs": pairs, "read_bases": bases, "wall_s": wall, "pairs_per_s": pairs / wall,
+               "gbases_per_s": bases / wall / 1e9, "offered_pairs_per_s": sum(len(q) for q in ids) / seconds,
+               "steps": steps, "step_windows": 48, "budget_bytes": budget,
+               "kernel_launches": launches, **_percentiles(lat)}
+        return out, ids, got
+
+    served, ids, got = serve(2000.0, args.serve_seconds, 5, True)
+    # Every served request against the oracle (pool pairs aligned once on the host cores).
+    ref = oracle.align(pool, W=W, O=O, k=K)
+    bad = 0
+    for q, (d, st, rc, off, runs) in zip(ids, got):
+        ok = (np.array_equal(d, ref.dist[q]) and np.array_equal(st, ref.status[q])
+              and np.array_equal(rc, ref.ref_consumed[q]))
+        if ok:
+            for p, pid in enumerate(q):
+                if not np.array_equal(runs[off[p]:off[p + 1]], ref.runs(int(pid))):
+                    ok = False
+                    break
+        bad += 0 if ok else 1
+    served["oracle_check"] = {"requests": len(got), "differing_requests": bad,
+                              "pairs": int(sum(len(q) for q in ids))}
+    saturated, _, _ = serve(20000.0, args.saturate_seconds, 6, False)
 
     # -- plain per-request launch: each request alone, in arrival order --
-    n_plain = int(np.searchsorted(arrivals, args.plain_serve_seconds))
+    reqs = datagen.make_requests(2000.0, args.plain_serve_seconds, seed=5)
+    arrivals = np.array([r.arrival_s for r in reqs])
     lat_p, pairs_p, bases_p = [], 0, 0
     s = torch.cuda.Stream(dev)
     t0 = time.perf_counter()
-    for i in range(n_plain):
+    for i, r in enumerate(reqs):
         wait = arrivals[i] - (time.perf_counter() - t0)
         if wait > 0:
             time.sleep(wait)
-        sub = pool.subset(ids[i])
+        sub = pool.subset((np.asarray(r.pair_ids, dtype=np.int64) % POOL_PAIRS).tolist())
         with torch.cuda.stream(s):
             from paper_2203_15561_gb300.pipeline import DeviceBatch
             dbq = DeviceBatch(sub, W=W, O=O, k=K, device=str(dev))
@@ -568,14 +606,17 @@ def run_serving(args, dev):
         bases_p += sub.read_bases
         del h, runs, dbq
     wall_p = time.perf_counter() - t0
-    plain = {"requests": n_plain, "pairs": pairs_p, "wall_s": wall_p,
+    plain = {"requests": len(reqs), "pairs": pairs_p, "wall_s": wall_p,
              "pairs_per_s": pairs_p / wall_p if wall_p > 0 else None,
              "gbases_per_s": bases_p / wall_p / 1e9 if wall_p > 0 else None,
              **_percentiles(lat_p)}
-    offered = sum(len(q) for q in ids[:n_req]) / args.serve_seconds
     return {"workload": "serving-poisson-2000rps (1-64 workload-4 pairs per request, seed 5, "
-                        f"{args.serve_seconds:g} s of arrivals, pool of {pool_n} distinct pairs)",
-            "offered_pairs_per_s": offered, "served": served, "plain_per_request": plain}
+                        f"{args.serve_seconds:g} s of arrivals, pool of {POOL_PAIRS} distinct pairs)",
+            "offered_pairs_per_s": served["offered_pairs_per_s"], "served": served,
+            "saturated": saturated, "plain_per_request": plain,
+            "step": "one captured CUDA graph per step (counters, step kernel, finished slots to "
+                    "host-mapped memory); admission copies and result harvesting overlap the "
+                    "running step"}
 
 
 def _rows_per_window(cells, windows):

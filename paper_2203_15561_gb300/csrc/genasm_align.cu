@@ -226,57 +226,75 @@ cudaError_t launch_plain(const AlignParams& p, cudaStream_t s) {
 // one slice of each other: a batch whose pairs outnumber the resident groups
 // but not by a whole multiple no longer ends with a round in which a few
 // groups run alone (10,000 equal pairs on 4,864 groups: three pair lengths
-// without slices, about 2.06 with them). Pushing is lock-free: a producer
-// takes a tail position with atomicAdd, writes the pair into the ring slot
-// and then publishes the slot with its sequence number (position + 1); a
-// consumer claims the head position with atomicCAS once its slot carries the
-// head's sequence number. A group that finds the head unpublished stops
-// (the queue is empty: every pair still unfinished is held by a group, which
-// takes it back itself), so no group ever waits.
+// without slices, about 2.06 with them).
+//
+// The FIFO is a bounded ring of n slots (n = pairs, so it can hold every
+// pair) with a sequence number per slot: position x lives in slot x % n; the
+// slot holds position x's pair once its number is x + 1, and is free for
+// position x + n once its number is x + n. A group that wants a pair reserves
+// the next head position with atomicAdd and takes the pair once that position
+// is published; until then it stays idle while the other groups of its warp
+// go on (it checks again after each of their windows), and it stops once no
+// pair is left unfinished. A group that ends a turn claims the tail position
+// with atomicCAS when its slot is free, writes the pair and publishes it; if
+// the slot is not free yet or the claim keeps losing races, the group keeps
+// the pair for another turn. No group ever waits on another, and every pair
+// not yet finished is held by a running group or published in the ring.
 // ---------------------------------------------------------------------------
 
 struct BatchArgs {
-  uint32_t* queue;        // [0] hand-out counter (unsliced), [1] ring head, [2] ring tail
+  uint32_t* queue;        // [0] hand-out counter (unsliced); ring: [1] head, [2] tail,
+                          // [3] pairs not finished, [4] a warp's wait ran out
   uint32_t* order;        // hand-out order / the ring's slots (nullptr: index order, unsliced)
   uint64_t* spill;        // [groups][kMaxRows * kMaxStride]
   int table_entries;
   uint32_t slice;         // windows per turn (0: a pair runs to its end)
-  uint32_t* ring_seq;     // per ring slot: the position it holds + 1
+  uint32_t* ring_seq;     // per ring slot: its sequence number
   SlotState* state;       // per pair: saved window state (all zero: not started)
 };
 
 constexpr uint32_t kNoPair = 0xffffffffu;
+// Polls of a warp whose groups all wait for a pair (about 0.2 microseconds
+// each): seconds, far beyond any legitimate wait (the rest of the
+// longest pair); past it the warp stops and flags the launch.
+constexpr uint32_t kRingPolls = 25u * 1000u * 1000u;
 
-// Takes the pair at the ring's head, or kNoPair when the head slot is not
-// published (nothing waiting) or the claim keeps losing races.
-__device__ __forceinline__ uint32_t ring_pop(const BatchArgs& a, uint32_t n) {
-  volatile uint32_t* head = a.queue + 1;
+// The pair at reserved ring position x, or kNoPair while it is not published.
+__device__ __forceinline__ uint32_t ring_take(const BatchArgs& a, uint32_t n, uint32_t x) {
   volatile uint32_t* seq = a.ring_seq;
   volatile uint32_t* slot = a.order;
-  for (int tries = 0; tries < 1024; ++tries) {
-    const uint32_t h = *head;
-    const uint32_t x = h % n;
-    if (seq[x] != h + 1u) return kNoPair;
-    __threadfence();
-    const uint32_t pair = slot[x];
-    if (atomicCAS(a.queue + 1, h, h + 1u) == h) {
-      __threadfence();
-      return pair;
-    }
-  }
-  return kNoPair;
+  const uint32_t s = x % n;
+  if (seq[s] != x + 1u) return kNoPair;
+  __threadfence();
+  const uint32_t pair = slot[s];
+  __threadfence();
+  seq[s] = x + n;  // free for position x + n
+  return pair;
 }
 
-// Puts a pair (its state already saved) at the ring's tail.
-__device__ __forceinline__ void ring_push(const BatchArgs& a, uint32_t n, uint32_t pair) {
-  __threadfence();  // the saved state before the publication
-  const uint32_t t = atomicAdd(a.queue + 2, 1u);
-  const uint32_t x = t % n;
-  volatile uint32_t* slot = a.order;
+// Puts a pair (its state already saved) at the ring's tail; false when the
+// tail slot is not free yet or the claim lost too many races.
+__device__ __forceinline__ bool ring_try_push(const BatchArgs& a, uint32_t n, uint32_t pair) {
+  volatile uint32_t* tail = a.queue + 2;
   volatile uint32_t* seq = a.ring_seq;
-  slot[x] = pair;
-  __threadfence();
-  seq[x] = t + 1u;
+  volatile uint32_t* slot = a.order;
+  __threadfence();  // the saved state before the publication
+  for (int tries = 0; tries < 16; ++tries) {
+    const uint32_t t = *tail;
+    const uint32_t s = t % n;
+    const uint32_t q = seq[s];
+    if (q == t) {
+      if (atomicCAS(a.queue + 2, t, t + 1u) == t) {
+        slot[s] = pair;
+        __threadfence();
+        seq[s] = t + 1u;
+        return true;
+      }
+    } else if (q != t + 1u) {
+      return false;  // the slot still holds position t - n
+    }
+  }
+  return false;
 }
 
 constexpr int kSpillEntries = kMaxRows * kMaxStride;
@@ -301,22 +319,32 @@ __global__ void __launch_bounds__(256) __maxnreg__(R)
   st.busy = false;
   bool drained = false;
   uint32_t budget = 0;
+  uint32_t resv = kNoPair;  // lane 0: the ring position this group has reserved
+  uint32_t idle = 0;        // consecutive polls of a warp with no pair to work on
   for (;;) {
     // Groups without a pair take the next one from the queue.
     const bool want = !st.busy && !drained;
     uint32_t pair = kNoPair;
+    bool quit = false;
     if (want && r == 0) {
       if (a.slice) {
-        pair = ring_pop(a, p.n_pairs);
+        if (resv == kNoPair) resv = atomicAdd(a.queue + 1, 1u);
+        pair = ring_take(a, p.n_pairs, resv);
+        if (pair != kNoPair) resv = kNoPair;
+        else quit = *reinterpret_cast<volatile uint32_t*>(a.queue + 3) == 0u;  // all finished
       } else {
         const uint32_t idx = atomicAdd(a.queue, 1u);
         if (idx < p.n_pairs) pair = a.order ? a.order[idx] : idx;
+        else quit = true;
       }
     }
     pair = __shfl_sync(kFull, pair, gbase);
+    quit = __shfl_sync(kFull, quit ? 1u : 0u, gbase) != 0u;
+    bool ended = false;  // a pair that finished at its start
     if (want) {
       if (pair != kNoPair) {
         begin_pair(p, pair, st, r == 0);
+        ended = !st.busy;
         if (a.slice) {
           // Another SM may have saved this state: read it from L2, not L1.
           const SlotState* sp = a.state + pair;
@@ -332,19 +360,40 @@ __global__ void __launch_bounds__(256) __maxnreg__(R)
           if (s.windows > 0) resume_pair(s, st);  // a pair that had turns already
           budget = a.slice;
         }
-      } else {
+      } else if (quit) {
         drained = true;
       }
     }
     if (!__any_sync(kFull, st.busy || !drained)) break;
-    if (__any_sync(kFull, st.busy)) step_window<G>(p, r, gbase, st, gs, table, a.table_entries, spill);
-    // End of a turn: the pair goes back to the queue's tail.
-    if (a.slice && st.busy && --budget == 0) {
-      if (r == 0) {
-        save_pair(st, a.state[st.pair]);
-        ring_push(a, p.n_pairs, st.pair);
+    const bool was_busy = st.busy;
+    if (__any_sync(kFull, st.busy)) {
+      step_window<G>(p, r, gbase, st, gs, table, a.table_entries, spill);
+      idle = 0;
+    } else {
+      // Every group of the warp waits for a pair: poll again shortly.
+      __nanosleep(200);
+      if (++idle == kRingPolls) {
+        if (lane == 0) atomicExch(a.queue + 4, 1u);
+        drained = true;
       }
-      st.busy = false;
+    }
+    if (a.slice) {
+      if ((was_busy && !st.busy) || ended) {
+        if (r == 0) atomicSub(a.queue + 3, 1u);  // this pair is finished
+      }
+      // End of a turn: the pair goes back to the queue's tail (or, if the ring
+      // cannot take it now, stays for another turn).
+      const bool turn_end = st.busy && --budget == 0;
+      uint32_t pushed = 0;
+      if (turn_end && r == 0) {
+        save_pair(st, a.state[st.pair]);
+        pushed = ring_try_push(a, p.n_pairs, st.pair) ? 1u : 0u;
+      }
+      pushed = __shfl_sync(kFull, pushed, gbase);
+      if (turn_end) {
+        if (pushed) st.busy = false;
+        else budget = a.slice;
+      }
     }
   }
 }
@@ -436,7 +485,9 @@ int band_top_for(int O) { return O >= 16 ? std::min(22, O - 1) : -1; }
 // windows when the pairs outnumber the resident groups less than 16 times
 // over (more pairs than that leave a tail of under a sixteenth of a round).
 uint32_t slice_for(uint32_t n_pairs, const BatchPlan& plan) {
-  if (plan.slice_windows < 0) return 0u;
+  // A ring of one slot could not tell "position x published" (x + 1) from
+  // "free for position x + 1" (x + 1): a single pair runs unsliced.
+  if (plan.slice_windows < 0 || n_pairs < 2) return 0u;
   if (plan.slice_windows > 0) return static_cast<uint32_t>(plan.slice_windows);
   const uint64_t groups = static_cast<uint64_t>(plan.blocks) * plan.pairs_per_block;
   return n_pairs > groups && n_pairs < 16 * groups ? 32u : 0u;
@@ -525,8 +576,11 @@ cudaError_t launch_lpt_order(const uint32_t* read_len, uint32_t n, uint32_t* his
 // The ring of the sliced queue starts full: slot x holds hand-out position x
 // (the LPT order, or pair x), published with sequence number x + 1.
 __global__ void ring_init_kernel(uint32_t n, bool identity, uint32_t* __restrict__ slot,
-                                 uint32_t* __restrict__ seq, uint32_t* __restrict__ tail) {
-  if (blockIdx.x == 0 && threadIdx.x == 0) *tail = n;  // the ring starts full
+                                 uint32_t* __restrict__ seq, uint32_t* __restrict__ queue) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    queue[2] = n;  // tail: the ring starts full
+    queue[3] = n;  // pairs not finished
+  }
   for (uint32_t x = blockIdx.x * blockDim.x + threadIdx.x; x < n; x += gridDim.x * blockDim.x) {
     if (identity) slot[x] = x;
     seq[x] = x + 1u;
@@ -566,7 +620,7 @@ cudaError_t launch_batched(const AlignParams& p, const BatchPlan& plan, void* ws
   if (slice) {
     if ((e = cudaMemsetAsync(state, 0, sizeof(SlotState) * p.n_pairs, s)) != cudaSuccess) return e;
     const int blocks = static_cast<int>(std::min<uint32_t>((p.n_pairs + 255) / 256, 1024u));
-    ring_init_kernel<<<blocks, 256, 0, s>>>(p.n_pairs, !plan.lpt, order, ring_seq, queue + 2);
+    ring_init_kernel<<<blocks, 256, 0, s>>>(p.n_pairs, !plan.lpt, order, ring_seq, queue);
     count_launches(1);
   }
   BatchArgs a{queue, (plan.lpt || slice) ? order : nullptr,
@@ -807,6 +861,8 @@ __global__ void __launch_bounds__(256, 1) align_step_kernel(const AlignParams p,
   st.busy = false;
   bool drained = false;
   uint32_t slot = 0, budget = 0;
+  const uint32_t n_active = a.counters[2];
+  const uint32_t max_windows = a.counters[3];
   for (;;) {
     const bool want = !st.busy && !drained;
     uint32_t idx = 0xffffffffu;
@@ -814,11 +870,11 @@ __global__ void __launch_bounds__(256, 1) align_step_kernel(const AlignParams p,
     idx = __shfl_sync(kFull, idx, gbase);
     bool finished = false;
     if (want) {
-      if (idx < a.n_active) {
+      if (idx < n_active) {
         slot = a.active[idx];
         begin_pair(p, slot, st, r == 0);  // a fresh slot (all zero) starts here
         if (st.busy) resume_pair(a.state[slot], st);
-        budget = a.max_windows;
+        budget = max_windows;
         finished = !st.busy;
       } else {
         drained = true;
@@ -841,18 +897,25 @@ __global__ void __launch_bounds__(256, 1) align_step_kernel(const AlignParams p,
 
 #define GA_STEP_VARIANTS(X) X(8) X(16) X(32)
 
+cudaError_t prepare_step(const BatchPlan& plan) {
+  cudaError_t e = cudaErrorInvalidValue;
+#define GA_STEP_PREPARE(g)                                                                       \
+  if (plan.lanes_per_pair == g)                                                                  \
+    e = cudaFuncSetAttribute(align_step_kernel<g>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
+                             static_cast<int>(plan.smem_bytes));
+  GA_STEP_VARIANTS(GA_STEP_PREPARE)
+#undef GA_STEP_PREPARE
+  return e;
+}
+
 cudaError_t launch_step(const AlignParams& p, const BatchPlan& plan, const StepArgs& a,
                         cudaStream_t s) {
-  if (a.n_active == 0) return cudaSuccess;
   const int threads = plan.pairs_per_block * plan.lanes_per_pair;
   AlignParams q = p;
   q.band_top = plan.band_top;
   cudaError_t e = cudaErrorInvalidValue;
 #define GA_STEP_LAUNCH(g)                                                                         \
   if (plan.lanes_per_pair == g) {                                                                 \
-    e = cudaFuncSetAttribute(align_step_kernel<g>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
-                             static_cast<int>(plan.smem_bytes));                                  \
-    if (e != cudaSuccess) return e;                                                               \
     align_step_kernel<g><<<plan.blocks, threads, plan.smem_bytes, s>>>(q, a);                     \
     e = cudaGetLastError();                                                                       \
   }
@@ -860,6 +923,23 @@ cudaError_t launch_step(const AlignParams& p, const BatchPlan& plan, const StepA
 #undef GA_STEP_LAUNCH
   if (e == cudaSuccess) count_launches(1);
   return e;
+}
+
+// The finished count and the finished slots of a step, into host-mapped memory
+// (one block; the host reads them once the step's event has completed).
+__global__ void step_copyout_kernel(const uint32_t* __restrict__ counters,
+                                    const uint32_t* __restrict__ done, uint32_t* host_count,
+                                    uint32_t* host_done) {
+  const uint32_t nd = counters[1];
+  for (uint32_t q = threadIdx.x; q < nd; q += blockDim.x) host_done[q] = done[q];
+  if (threadIdx.x == 0) host_count[0] = nd;
+}
+
+cudaError_t launch_step_copyout(const uint32_t* counters, const uint32_t* done,
+                                uint32_t* host_count, uint32_t* host_done, cudaStream_t s) {
+  step_copyout_kernel<<<1, 256, 0, s>>>(counters, done, host_count, host_done);
+  count_launches(1);
+  return cudaGetLastError();
 }
 
 bool step_variant_exists(int G) {

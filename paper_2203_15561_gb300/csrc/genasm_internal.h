@@ -80,17 +80,24 @@ struct SlotState {
 
 struct StepArgs {
   const uint32_t* active;  // slots to advance this step
-  uint32_t n_active;
-  uint32_t* counters;      // [0] work counter, [1] finished count (both zeroed per step)
+  uint32_t* counters;      // [0] work counter, [1] finished count (both zeroed per step),
+                           // [2] active slots, [3] windows per step (set before each step)
   SlotState* state;        // per slot
   uint32_t* done;          // slots that finished this step
   uint64_t* spill;         // [groups][65 * 66]
   int table_entries;
-  uint32_t max_windows;
 };
 
+// The serving step kernel reads its active count and window budget from
+// device memory (counters[2], counters[3]), so one captured launch serves every
+// step. prepare_step sets the kernel's shared-memory attribute (once, outside
+// any capture); launch_step launches it; launch_step_copyout copies the
+// finished count and the finished slots into host-mapped memory after it.
+cudaError_t prepare_step(const BatchPlan& plan);
 cudaError_t launch_step(const AlignParams& p, const BatchPlan& plan, const StepArgs& a,
                         cudaStream_t s);
+cudaError_t launch_step_copyout(const uint32_t* counters, const uint32_t* done,
+                                uint32_t* host_count, uint32_t* host_done, cudaStream_t s);
 bool step_variant_exists(int G);
 
 WorkspaceLayout workspace_layout(uint32_t n_pairs, const BatchPlan& plan);

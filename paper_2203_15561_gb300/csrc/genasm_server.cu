@@ -3,20 +3,30 @@
 // A request (1..n pairs, host ASCII) is copied at submission and waits until
 // the device-memory budget has room for it: its packed sequences, its CIGAR
 // capacity (read+ref+1 runs per pair) and one slot per pair, all carved from
-// arenas allocated once at creation. Each ga_server_step
-//   1. admits waiting requests in arrival order while they fit: H2D of their
+// arenas allocated once at creation. The device work of a step is one
+// captured CUDA graph (zero the step counters, the resumable step kernel over
+// every admitted, unfinished pair, then a copy of the finished slots into
+// host-mapped memory); the kernel reads the active count and the window
+// budget from device memory, so the same graph serves every step. Each
+// ga_server_step
+//   1. waits for the step launched by the previous call and takes the slots
+//      that finished in it (one event wait, no copy);
+//   2. admits waiting requests in arrival order while they fit: H2D of their
 //      ASCII through a pinned staging buffer, 2-bit packing into the arena,
-//      per-slot metadata, zeroed window state;
-//   2. launches the resumable step kernel over every admitted, unfinished
-//      pair: each advances by at most `max_windows` windows and keeps its
-//      window state (positions, edit count, open CIGAR run) on the device;
-//   3. reads back which pairs finished, and for every request whose pairs
-//      are all done gathers the CIGAR runs into one buffer, copies distances,
-//      statuses and runs to host memory and frees the request's device space.
+//      per-slot metadata, zeroed window state (on the copy stream);
+//   3. launches the next step (after the copies, on the compute stream) and
+//      returns without waiting for it: every admitted pair advances by at
+//      most `max_windows` windows, its window state (positions, edit count,
+//      open CIGAR run) kept on the device;
+//   4. meanwhile, for every request whose pairs are all done, gathers the
+//      CIGAR runs into one buffer, copies distances, statuses and runs to host
+//      memory and frees the request's device space (copy stream);
+//   5. admits requests that arrived meanwhile, so their copies and packing
+//      overlap the running step and they join the next one.
 // Requests admitted at different steps therefore share launches and overlap
-// on the device, and a finished request's memory is reused at the next step.
-// Every wait is a host-side stream synchronization; no kernel waits on
-// another.
+// on the device, and a finished request's memory is reused by the next
+// admission. Every wait is a host-side event or stream synchronization; no
+// kernel waits on another.
 #include <algorithm>
 #include <chrono>
 #include <cstdlib>
@@ -139,6 +149,21 @@ struct ga_server {
   uint64_t* d_list = nullptr;    // gather list (3 x uint64 per pair)
   uint32_t* d_out = nullptr;     // gathered runs of finished requests
   uint64_t out_cap = 0;
+  // the step: a captured graph on the compute stream, its finished slots in
+  // host-mapped memory
+  cudaStream_t cstream = nullptr;
+  cudaGraph_t step_graph = nullptr;
+  cudaGraphExec_t step_exec = nullptr;
+  uint64_t step_kernels = 0;  // kernels one replay launches
+  cudaEvent_t ev_admit = nullptr, ev_step = nullptr;
+  cudaEvent_t ev_staged = nullptr;  // the last H2D copy out of h_ascii has been issued before it
+  bool staged = false;
+  bool inflight = false;
+  uint32_t* h_count_map = nullptr;  // [0] slots finished in the last step
+  uint32_t* h_done_map = nullptr;   // those slots
+  uint32_t* d_count_map = nullptr;  // device views of the two
+  uint32_t* d_done_map = nullptr;
+  uint32_t* h_ctl = nullptr;        // pinned: active count, windows per step
   // pinned host staging
   uint8_t* h_ascii = nullptr;
   uint64_t* h_meta64 = nullptr;  // 3 arrays of max_slots uint64 (read_off, ref_off, cigar_off)
@@ -199,7 +224,16 @@ void server_free(ga_server* s) {
   cudaFreeHost(s->h_list);
   cudaFreeHost(s->h_out);
   cudaFreeHost(s->h_small);
+  cudaFreeHost(s->h_count_map);
+  cudaFreeHost(s->h_done_map);
+  cudaFreeHost(s->h_ctl);
+  if (s->step_exec) cudaGraphExecDestroy(s->step_exec);
+  if (s->step_graph) cudaGraphDestroy(s->step_graph);
+  if (s->ev_admit) cudaEventDestroy(s->ev_admit);
+  if (s->ev_step) cudaEventDestroy(s->ev_step);
+  if (s->ev_staged) cudaEventDestroy(s->ev_staged);
   if (s->stream) cudaStreamDestroy(s->stream);
+  if (s->cstream) cudaStreamDestroy(s->cstream);
   for (Request* r : s->pending) delete r;
   std::vector<Request*> owners;  // admitted, unfinished requests
   for (Request* r : s->slot_owner)
@@ -214,6 +248,59 @@ void server_free(ga_server* s) {
 constexpr uint64_t kAsciiStaging = 64ull << 20;  // ASCII bytes admitted per step (at most)
 constexpr uint64_t kOutRuns = 16ull << 20;        // runs gathered per step (at most, 64 MB)
 constexpr uint64_t kListPairs = 1ull << 16;       // pairs harvested per step (at most)
+
+// The alignment parameters of the step kernel over the server's slots.
+ga::AlignParams step_params(const ga_server* s) {
+  ga::AlignParams p{};
+  p.reads = s->d_seq;
+  p.read_off = s->d_read_off;
+  p.read_len = s->d_read_len;
+  p.refs = s->d_seq;
+  p.ref_off = s->d_ref_off;
+  p.ref_len = s->d_ref_len;
+  p.n_pairs = s->max_slots;
+  p.W = s->W;
+  p.O = s->O;
+  p.kmax = s->k < s->W ? s->k : s->W;
+  p.tb_table = ga::tb_table(ga::kTbOrderDefault);
+  p.dist = s->d_dist;
+  p.status = s->d_status;
+  p.ref_consumed = s->d_ref_consumed;
+  p.cigar = s->d_cigar;
+  p.cigar_off = s->d_cigar_off;
+  p.cigar_cap = s->d_cigar_cap;
+  p.n_runs = s->d_n_runs;
+  p.n_windows = s->d_n_windows;
+  p.cells = s->d_cells;
+  return p;
+}
+
+// Captures the step's device work into a graph (once, at creation).
+cudaError_t capture_step(ga_server* s) {
+  cudaError_t e = ga::prepare_step(s->plan);
+  if (e != cudaSuccess) return e;
+  ga::StepArgs a{};
+  a.active = s->d_active;
+  a.counters = s->d_counters;
+  a.state = s->d_state;
+  a.done = s->d_done;
+  a.spill = s->d_spill;
+  a.table_entries = s->plan.table_entries;
+  const uint64_t before = ga_launch_count();
+  e = cudaStreamBeginCapture(s->cstream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  cudaError_t e1 = cudaMemsetAsync(s->d_counters, 0, 8, s->cstream);
+  if (e1 == cudaSuccess) e1 = ga::launch_step(step_params(s), s->plan, a, s->cstream);
+  if (e1 == cudaSuccess)
+    e1 = ga::launch_step_copyout(s->d_counters, s->d_done, s->d_count_map, s->d_done_map,
+                                 s->cstream);
+  e = cudaStreamEndCapture(s->cstream, &s->step_graph);
+  if (e1 != cudaSuccess) return e1;
+  if (e != cudaSuccess) return e;
+  s->step_kernels = ga_launch_count() - before;
+  ga::uncount_launches(s->step_kernels);  // captured, not run: counted at each replay
+  return cudaGraphInstantiate(&s->step_exec, s->step_graph, 0);
+}
 
 }  // namespace
 
@@ -239,6 +326,10 @@ extern "C" int ga_server_create(size_t budget_bytes, int W, int O, int k, ga_ser
                          ga::table_entries_for(G, W, O, rows, ga::band_top_for(O) >= 0), 1, true,
                          &s->plan);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->cstream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_admit, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_step, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_staged, cudaEventDisableTiming);
   // Fixed parts first, then the arenas from what is left of the budget.
   const uint64_t groups = static_cast<uint64_t>(s->plan.blocks) * s->plan.pairs_per_block;
   const uint64_t spill_bytes = groups * 8ull * ga::kMaxRows * ga::kMaxStride;
@@ -286,6 +377,12 @@ extern "C" int ga_server_create(size_t budget_bytes, int W, int O, int k, ga_ser
   if (e == cudaSuccess) e = cudaMallocHost(&s->h_list, 24ull * kListPairs);
   if (e == cudaSuccess) e = cudaMallocHost(&s->h_out, 4ull * kOutRuns);
   if (e == cudaSuccess) e = cudaMallocHost(&s->h_small, 16ull * M);
+  if (e == cudaSuccess) e = cudaHostAlloc(&s->h_count_map, 64, cudaHostAllocMapped);
+  if (e == cudaSuccess) e = cudaHostAlloc(&s->h_done_map, 4ull * M, cudaHostAllocMapped);
+  if (e == cudaSuccess) e = cudaMallocHost(&s->h_ctl, 64);
+  if (e == cudaSuccess) e = cudaHostGetDevicePointer(&s->d_count_map, s->h_count_map, 0);
+  if (e == cudaSuccess) e = cudaHostGetDevicePointer(&s->d_done_map, s->h_done_map, 0);
+  if (e == cudaSuccess) e = capture_step(s);
   if (e != cudaSuccess) {
     server_free(s);
     delete s;
@@ -354,6 +451,12 @@ namespace {
 int admit(ga_server* s, std::vector<Request*>& finished) {
   uint64_t staged = 0;
   std::vector<Request*> batch;
+  // The pinned staging buffer is reused: the previous admission's copy out of
+  // it must have completed before it is written again.
+  if (s->staged && !s->pending.empty()) {
+    if (cudaEventSynchronize(s->ev_staged) != cudaSuccess) return GA_ECUDA;
+    s->staged = false;
+  }
   while (!s->pending.empty()) {
     Request* r = s->pending.front();
     if (r->n == 0) {
@@ -387,8 +490,10 @@ int admit(ga_server* s, std::vector<Request*>& finished) {
   }
   if (batch.empty()) return GA_OK;
   cudaStream_t st = s->stream;
-  if (cudaMemcpyAsync(s->d_ascii, s->h_ascii, staged, cudaMemcpyHostToDevice, st) != cudaSuccess)
+  if (cudaMemcpyAsync(s->d_ascii, s->h_ascii, staged, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaEventRecord(s->ev_staged, st) != cudaSuccess)
     return GA_ECUDA;
+  s->staged = true;
   const uint32_t M = s->max_slots;
   uint64_t aoff = 0;
   for (Request* r : batch) {
@@ -517,58 +622,16 @@ int harvest(ga_server* s, const std::vector<Request*>& finished) {
 
 extern "C" int ga_server_step(ga_server* s, uint32_t* n_active) {
   if (!s) return GA_EINVAL;
-  std::vector<Request*> finished;  // requests with no pairs finish at admission
-  int rc = admit(s, finished);
-  if (rc != GA_OK) return rc;
-  cudaStream_t st = s->stream;
-  if (!s->active.empty()) {
-    const uint32_t na = static_cast<uint32_t>(s->active.size());
-    std::memcpy(s->h_active, s->active.data(), 4ull * na);
-    if (cudaMemcpyAsync(s->d_active, s->h_active, 4ull * na, cudaMemcpyHostToDevice, st) != cudaSuccess ||
-        cudaMemsetAsync(s->d_counters, 0, 8, st) != cudaSuccess)
-      return GA_ECUDA;
-    ga::AlignParams p{};
-    p.reads = s->d_seq;
-    p.read_off = s->d_read_off;
-    p.read_len = s->d_read_len;
-    p.refs = s->d_seq;
-    p.ref_off = s->d_ref_off;
-    p.ref_len = s->d_ref_len;
-    p.n_pairs = s->max_slots;
-    p.W = s->W;
-    p.O = s->O;
-    p.kmax = s->k < s->W ? s->k : s->W;
-    p.tb_table = ga::tb_table(ga::kTbOrderDefault);
-    p.dist = s->d_dist;
-    p.status = s->d_status;
-    p.ref_consumed = s->d_ref_consumed;
-    p.cigar = s->d_cigar;
-    p.cigar_off = s->d_cigar_off;
-    p.cigar_cap = s->d_cigar_cap;
-    p.n_runs = s->d_n_runs;
-    p.n_windows = s->d_n_windows;
-    p.cells = s->d_cells;
-    ga::StepArgs a{};
-    a.active = s->d_active;
-    a.n_active = na;
-    a.counters = s->d_counters;
-    a.state = s->d_state;
-    a.done = s->d_done;
-    a.spill = s->d_spill;
-    a.table_entries = s->plan.table_entries;
-    a.max_windows = s->max_windows;
-    if (ga::launch_step(p, s->plan, a, st) != cudaSuccess) return GA_ECUDA;
-    if (cudaMemcpyAsync(s->h_counters, s->d_counters, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-        cudaStreamSynchronize(st) != cudaSuccess)
-      return GA_ECUDA;
-    const uint32_t nd = s->h_counters[1];
+  std::vector<Request*> finished;
+  // 1. The step in flight: wait for it and take the slots that finished.
+  if (s->inflight) {
+    if (cudaEventSynchronize(s->ev_step) != cudaSuccess) return GA_ECUDA;
+    s->inflight = false;
+    const uint32_t nd = *reinterpret_cast<volatile uint32_t*>(s->h_count_map);
     if (nd > 0) {
-      if (cudaMemcpyAsync(s->h_done, s->d_done, 4ull * nd, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-          cudaStreamSynchronize(st) != cudaSuccess)
-        return GA_ECUDA;
       std::vector<char> gone(s->max_slots, 0);
       for (uint32_t q = 0; q < nd; ++q) {
-        const uint32_t slot = s->h_done[q];
+        const uint32_t slot = reinterpret_cast<volatile uint32_t*>(s->h_done_map)[q];
         if (slot >= s->max_slots || !s->slot_owner[slot]) return GA_ECUDA;
         gone[slot] = 1;
         Request* r = s->slot_owner[slot];
@@ -580,7 +643,35 @@ extern "C" int ga_server_step(ga_server* s, uint32_t* n_active) {
       s->active.resize(w);
     }
   }
+  // 2. Requests waiting for admission (requests with no pairs finish here).
+  int rc = admit(s, finished);
+  if (rc != GA_OK) return rc;
+  // 3. The next step, after the admission copies: active slots and sizes,
+  // then the captured launch; it runs while the host goes on.
+  if (!s->active.empty()) {
+    const uint32_t na = static_cast<uint32_t>(s->active.size());
+    std::memcpy(s->h_active, s->active.data(), 4ull * na);
+    s->h_ctl[0] = na;
+    s->h_ctl[1] = s->max_windows;
+    if (cudaMemcpyAsync(s->d_active, s->h_active, 4ull * na, cudaMemcpyHostToDevice, s->stream) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(s->d_counters + 2, s->h_ctl, 8, cudaMemcpyHostToDevice, s->stream) !=
+            cudaSuccess ||
+        cudaEventRecord(s->ev_admit, s->stream) != cudaSuccess ||
+        cudaStreamWaitEvent(s->cstream, s->ev_admit, 0) != cudaSuccess ||
+        cudaGraphLaunch(s->step_exec, s->cstream) != cudaSuccess ||
+        cudaEventRecord(s->ev_step, s->cstream) != cudaSuccess)
+      return GA_ECUDA;
+    ga::count_launches(s->step_kernels);
+    s->inflight = true;
+  }
+  // 4. Results of the requests that finished, while the step runs.
   rc = harvest(s, finished);
+  if (rc != GA_OK) return rc;
+  // 5. Requests that arrived meanwhile: their copies overlap the running step.
+  std::vector<Request*> empty_ones;
+  rc = admit(s, empty_ones);
+  if (rc == GA_OK) rc = harvest(s, empty_ones);
   if (n_active) *n_active = static_cast<uint32_t>(s->active.size() + s->pending.size());
   return rc;
 }
@@ -618,6 +709,7 @@ extern "C" int ga_server_pending(ga_server* s, uint32_t* waiting, uint32_t* acti
 
 extern "C" int ga_server_destroy(ga_server* s) {
   if (!s) return GA_OK;
+  if (s->cstream) cudaStreamSynchronize(s->cstream);
   if (s->stream) cudaStreamSynchronize(s->stream);
   server_free(s);
   delete s;
