@@ -475,6 +475,7 @@ def _percentiles(lat_ms):
 
 
 POOL_PAIRS = 1 << 16
+STEP_WINDOWS = 128  # windows a served pair advances per step
 
 
 def run_serving(args, dev):
@@ -510,7 +511,7 @@ def run_serving(args, dev):
         free, _ = torch.cuda.mem_get_info(dev)
         budget = int(min(40 << 30, 0.6 * free))
         srv = ga.ga_server_create(budget, W, O, K)
-        ga.ga_server_set_step_windows(srv, 48)
+        ga.ga_server_set_step_windows(srv, STEP_WINDOWS)
         n_req = len(reqs)
         lat = np.zeros(n_req)
         got = [None] * n_req if check else None
@@ -562,7 +563,7 @@ def run_serving(args, dev):
         out = {"offered_requests_per_s": rate, "seconds_of_arrivals": seconds, "requests": n_req,
                "pairs": pairs, "read_bases": bases, "wall_s": wall, "pairs_per_s": pairs / wall,
                "gbases_per_s": bases / wall / 1e9, "offered_pairs_per_s": sum(len(q) for q in ids) / seconds,
-               "steps": steps, "step_windows": 48, "budget_bytes": budget,
+               "steps": steps, "step_windows": STEP_WINDOWS, "budget_bytes": budget,
                "kernel_launches": launches, **_percentiles(lat)}
         return out, ids, got
 

@@ -131,7 +131,7 @@ int ga_workspace_size(uint32_t n_pairs, int W, int O, int k, size_t* bytes_out);
  *                    queue (their window state is saved between turns), so
  *                    that all pairs finish together instead of the last
  *                    ones running alone; -1 = off (a pair runs to its end);
- *                    0 = automatic (turns of 32 windows when the pairs
+ *                    0 = automatic (turns of 64 windows when the pairs
  *                    outnumber the resident groups, but less than 16 times).
  */
 typedef struct ga_tuning_s {

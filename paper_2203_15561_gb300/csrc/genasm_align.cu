@@ -299,11 +299,10 @@ __device__ __forceinline__ bool ring_try_push(const BatchArgs& a, uint32_t n, ui
 
 constexpr int kSpillEntries = kMaxRows * kMaxStride;
 
-// R caps the registers per thread (255: no cap beyond the architecture's):
-// fewer registers let more blocks share an SM when the tables are small.
-template <int G, int R>
-__global__ void __launch_bounds__(256) __maxnreg__(R)
-    align_batched_kernel(const AlignParams p, const BatchArgs a) {
+// The body of the batched kernel; the kernels below differ only in their
+// register budget.
+template <int G>
+__device__ __forceinline__ void batched_body(const AlignParams& p, const BatchArgs& a) {
   extern __shared__ __align__(16) uint64_t smem[];
   const int lane = threadIdx.x & 31;
   const int group_in_block = threadIdx.x / G;
@@ -398,6 +397,25 @@ __global__ void __launch_bounds__(256) __maxnreg__(R)
   }
 }
 
+// R caps the registers per thread (255: the kernel as compiled, launch
+// bounds of one block per SM; 168 or 128: fewer registers, so that more
+// blocks share an SM when the tables are small).
+template <int G>
+__global__ void __launch_bounds__(256, 1) align_batched_kernel(const AlignParams p, const BatchArgs a) {
+  batched_body<G>(p, a);
+}
+template <int G, int R>
+__global__ void __maxnreg__(R) align_batched_capped_kernel(const AlignParams p, const BatchArgs a) {
+  batched_body<G>(p, a);
+}
+
+// The kernel of variant (G, R).
+template <int G, int R>
+constexpr auto batched_kernel_of() {
+  if constexpr (R == 255) return align_batched_kernel<G>;
+  else return align_batched_capped_kernel<G, R>;
+}
+
 // Counting sort of pairs by read length, longest first (LPT hand-out).
 __device__ __forceinline__ uint32_t lpt_bucket(uint32_t read_len) {
   // 64-base buckets up to 65,535 bases; longer reads share the top bucket.
@@ -459,11 +477,11 @@ bool batch_variant_exists(int G, int max_registers) {
 static cudaError_t variant_setup(int G, int R, int threads, size_t smem, int* per_sm) {
 #define GA_SETUP(g, r)                                                                          \
   if (G == g && R == r) {                                                                       \
-    cudaError_t e = cudaFuncSetAttribute(align_batched_kernel<g, r>,                            \
+    cudaError_t e = cudaFuncSetAttribute(batched_kernel_of<g, r>(),                             \
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,           \
                                          static_cast<int>(smem));                               \
     if (e != cudaSuccess) return e;                                                             \
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, align_batched_kernel<g, r>,    \
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, batched_kernel_of<g, r>(),     \
                                                          threads, smem);                        \
   }
   GA_BATCH_VARIANTS(GA_SETUP)
@@ -474,23 +492,25 @@ static cudaError_t variant_setup(int G, int R, int threads, size_t smem, int* pe
 static void variant_launch(int G, int R, int blocks, int threads, size_t smem, cudaStream_t s,
                            const AlignParams& p, const BatchArgs& a) {
 #define GA_LAUNCH(g, r) \
-  if (G == g && R == r) align_batched_kernel<g, r><<<blocks, threads, smem, s>>>(p, a);
+  if (G == g && R == r) batched_kernel_of<g, r>()<<<blocks, threads, smem, s>>>(p, a);
   GA_BATCH_VARIANTS(GA_LAUNCH)
 #undef GA_LAUNCH
 }
 
 int band_top_for(int O) { return O >= 16 ? std::min(22, O - 1) : -1; }
 
-// Windows per turn of the sliced queue: the plan's choice, else slices of 32
+// Windows per turn of the sliced queue: the plan's choice, else turns of 64
 // windows when the pairs outnumber the resident groups less than 16 times
 // over (more pairs than that leave a tail of under a sixteenth of a round).
+// Shorter turns cost more than they save: 8 windows made workload 2 18%
+// slower, 32 about even, 64 2% faster than no turns.
 uint32_t slice_for(uint32_t n_pairs, const BatchPlan& plan) {
   // A ring of one slot could not tell "position x published" (x + 1) from
   // "free for position x + 1" (x + 1): a single pair runs unsliced.
   if (plan.slice_windows < 0 || n_pairs < 2) return 0u;
   if (plan.slice_windows > 0) return static_cast<uint32_t>(plan.slice_windows);
   const uint64_t groups = static_cast<uint64_t>(plan.blocks) * plan.pairs_per_block;
-  return n_pairs > groups && n_pairs < 16 * groups ? 32u : 0u;
+  return n_pairs > groups && n_pairs < 16 * groups ? 64u : 0u;
 }
 
 int table_entries_for(int G, int W, int O, int rows, bool band) {

@@ -245,7 +245,7 @@ void server_free(ga_server* s) {
   for (auto& kv : s->handed_out) delete kv.second;
 }
 
-constexpr uint64_t kAsciiStaging = 64ull << 20;  // ASCII bytes admitted per step (at most)
+constexpr uint64_t kAsciiStaging = 256ull << 20;  // ASCII bytes admitted per admission (at most)
 constexpr uint64_t kOutRuns = 16ull << 20;        // runs gathered per step (at most, 64 MB)
 constexpr uint64_t kListPairs = 1ull << 16;       // pairs harvested per step (at most)
 

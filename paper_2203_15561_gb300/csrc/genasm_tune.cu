@@ -76,14 +76,20 @@ std::vector<ga_tuning> candidates(int rows) {
   // global memory, so larger tables that cover the tail of d_min are tried too.
   const int lo = std::min(65, std::max(4, rows + 5));
   const int hi = std::min(65, std::max(6, rows + 8));
+  // The mean hides the windows that lose the read's path (random-versus-random
+  // windows with d_min near 32 amid windows near 8): the library's 39 rows,
+  // which hold those too, are always a candidate.
   const int tail = std::min(65, std::max(8, rows + 16));
+  std::vector<int> row_set;
+  for (int r : {lo, hi, tail, 39})
+    if (std::find(row_set.begin(), row_set.end(), r) == row_set.end()) row_set.push_back(r);
   std::vector<ga_tuning> c;
   const int shapes[][2] = {{4, 8}, {4, 16}, {8, 4}, {8, 8}, {16, 2}, {16, 4}, {32, 1}, {32, 2}};
   for (const auto& s : shapes)
-    for (int r : {lo, hi, tail}) c.push_back(ga_tuning{s[0], s[1], r, 1, 0, 0});
+    for (int r : row_set) c.push_back(ga_tuning{s[0], s[1], r, 1, 0, 0});
   for (int regs : {168, 128})
     for (int ppb : {4, 8})
-      for (int r : {lo, hi, tail}) c.push_back(ga_tuning{8, ppb, r, 1, regs, 0});
+      for (int r : row_set) c.push_back(ga_tuning{8, ppb, r, 1, regs, 0});
   return c;
 }
 
