@@ -245,7 +245,10 @@ void server_free(ga_server* s) {
   for (auto& kv : s->handed_out) delete kv.second;
 }
 
-constexpr uint64_t kAsciiStaging = 256ull << 20;  // ASCII bytes admitted per admission (at most)
+// ASCII bytes one admission can stage: an eighth of the budget, between
+// 16 MB and 256 MB (a request larger than that is refused at submission).
+constexpr uint64_t kAsciiStagingMin = 16ull << 20;
+constexpr uint64_t kAsciiStagingMax = 256ull << 20;
 constexpr uint64_t kOutRuns = 16ull << 20;        // runs gathered per step (at most, 64 MB)
 constexpr uint64_t kListPairs = 1ull << 16;       // pairs harvested per step (at most)
 
@@ -335,7 +338,9 @@ extern "C" int ga_server_create(size_t budget_bytes, int W, int O, int k, ga_ser
   const uint64_t spill_bytes = groups * 8ull * ga::kMaxRows * ga::kMaxStride;
   s->max_slots = static_cast<uint32_t>(std::min<uint64_t>(1u << 20, budget_bytes / 8192 + 64));
   const uint64_t per_slot = 8 * 4 + 4 * 6 + 4 * 2 + sizeof(ga::SlotState);
-  const uint64_t fixed = spill_bytes + kAsciiStaging + kOutRuns * 4 + kListPairs * 24 +
+  const uint64_t staging =
+      std::min(kAsciiStagingMax, std::max(kAsciiStagingMin, static_cast<uint64_t>(budget_bytes) / 8));
+  const uint64_t fixed = spill_bytes + staging + kOutRuns * 4 + kListPairs * 24 +
                          static_cast<uint64_t>(s->max_slots) * per_slot;
   if (e == cudaSuccess && budget_bytes < fixed + (64ull << 20)) {
     server_free(s);
@@ -348,7 +353,7 @@ extern "C" int ga_server_create(size_t budget_bytes, int W, int O, int k, ga_ser
   const uint32_t M = s->max_slots;
   if (e == cudaSuccess) e = dev_alloc(s, &s->d_seq, seq_bytes);
   if (e == cudaSuccess) e = dev_alloc(s, &s->d_cigar, cig_runs);
-  if (e == cudaSuccess) e = dev_alloc(s, &s->d_ascii, kAsciiStaging);
+  if (e == cudaSuccess) e = dev_alloc(s, &s->d_ascii, staging);
   if (e == cudaSuccess) e = dev_alloc(s, &s->d_read_off, M);
   if (e == cudaSuccess) e = dev_alloc(s, &s->d_ref_off, M);
   if (e == cudaSuccess) e = dev_alloc(s, &s->d_cigar_off, M);
@@ -368,7 +373,7 @@ extern "C" int ga_server_create(size_t budget_bytes, int W, int O, int k, ga_ser
   if (e == cudaSuccess) e = dev_alloc(s, &s->d_spill, spill_bytes / 8);
   if (e == cudaSuccess) e = dev_alloc(s, &s->d_list, 3 * kListPairs);
   if (e == cudaSuccess) e = dev_alloc(s, &s->d_out, kOutRuns);
-  if (e == cudaSuccess) e = cudaMallocHost(&s->h_ascii, kAsciiStaging);
+  if (e == cudaSuccess) e = cudaMallocHost(&s->h_ascii, staging);
   if (e == cudaSuccess) e = cudaMallocHost(&s->h_meta64, 8ull * 3 * M);
   if (e == cudaSuccess) e = cudaMallocHost(&s->h_meta32, 4ull * 3 * M);
   if (e == cudaSuccess) e = cudaMallocHost(&s->h_active, 4ull * M);
@@ -389,7 +394,7 @@ extern "C" int ga_server_create(size_t budget_bytes, int W, int O, int k, ga_ser
     cudaGetLastError();
     return e == cudaErrorMemoryAllocation ? GA_ENOMEM : GA_ECUDA;
   }
-  s->ascii_cap = kAsciiStaging;
+  s->ascii_cap = staging;
   s->out_cap = kOutRuns;
   s->seq_alloc = RangeAlloc(seq_bytes);
   s->cig_alloc = RangeAlloc(cig_runs);
