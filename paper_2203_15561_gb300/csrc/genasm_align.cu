@@ -228,28 +228,32 @@ cudaError_t launch_plain(const AlignParams& p, cudaStream_t s) {
 // groups run alone (10,000 equal pairs on 4,864 groups: three pair lengths
 // without slices, about 2.06 with them).
 //
-// The FIFO is a bounded ring of n slots (n = pairs, so it can hold every
-// pair) with a sequence number per slot: position x lives in slot x % n; the
-// slot holds position x's pair once its number is x + 1, and is free for
-// position x + n once its number is x + n. A group that wants a pair reserves
-// the next head position with atomicAdd and takes the pair once that position
-// is published; until then it stays idle while the other groups of its warp
-// go on (it checks again after each of their windows), and it stops once no
-// pair is left unfinished. A group that ends a turn claims the tail position
-// with atomicCAS when its slot is free, writes the pair and publishes it; if
-// the slot is not free yet or the claim keeps losing races, the group keeps
-// the pair for another turn. No group ever waits on another, and every pair
+// The FIFO is a bounded ring of 2n slots (n = pairs) with a sequence number
+// per slot: position x lives in slot x % 2n; the slot holds position x's
+// pair once its number is x + 1, and is free for position x + 2n once its
+// number is x + 2n. A group that wants a pair reserves the next head position
+// with atomicAdd and takes the pair once that position is published; until
+// then it stays idle while the other groups of its warp go on (it checks
+// again after each of their windows), and it stops once no pair is left
+// unfinished. A group that ends a turn claims the next tail position with
+// atomicAdd; the slot it lands in held position y - 2n, which was published
+// at least n pushes earlier and taken as soon as its reserver looked (at most
+// n pairs are ever in the ring), so the slot is free; the group writes the
+// pair and publishes it. The wait for a free slot is bounded: should it run
+// out, the group keeps its pair for another turn and flags the launch, and the
+// reserver of the lost position stops with the others at the end. Every pair
 // not yet finished is held by a running group or published in the ring.
 // ---------------------------------------------------------------------------
 
 struct BatchArgs {
   uint32_t* queue;        // [0] hand-out counter (unsliced); ring: [1] head, [2] tail,
                           // [3] pairs not finished, [4] a warp's wait ran out
-  uint32_t* order;        // hand-out order / the ring's slots (nullptr: index order, unsliced)
+  uint32_t* order;        // hand-out order (nullptr: index order)
   uint64_t* spill;        // [groups][kMaxRows * kMaxStride]
   int table_entries;
   uint32_t slice;         // windows per turn (0: a pair runs to its end)
-  uint32_t* ring_seq;     // per ring slot: its sequence number
+  uint32_t* ring;         // 2n ring slots: pair ids
+  uint32_t* ring_seq;     // 2n: each slot's sequence number
   SlotState* state;       // per pair: saved window state (all zero: not started)
 };
 
@@ -259,42 +263,41 @@ constexpr uint32_t kNoPair = 0xffffffffu;
 // longest pair); past it the warp stops and flags the launch.
 constexpr uint32_t kRingPolls = 25u * 1000u * 1000u;
 
+// Polls of a push waiting for its slot: a fifth of a second at most.
+constexpr uint32_t kPushPolls = 1000u * 1000u;
+
 // The pair at reserved ring position x, or kNoPair while it is not published.
-__device__ __forceinline__ uint32_t ring_take(const BatchArgs& a, uint32_t n, uint32_t x) {
+__device__ __forceinline__ uint32_t ring_take(const BatchArgs& a, uint32_t cap, uint32_t x) {
   volatile uint32_t* seq = a.ring_seq;
-  volatile uint32_t* slot = a.order;
-  const uint32_t s = x % n;
+  volatile uint32_t* slot = a.ring;
+  const uint32_t s = x % cap;
   if (seq[s] != x + 1u) return kNoPair;
   __threadfence();
   const uint32_t pair = slot[s];
   __threadfence();
-  seq[s] = x + n;  // free for position x + n
+  seq[s] = x + cap;  // free for position x + cap
   return pair;
 }
 
-// Puts a pair (its state already saved) at the ring's tail; false when the
-// tail slot is not free yet or the claim lost too many races.
-__device__ __forceinline__ bool ring_try_push(const BatchArgs& a, uint32_t n, uint32_t pair) {
-  volatile uint32_t* tail = a.queue + 2;
+// Puts a pair (its state already saved) at the ring's tail; false (the pair
+// stays with its group) only if the slot's wait ran out.
+__device__ __forceinline__ bool ring_push(const BatchArgs& a, uint32_t cap, uint32_t pair) {
   volatile uint32_t* seq = a.ring_seq;
-  volatile uint32_t* slot = a.order;
+  volatile uint32_t* slot = a.ring;
   __threadfence();  // the saved state before the publication
-  for (int tries = 0; tries < 16; ++tries) {
-    const uint32_t t = *tail;
-    const uint32_t s = t % n;
-    const uint32_t q = seq[s];
-    if (q == t) {
-      if (atomicCAS(a.queue + 2, t, t + 1u) == t) {
-        slot[s] = pair;
-        __threadfence();
-        seq[s] = t + 1u;
-        return true;
-      }
-    } else if (q != t + 1u) {
-      return false;  // the slot still holds position t - n
+  const uint32_t y = atomicAdd(a.queue + 2, 1u);
+  const uint32_t s = y % cap;
+  for (uint32_t polls = 0; seq[s] != y; ++polls) {
+    if (polls == kPushPolls) {
+      atomicExch(a.queue + 4, 1u);
+      return false;
     }
+    __nanosleep(200);
   }
-  return false;
+  slot[s] = pair;
+  __threadfence();
+  seq[s] = y + 1u;
+  return true;
 }
 
 constexpr int kSpillEntries = kMaxRows * kMaxStride;
@@ -328,7 +331,7 @@ __device__ __forceinline__ void batched_body(const AlignParams& p, const BatchAr
     if (want && r == 0) {
       if (a.slice) {
         if (resv == kNoPair) resv = atomicAdd(a.queue + 1, 1u);
-        pair = ring_take(a, p.n_pairs, resv);
+        pair = ring_take(a, 2u * p.n_pairs, resv);
         if (pair != kNoPair) resv = kNoPair;
         else quit = *reinterpret_cast<volatile uint32_t*>(a.queue + 3) == 0u;  // all finished
       } else {
@@ -386,7 +389,7 @@ __device__ __forceinline__ void batched_body(const AlignParams& p, const BatchAr
       uint32_t pushed = 0;
       if (turn_end && r == 0) {
         save_pair(st, a.state[st.pair]);
-        pushed = ring_try_push(a, p.n_pairs, st.pair) ? 1u : 0u;
+        pushed = ring_push(a, 2u * p.n_pairs, st.pair) ? 1u : 0u;
       }
       pushed = __shfl_sync(kFull, pushed, gbase);
       if (turn_end) {
@@ -505,8 +508,7 @@ int band_top_for(int O) { return O >= 16 ? std::min(22, O - 1) : -1; }
 // Shorter turns cost more than they save: 8 windows made workload 2 18%
 // slower, 32 about even, 64 2% faster than no turns.
 uint32_t slice_for(uint32_t n_pairs, const BatchPlan& plan) {
-  // A ring of one slot could not tell "position x published" (x + 1) from
-  // "free for position x + 1" (x + 1): a single pair runs unsliced.
+  // A single pair has nobody to take turns with.
   if (plan.slice_windows < 0 || n_pairs < 2) return 0u;
   if (plan.slice_windows > 0) return static_cast<uint32_t>(plan.slice_windows);
   const uint64_t groups = static_cast<uint64_t>(plan.blocks) * plan.pairs_per_block;
@@ -593,17 +595,19 @@ cudaError_t launch_lpt_order(const uint32_t* read_len, uint32_t n, uint32_t* his
   return cudaGetLastError();
 }
 
-// The ring of the sliced queue starts full: slot x holds hand-out position x
-// (the LPT order, or pair x), published with sequence number x + 1.
-__global__ void ring_init_kernel(uint32_t n, bool identity, uint32_t* __restrict__ slot,
-                                 uint32_t* __restrict__ seq, uint32_t* __restrict__ queue) {
+// The ring of the sliced queue (2n slots) starts with every pair: slot x < n
+// holds hand-out position x (the LPT order, or pair x), published with
+// sequence number x + 1; slots n..2n-1 are free for positions n..2n-1.
+__global__ void ring_init_kernel(uint32_t n, const uint32_t* __restrict__ order,
+                                 uint32_t* __restrict__ ring, uint32_t* __restrict__ seq,
+                                 uint32_t* __restrict__ queue) {
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    queue[2] = n;  // tail: the ring starts full
+    queue[2] = n;  // tail: the ring starts with every pair
     queue[3] = n;  // pairs not finished
   }
-  for (uint32_t x = blockIdx.x * blockDim.x + threadIdx.x; x < n; x += gridDim.x * blockDim.x) {
-    if (identity) slot[x] = x;
-    seq[x] = x + 1u;
+  for (uint32_t x = blockIdx.x * blockDim.x + threadIdx.x; x < 2u * n; x += gridDim.x * blockDim.x) {
+    if (x < n) ring[x] = order ? order[x] : x;
+    seq[x] = x < n ? x + 1u : x;
   }
 }
 
@@ -614,8 +618,9 @@ WorkspaceLayout workspace_layout(uint32_t n_pairs, const BatchPlan& plan) {
   L.hist = up(L.queue + 256);
   L.order = up(L.hist + sizeof(uint32_t) * kLptBuckets);
   L.locate = up(L.order + sizeof(uint32_t) * static_cast<size_t>(n_pairs));
-  L.ring_seq = up(L.locate + sizeof(int32_t) * static_cast<size_t>(n_pairs));
-  L.state = up(L.ring_seq + sizeof(uint32_t) * static_cast<size_t>(n_pairs));
+  L.ring = up(L.locate + sizeof(int32_t) * static_cast<size_t>(n_pairs));
+  L.ring_seq = up(L.ring + 2 * sizeof(uint32_t) * static_cast<size_t>(n_pairs));
+  L.state = up(L.ring_seq + 2 * sizeof(uint32_t) * static_cast<size_t>(n_pairs));
   L.spill = up(L.state + sizeof(SlotState) * static_cast<size_t>(n_pairs));
   const size_t groups = static_cast<size_t>(plan.blocks) * plan.pairs_per_block;
   L.total = up(L.spill + groups * sizeof(uint64_t) * kSpillEntries);
@@ -635,17 +640,19 @@ cudaError_t launch_batched(const AlignParams& p, const BatchPlan& plan, void* ws
   if (plan.lpt && (e = launch_lpt_order(p.read_len, p.n_pairs, hist, order, s)) != cudaSuccess)
     return e;
   const uint32_t slice = spill_area ? slice_for(p.n_pairs, plan) : 0u;
+  uint32_t* ring = reinterpret_cast<uint32_t*>(w + L.ring);
   uint32_t* ring_seq = reinterpret_cast<uint32_t*>(w + L.ring_seq);
   SlotState* state = reinterpret_cast<SlotState*>(w + L.state);
   if (slice) {
     if ((e = cudaMemsetAsync(state, 0, sizeof(SlotState) * p.n_pairs, s)) != cudaSuccess) return e;
     const int blocks = static_cast<int>(std::min<uint32_t>((p.n_pairs + 255) / 256, 1024u));
-    ring_init_kernel<<<blocks, 256, 0, s>>>(p.n_pairs, !plan.lpt, order, ring_seq, queue);
+    ring_init_kernel<<<blocks, 256, 0, s>>>(p.n_pairs, plan.lpt ? order : nullptr, ring,
+                                            ring_seq, queue);
     count_launches(1);
   }
-  BatchArgs a{queue, (plan.lpt || slice) ? order : nullptr,
+  BatchArgs a{queue, plan.lpt ? order : nullptr,
               spill_area ? reinterpret_cast<uint64_t*>(w + L.spill) : nullptr, plan.table_entries,
-              slice, ring_seq, state};
+              slice, ring, ring_seq, state};
   const int threads = plan.pairs_per_block * plan.lanes_per_pair;
   AlignParams q = p;
   q.band_top = plan.band_top;

@@ -63,7 +63,8 @@ struct WorkspaceLayout {
   size_t hist;    // uint32[kLptBuckets]
   size_t order;   // uint32[n_pairs]
   size_t locate;  // int32[n_pairs]: the locate step's edit counts
-  size_t ring_seq;  // uint32[n_pairs]: sequence numbers of the sliced queue's ring
+  size_t ring;    // uint32[2 n_pairs]: slots of the sliced queue's ring
+  size_t ring_seq;  // uint32[2 n_pairs]: their sequence numbers
   size_t state;   // SlotState[n_pairs]: window state of pairs between turns
   size_t spill;   // uint64[groups][kMaxRows * kMaxCols]
   size_t total;
