@@ -75,7 +75,8 @@ def parse():
     ap.add_argument("--no-free", action="store_true",
                     help="skip the free-start first window leg (ga_align_batch_locate)")
     ap.add_argument("--tuning", default="",
-                    help="G,pairs_per_block,table_rows: fixed tuning of the batched kernel instead of the autotuner")
+                    help="G,pairs_per_block,table_rows[,max_registers[,slice_windows]]: fixed tuning "
+                         "of the batched kernel instead of the autotuner")
     return ap.parse_args()
 
 
@@ -271,8 +272,9 @@ def run_ours(args):
 
     # ---- batched (the headline): autotuned, alignment replayed from a CUDA graph ----
     if args.tuning:
-        g_, ppb_, rows_ = (int(v) for v in args.tuning.split(","))
-        ga.ga_tuning_set(W, O, K, ga.ga_tuning(g_, ppb_, rows_, 1, 0))
+        fields = [int(v) for v in args.tuning.split(",")] + [0, 0]
+        g_, ppb_, rows_, regs_, slice_ = fields[:5]
+        ga.ga_tuning_set(W, O, K, ga.ga_tuning(g_, ppb_, rows_, 1, regs_, slice_))
         tuned, tune_ms = ga.ga_tuning_get(W, O, K), None
         db.run("batched")  # sizes the workspace for the fixed tuning
     else:
@@ -346,6 +348,7 @@ def run_ours(args):
                 "peak_source": "measured on this GPU by ga_measure_int_peak (DC cell mix: 2 SHF + 4 LOP3)",
                 "peak_lop3": peaks[0] / 1e12, "peak_shf": peaks[1] / 1e12,
                 "algorithmic_ops_per_launch": cells * OPS_PER_CELL, "cells_per_launch": cells,
+                "rows_per_window": _rows_per_window(res.cells, res.n_windows),
                 "windows_per_launch": windows, "align_ms": align_ms, "pack_ms": pack_ms}
     # Shared-memory side (secondary bound): the DC stores rows 0..d_min of the
     # W-O+1 traceback columns of a window as 4-byte band entries (cells x
@@ -439,9 +442,11 @@ def run_ours(args):
             "config": {"workload": WORKLOAD_NAMES[args.workload],
                        "W": W, "O": O, "k": K, "pairs_per_gpu": n, "read_bases_per_gpu": read_bases,
                        "kernel": "batched (persistent, LPT work queue, CUDA graph)",
-                       ("tuning" if args.tuning else "autotuned"): {"lanes_per_pair": tuned.lanes_per_pair,
-                                     "pairs_per_block": tuned.pairs_per_block,
-                                     "table_rows": tuned.table_rows, "tune_ms": tune_ms},
+                       ("tuning" if args.tuning else "autotuned"): {**tuned.as_dict(),
+                                                                           "tune_ms": tune_ms},
+                       "queue": "FIFO ring of pairs in turns of windows (slice_windows 0: turns of "
+                                "64 when the pairs outnumber the resident groups less than 16 times "
+                                "over, as here; -1: each pair to its end)",
                        "l2": "no flush: each step streams 210 MB of ASCII input (> 126 MB L2) and "
                              "writes ~0.5 GB of CIGAR runs, which evicts the previous step's data"},
             "gbases_per_s": gbases,
@@ -486,10 +491,17 @@ def run_serving(args, dev):
     Gbases, would take the input generator tens of minutes). Every request is
     copied into the server at submission, so reuse shares no work. Latency =
     arrival -> result visible on the host. Every served request is checked
-    against the oracle's result for its pool pairs (after the timed span).
-    A second span offers ten times the load (20,000 requests/s) to find the
-    server's capacity and its latency when saturated."""
+    against the oracle's result for its pool pairs (aligned on the host cores
+    before the span) by a checker thread while the span runs: distances,
+    statuses, reference ends and every CIGAR run (libc memcmp against the
+    oracle's arrays), each result released once it is checked. Keeping the
+    results for a later check would hold the whole span's CIGARs (about 100 GB
+    for 60 s) in host memory. A second span offers ten times the load (20,000
+    requests/s) to find the server's capacity and its latency when
+    saturated."""
+    import collections
     import ctypes
+    import queue
     import torch
     import oracle
     import paper_2203_15561_gb300 as ga
@@ -500,6 +512,55 @@ def run_serving(args, dev):
     reads_p, refs_p = pool.reads.ctypes.data, pool.refs.ctypes.data
     f_poll = ga._typed("ga_server_poll", ga._i, [ga._vp, ctypes.POINTER(ga.ga_result), ga._i,
                                                  ctypes.POINTER(ga._i)])
+    ref = oracle.align(pool, W=W, O=O, k=K)  # the pool pairs, once, before the spans
+
+    class RawResult(ctypes.Structure):  # ga_result with its pointers read as addresses
+        _fields_ = [("ticket", ctypes.c_uint64), ("tag", ctypes.c_uint64),
+                    ("n_pairs", ctypes.c_uint32), ("dist", ctypes.c_void_p),
+                    ("status", ctypes.c_void_p), ("ref_consumed", ctypes.c_void_p),
+                    ("cigar_off", ctypes.c_void_p), ("cigar", ctypes.c_void_p),
+                    ("submit_ms", ctypes.c_double), ("admit_ms", ctypes.c_double),
+                    ("done_ms", ctypes.c_double)]
+
+    libc = ctypes.CDLL(None)
+    memcmp = libc.memcmp
+    memcmp.restype = ctypes.c_int
+    memcmp.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]
+    ref_cigar = ref.cigar.ctypes.data
+
+    def check_results(ids, work, done, bad):
+        """Checker thread: compares each queued result with the oracle and
+        hands its ticket back for release."""
+        scal = np.empty((3, 64), np.int32)
+        offs = np.empty(65, np.uint64)
+        a_scal, a_offs = scal.ctypes.data, offs.ctypes.data
+        while True:
+            item = work.get()
+            if item is None:
+                return
+            i, ticket, n, a_dist, a_status, a_rc, a_off, a_cig = item
+            q = ids[i]
+            ok = n == len(q) and n <= 64
+            if ok and n:
+                ctypes.memmove(a_scal, a_dist, 4 * n)
+                ctypes.memmove(a_scal + 256, a_status, 4 * n)
+                ctypes.memmove(a_scal + 512, a_rc, 4 * n)
+                ctypes.memmove(a_offs, a_off, 8 * (n + 1))
+                off = offs[:n + 1].astype(np.int64)
+                cnt = np.diff(off)
+                ok = (np.array_equal(scal[0, :n], ref.dist[q]) and np.array_equal(scal[1, :n], ref.status[q])
+                      and np.array_equal(scal[2, :n], ref.ref_consumed[q])
+                      and np.array_equal(cnt, ref.n_runs[q].astype(np.int64)))
+                if ok:
+                    src = (a_cig + 4 * off[:-1]).tolist()
+                    dst = (ref_cigar + 4 * ref.cigar_off[q].astype(np.int64)).tolist()
+                    for x, y, b in zip(src, dst, (4 * cnt).tolist()):
+                        if b and memcmp(x, y, b) != 0:
+                            ok = False
+                            break
+            if not ok:
+                bad.append(i)
+            done.append(ticket)
 
     def serve(rate, seconds, seed, check):
         reqs = datagen.make_requests(rate, seconds, seed=seed)
@@ -514,14 +575,21 @@ def run_serving(args, dev):
         ga.ga_server_set_step_windows(srv, STEP_WINDOWS)
         n_req = len(reqs)
         lat = np.zeros(n_req)
-        got = [None] * n_req if check else None
+        work, done_t, bad = queue.SimpleQueue(), collections.deque(), []
+        checker = None
+        if check:
+            checker = threading.Thread(target=check_results, args=(ids, work, done_t, bad), daemon=True)
+            checker.start()
         pairs = bases = steps = 0
-        buf = (ga.ga_result * 1024)()
+        raw = (RawResult * 1024)()
+        buf = ctypes.cast(raw, ctypes.POINTER(ga.ga_result))
         nres = ga._i(0)
         launches0 = ga.ga_launch_count()
         t0 = time.perf_counter()
         nxt = done = inflight = 0
         while done < n_req:
+            while done_t:
+                ga.ga_server_release(srv, done_t.popleft())
             now = time.perf_counter() - t0
             while nxt < n_req and arrivals[nxt] <= now:
                 ro, rl, fo, fl = meta[nxt]
@@ -541,48 +609,41 @@ def run_serving(args, dev):
                     break
                 t = time.perf_counter() - t0
                 for q in range(nres.value):
-                    r = buf[q]
-                    i = int(r.tag)
+                    r = raw[q]
+                    i = r.tag
                     lat[i] = 1e3 * (t - arrivals[i])
-                    n = int(r.n_pairs)
+                    n = r.n_pairs
                     pairs += n
                     bases += int(meta[i][1].sum())
                     if check:
-                        off = np.ctypeslib.as_array(r.cigar_off, shape=(n + 1,)).copy()
-                        got[i] = (np.ctypeslib.as_array(r.dist, shape=(n,)).copy(),
-                                  np.ctypeslib.as_array(r.status, shape=(n,)).copy(),
-                                  np.ctypeslib.as_array(r.ref_consumed, shape=(n,)).copy(), off,
-                                  np.ctypeslib.as_array(r.cigar, shape=(int(off[-1]),)).copy()
-                                  if off[-1] else np.zeros(0, np.uint32))
-                    ga.ga_server_release(srv, r.ticket)
+                        work.put((i, r.ticket, n, r.dist, r.status, r.ref_consumed, r.cigar_off, r.cigar))
+                    else:
+                        ga.ga_server_release(srv, r.ticket)
                 done += nres.value
                 inflight -= nres.value
         wall = time.perf_counter() - t0
         launches = ga.ga_launch_count() - launches0
+        if checker is not None:
+            work.put(None)
+            checker.join()
+            while done_t:
+                ga.ga_server_release(srv, done_t.popleft())
         ga.ga_server_destroy(srv)
         out = {"offered_requests_per_s": rate, "seconds_of_arrivals": seconds, "requests": n_req,
                "pairs": pairs, "read_bases": bases, "wall_s": wall, "pairs_per_s": pairs / wall,
                "gbases_per_s": bases / wall / 1e9, "offered_pairs_per_s": sum(len(q) for q in ids) / seconds,
                "steps": steps, "step_windows": STEP_WINDOWS, "budget_bytes": budget,
                "kernel_launches": launches, **_percentiles(lat)}
-        return out, ids, got
+        if check:
+            out["oracle_check"] = {"requests": n_req, "differing_requests": len(bad),
+                                   "pairs": int(sum(len(q) for q in ids)),
+                                   "how": "checker thread during the span: distances, statuses, "
+                                          "reference ends, run counts and every CIGAR run "
+                                          "against the oracle"}
+        return out
 
-    served, ids, got = serve(2000.0, args.serve_seconds, 5, True)
-    # Every served request against the oracle (pool pairs aligned once on the host cores).
-    ref = oracle.align(pool, W=W, O=O, k=K)
-    bad = 0
-    for q, (d, st, rc, off, runs) in zip(ids, got):
-        ok = (np.array_equal(d, ref.dist[q]) and np.array_equal(st, ref.status[q])
-              and np.array_equal(rc, ref.ref_consumed[q]))
-        if ok:
-            for p, pid in enumerate(q):
-                if not np.array_equal(runs[off[p]:off[p + 1]], ref.runs(int(pid))):
-                    ok = False
-                    break
-        bad += 0 if ok else 1
-    served["oracle_check"] = {"requests": len(got), "differing_requests": bad,
-                              "pairs": int(sum(len(q) for q in ids))}
-    saturated, _, _ = serve(20000.0, args.saturate_seconds, 6, False)
+    served = serve(2000.0, args.serve_seconds, 5, True)
+    saturated = serve(20000.0, args.saturate_seconds, 6, False)
 
     # -- plain per-request launch: each request alone, in arrival order --
     reqs = datagen.make_requests(2000.0, args.plain_serve_seconds, seed=5)
