@@ -799,6 +799,8 @@ def run_ablation(db, dev, align_ms):
     import torch
 
     n = db.n
+    db.run("batched", stats=True)  # the production outputs (earlier legs may leave others)
+    torch.cuda.synchronize(dev)
     ref = [t[:n].clone() for t in (db.dist, db.status, db.ref_consumed, db.n_runs, db.n_windows,
                                     db.cells)]
     tb = torch.zeros(5 * n, dtype=torch.int64, device=dev)
