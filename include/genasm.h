@@ -62,6 +62,9 @@ typedef struct CUstream_st* ga_stream_t; /* = cudaStream_t; NULL = legacy defaul
 #define GA_PAIR_EXCEEDS_K 1   /* some window's minimum edit count is above k */
 #define GA_PAIR_CIGAR_FULL 2  /* the pair's CIGAR capacity was too small */
 #define GA_PAIR_TB_STUCK 3    /* internal: traceback found no edge */
+#define GA_PAIR_TIMED_OUT 4   /* a bounded wait of the device work queue ran out before the
+                                 pair finished (distance and ref_consumed -1, no CIGAR runs);
+                                 the pairs that finished in the same call are valid */
 
 /* CIGAR op codes (BAM). */
 #define GA_OP_INS 1
@@ -315,6 +318,20 @@ int ga_cigar_compact_workspace_size(uint32_t n_pairs, size_t* bytes_out);
  * process (all threads, all devices). Used to account for device work.
  */
 uint64_t ga_launch_count(void);
+
+/*
+ * ga_set_queue_wait_limits - bounds, in polls of about 0.2 microseconds, of
+ * the two waits of the batched kernel's sliced work queue (ga_tuning
+ * slice_windows): a warp whose groups all wait for a published pair, and a
+ * group waiting for its ring slot at the end of a turn. 0 restores a default
+ * (seconds: far beyond any legitimate wait). A wait that runs out ends its
+ * group's work instead of hanging; pairs left unfinished report
+ * GA_PAIR_TIMED_OUT. The defaults are never reached in normal operation;
+ * short bounds exist to test that path. Applies to later launches (a
+ * captured CUDA graph keeps the bounds it was captured with). Process-wide.
+ * Returns GA_OK.
+ */
+int ga_set_queue_wait_limits(uint32_t idle_polls, uint32_t push_polls);
 
 /*
  * ga_measure_int_peak - measures, on the current device, the throughput of

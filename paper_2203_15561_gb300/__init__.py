@@ -31,6 +31,7 @@ GA_PAIR_OK = 0
 GA_PAIR_EXCEEDS_K = 1
 GA_PAIR_CIGAR_FULL = 2
 GA_PAIR_TB_STUCK = 3
+GA_PAIR_TIMED_OUT = 4
 
 GA_OP_INS = 1
 GA_OP_DEL = 2
@@ -193,6 +194,11 @@ def ga_cigar_compact(d_cigar, d_cigar_off, d_n_runs, n_pairs: int, d_out, out_ca
 
 def ga_launch_count() -> int:
     return int(lib().ga_launch_count())
+
+
+def ga_set_queue_wait_limits(idle_polls: int = 0, push_polls: int = 0) -> int:
+    f = _typed("ga_set_queue_wait_limits", _i, [_u32, _u32])
+    return _check(f(idle_polls, push_polls), "ga_set_queue_wait_limits")
 
 
 def ga_measure_int_peak(stream=None) -> tuple[float, float, float]:

@@ -2,6 +2,7 @@
 // persistent form with a device work queue. Both run the same per-window
 // code (genasm_window.cuh) and produce identical outputs.
 #include <algorithm>
+#include <atomic>
 #include <cstdint>
 
 #include <cuda_runtime.h>
@@ -255,15 +256,17 @@ struct BatchArgs {
   uint32_t* ring;         // 2n ring slots: pair ids
   uint32_t* ring_seq;     // 2n: each slot's sequence number
   SlotState* state;       // per pair: saved window state (all zero: not started)
+  uint32_t idle_polls;    // bound of a warp's wait for a published pair
+  uint32_t push_polls;    // bound of a push's wait for its slot
 };
 
 constexpr uint32_t kNoPair = 0xffffffffu;
-// Polls of a warp whose groups all wait for a pair (about 0.2 microseconds
-// each): seconds, far beyond any legitimate wait (the rest of the
-// longest pair); past it the warp stops and flags the launch.
+// Default bounds of the two waits (ga_set_queue_wait_limits changes them):
+// polls of a warp whose groups all wait for a pair (about 0.2 microseconds
+// each): seconds, far beyond any legitimate wait (the rest of the longest
+// pair); past it the warp stops and flags the launch. Polls of a push waiting
+// for its slot: a fifth of a second at most.
 constexpr uint32_t kRingPolls = 25u * 1000u * 1000u;
-
-// Polls of a push waiting for its slot: a fifth of a second at most.
 constexpr uint32_t kPushPolls = 1000u * 1000u;
 
 // The pair at reserved ring position x, or kNoPair while it is not published.
@@ -288,7 +291,7 @@ __device__ __forceinline__ bool ring_push(const BatchArgs& a, uint32_t cap, uint
   const uint32_t y = atomicAdd(a.queue + 2, 1u);
   const uint32_t s = y % cap;
   for (uint32_t polls = 0; seq[s] != y; ++polls) {
-    if (polls == kPushPolls) {
+    if (polls >= a.push_polls) {
       atomicExch(a.queue + 4, 1u);
       return false;
     }
@@ -374,7 +377,7 @@ __device__ __forceinline__ void batched_body(const AlignParams& p, const BatchAr
     } else {
       // Every group of the warp waits for a pair: poll again shortly.
       __nanosleep(200);
-      if (++idle == kRingPolls) {
+      if (++idle >= a.idle_polls) {
         if (lane == 0) atomicExch(a.queue + 4, 1u);
         drained = true;
       }
@@ -505,8 +508,10 @@ int band_top_for(int O) { return O >= 16 ? std::min(22, O - 1) : -1; }
 // Windows per turn of the sliced queue: the plan's choice, else turns of 64
 // windows when the pairs outnumber the resident groups less than 16 times
 // over (more pairs than that leave a tail of under a sixteenth of a round).
-// Shorter turns cost more than they save: 8 windows made workload 2 18%
-// slower, 32 about even, 64 2% faster than no turns.
+// Measured on 10,000 pairs of 10 kb (2.06 rounds of the grid): turns of 64
+// windows 14% faster than none, of 8, 16, 32 and 128 windows 18%, 9%, 3% and
+// 8% slower than 64; on 200,000 pairs of 100 bp-50 kb (longest first, every
+// warp ends within 0.01 ms of the others without turns) turns of 64 cost 8%.
 uint32_t slice_for(uint32_t n_pairs, const BatchPlan& plan) {
   // A single pair has nobody to take turns with.
   if (plan.slice_windows < 0 || n_pairs < 2) return 0u;
@@ -597,18 +602,39 @@ cudaError_t launch_lpt_order(const uint32_t* read_len, uint32_t n, uint32_t* his
 
 // The ring of the sliced queue (2n slots) starts with every pair: slot x < n
 // holds hand-out position x (the LPT order, or pair x), published with
-// sequence number x + 1; slots n..2n-1 are free for positions n..2n-1.
+// sequence number x + 1; slots n..2n-1 are free for positions n..2n-1. Every
+// pair starts as timed out (distance and reference end -1, no runs): a pair
+// that finishes overwrites it, and one left in the ring when a bounded wait
+// ran out keeps it.
 __global__ void ring_init_kernel(uint32_t n, const uint32_t* __restrict__ order,
                                  uint32_t* __restrict__ ring, uint32_t* __restrict__ seq,
-                                 uint32_t* __restrict__ queue) {
+                                 uint32_t* __restrict__ queue, int32_t* __restrict__ status,
+                                 int32_t* __restrict__ dist, int32_t* __restrict__ ref_consumed,
+                                 uint32_t* __restrict__ n_runs) {
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     queue[2] = n;  // tail: the ring starts with every pair
     queue[3] = n;  // pairs not finished
   }
   for (uint32_t x = blockIdx.x * blockDim.x + threadIdx.x; x < 2u * n; x += gridDim.x * blockDim.x) {
-    if (x < n) ring[x] = order ? order[x] : x;
+    if (x < n) {
+      ring[x] = order ? order[x] : x;
+      status[x] = kPairTimedOut;
+      dist[x] = -1;
+      ref_consumed[x] = -1;
+      n_runs[x] = 0u;
+    }
     seq[x] = x < n ? x + 1u : x;
   }
+}
+
+namespace {
+std::atomic<uint32_t> g_idle_polls{kRingPolls};
+std::atomic<uint32_t> g_push_polls{kPushPolls};
+}  // namespace
+
+void set_queue_wait_limits(uint32_t idle_polls, uint32_t push_polls) {
+  g_idle_polls.store(idle_polls ? idle_polls : kRingPolls, std::memory_order_relaxed);
+  g_push_polls.store(push_polls ? push_polls : kPushPolls, std::memory_order_relaxed);
 }
 
 WorkspaceLayout workspace_layout(uint32_t n_pairs, const BatchPlan& plan) {
@@ -647,12 +673,14 @@ cudaError_t launch_batched(const AlignParams& p, const BatchPlan& plan, void* ws
     if ((e = cudaMemsetAsync(state, 0, sizeof(SlotState) * p.n_pairs, s)) != cudaSuccess) return e;
     const int blocks = static_cast<int>(std::min<uint32_t>((p.n_pairs + 255) / 256, 1024u));
     ring_init_kernel<<<blocks, 256, 0, s>>>(p.n_pairs, plan.lpt ? order : nullptr, ring,
-                                            ring_seq, queue);
+                                            ring_seq, queue, p.status, p.dist,
+                                            p.ref_consumed, p.n_runs);
     count_launches(1);
   }
   BatchArgs a{queue, plan.lpt ? order : nullptr,
               spill_area ? reinterpret_cast<uint64_t*>(w + L.spill) : nullptr, plan.table_entries,
-              slice, ring, ring_seq, state};
+              slice, ring, ring_seq, state, g_idle_polls.load(std::memory_order_relaxed),
+              g_push_polls.load(std::memory_order_relaxed)};
   const int threads = plan.pairs_per_block * plan.lanes_per_pair;
   AlignParams q = p;
   q.band_top = plan.band_top;

@@ -148,6 +148,11 @@ int ga_workspace_size_tuned(uint32_t n_pairs, int W, int O, int k, const ga_tuni
 
 uint64_t ga_launch_count(void) { return ga::launch_count(); }
 
+int ga_set_queue_wait_limits(uint32_t idle_polls, uint32_t push_polls) {
+  ga::set_queue_wait_limits(idle_polls, push_polls);
+  return GA_OK;
+}
+
 int ga_cigar_compact_workspace_size(uint32_t n_pairs, size_t* bytes_out) {
   if (!bytes_out) return GA_EINVAL;
   *bytes_out = ga::compact_workspace_bytes(n_pairs);

@@ -109,6 +109,8 @@ cudaError_t wide_workspace_bytes(uint32_t n_pairs, size_t* bytes);
 cudaError_t launch_wide(const AlignParams& p, bool lpt, void* ws, size_t ws_bytes, cudaStream_t s);
 
 // Ablation kernels (genasm_ablation.cu): variant 0..3, see ga_align_ablation.
+// Bounds of the sliced queue's waits (polls; 0 = the default of seconds).
+void set_queue_wait_limits(uint32_t idle_polls, uint32_t push_polls);
 cudaError_t ablation_workspace_bytes(uint32_t n_pairs, int variant, size_t* bytes);
 cudaError_t launch_ablation(const AlignParams& p, int variant, uint64_t* table_bytes, void* ws,
                             size_t ws_bytes, cudaStream_t s);

@@ -49,7 +49,13 @@ constexpr int kMaxStride = 66;       // even row stride >= kMaxCols
 constexpr uint32_t kFull = 0xffffffffu;
 
 enum : uint32_t { kOpIns = 1, kOpDel = 2, kOpMatch = 7, kOpSubst = 8, kOpStuck = 15 };
-enum : int32_t { kPairOk = 0, kPairExceedsK = 1, kPairCigarFull = 2, kPairTbStuck = 3 };
+enum : int32_t {
+  kPairOk = 0,
+  kPairExceedsK = 1,
+  kPairCigarFull = 2,
+  kPairTbStuck = 3,
+  kPairTimedOut = 4  // a bounded wait of the work queue ran out before the pair finished
+};
 
 // Table row stride for `ncols` stored columns: the smallest even value, so
 // that every row starts on a 16-byte boundary and a lane can store two
