@@ -213,7 +213,18 @@ __global__ void gather_runs_kernel(const uint32_t* __restrict__ cigar, const uin
     const uint32_t* src = cigar + cigar_off[p];
     uint32_t* dst = out + out_off[p];
     const uint32_t cnt = n_runs[p];
-    for (uint32_t x = lane; x < cnt; x += 32) dst[x] = __ldcs(src + x);
+    // Four loads in flight per lane (the copy is bound by memory latency,
+    // not bandwidth, with one warp per pair).
+    uint32_t x = lane;
+    for (; x + 96 < cnt; x += 128) {
+      const uint32_t v0 = __ldcs(src + x), v1 = __ldcs(src + x + 32);
+      const uint32_t v2 = __ldcs(src + x + 64), v3 = __ldcs(src + x + 96);
+      dst[x] = v0;
+      dst[x + 32] = v1;
+      dst[x + 64] = v2;
+      dst[x + 96] = v3;
+    }
+    for (; x < cnt; x += 32) dst[x] = __ldcs(src + x);
   }
 }
 

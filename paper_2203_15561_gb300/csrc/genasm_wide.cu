@@ -33,9 +33,13 @@ namespace {
 
 using u128 = unsigned __int128;
 
-constexpr int kWW = 128;             // widest window
+constexpr int kWW = 128;             // widest window (the window columns of a build: WW = 96 or 128)
 constexpr int kWRows = kWW + 1;      // rows 0..128
 constexpr int kWStride = kWW + 2;    // entries per table row (columns 0..wt, even)
+// Windows of at most 96 bases run on a 96-column build: 6 columns per lane
+// instead of 8, a quarter less DC work than on the 128-column grid.
+constexpr int kWW96 = 96;
+constexpr int ww_for(int W) { return W <= kWW96 ? kWW96 : kWW; }
 constexpr int kWG = 16;              // lanes per pair
 constexpr int kWThreads = 128;       // threads per block (kWThreads / kWG pairs)
 constexpr size_t kWTableEntries = static_cast<size_t>(kWRows) * kWStride;
@@ -45,7 +49,7 @@ constexpr int kWBandMinO = 24;       // band tables need O >= 24 (A >= 23)
 int wide_band_top(int O) { return O >= kWBandMinO ? std::min(kWBandTop, O - 1) : -1; }
 // Band table row stride (entries): columns 0..W-O, whole chunks of a lane's columns.
 int wide_band_stride(int W, int O) {
-  constexpr int C = kWW / kWG;
+  const int C = ww_for(W) / kWG;
   return (W - O + 1 + C - 1) / C * C;
 }
 
@@ -71,11 +75,11 @@ __device__ __forceinline__ u128 ldg128(const u128* p) {
 // Pattern masks by ballots within the group (lane r contributes bit j = r + Gq)
 // and the PM[T[i]] columns i = r + Gq (all ones at i >= wt). Groups with ga
 // false take part in the ballots only.
-template <int G>
+template <int G, int WW>
 __device__ __forceinline__ void wide_masks(bool ga, int r, int gbase, const uint8_t* read,
                                            uint32_t pos_p, int wp, const uint8_t* ref,
                                            uint32_t pos_t, int wt, u128* pmcol) {
-  constexpr int Q = kWW / G;
+  constexpr int Q = WW / G;
   u128 L = 0, H = 0;
   uint32_t ct[Q];
 #pragma unroll
@@ -106,11 +110,11 @@ __device__ __forceinline__ void wide_masks(bool ga, int r, int gbase, const uint
 // the 64-bit band entries of a window that is not the last (kBand). Returns
 // d_min, or -1 above kmax or for a group with ga false (which only takes
 // part in the warp's votes).
-template <int G, bool kBand>
+template <int G, bool kBand, int WW>
 __device__ __forceinline__ int wide_dc(bool ga, int r, int gbase, int wp, int wt, int kmax,
                                        int ncols, int S, int store_rows, int band_top,
                                        const u128* pmcol, void* tabv) {
-  constexpr int C = kWW / G;
+  constexpr int C = WW / G;
   const int c0 = r * C;
   u128* tab = static_cast<u128*>(tabv);
   uint64_t* btab = static_cast<uint64_t*>(tabv);
@@ -126,7 +130,7 @@ __device__ __forceinline__ int wide_dc(bool ga, int r, int gbase, int wp, int wt
   }
   u128 Pr = ~static_cast<u128>(0), PrS = Pr, leftmost = Pr, initv = Pr;
   const int n_store = max(0, min(C, ncols - c0));
-  const bool store_end = r == G - 1 && ncols > kWW;
+  const bool store_end = r == G - 1 && ncols > WW;
   const int t_last = kmax + G - 1;
   bool going = ga && wt > 0;  // group-uniform
   int first = -1;             // lane 0: first solved row
@@ -169,7 +173,7 @@ __device__ __forceinline__ int wide_dc(bool ga, int r, int gbase, int wp, int wt
 #pragma unroll
         for (int x = 0; x < C; ++x)
           if (x < n_store) stg128(row + c0 + x, P[x]);
-        if (store_end) stg128(row + kWW, right);
+        if (store_end) stg128(row + WW, right);
       }
     }
     if (first < 0 && d >= 0 && d <= kmax && !bit128(P[0], wp - 1)) first = d;
@@ -188,7 +192,7 @@ __device__ __forceinline__ int wide_dc(bool ga, int r, int gbase, int wp, int wt
 // before the iteration that would need it and sets `over`. In a window that
 // is not the last the walk never reaches j = 0 (it stops W-O bases in).
 // Groups with run false only take part in the votes.
-template <int G, bool kBand>
+template <int G, bool kBand, int WW>
 __device__ __forceinline__ bool wide_tb(bool run, int r, int gbase, int wp, int wt, int dmin,
                                         bool last, int commit, int ncols, int S, int band_top,
                                         uint64_t order_table, const u128* pmcol, const void* tabv,
@@ -215,7 +219,7 @@ __device__ __forceinline__ bool wide_tb(bool run, int r, int gbase, int wp, int 
     const int jl = wp - 1 - cp - r;
     const int ic = min(il, cmax);
     const int rowm = max(rowd - S, 0);
-    const u128 pm = pmcol[min(il, kWW - 1)];
+    const u128 pm = pmcol[min(il, WW - 1)];
     const int jc = jl > 0 ? jl : 0;
     // On the walk's active cells matching bases always allow M (see tb_window).
     const bool m_ok = !bit128(pm, jc);
@@ -273,7 +277,7 @@ struct WideArgs {
 // One window of every busy group of the warp. The groups of a warp stay
 // converged: each pass runs when some group needs it, with per-group
 // predicates.
-template <int G>
+template <int G, int WW>
 __device__ __forceinline__ void wide_window(const AlignParams& p, const WideArgs& a, int r,
                                             int gbase, PairState& st, u128* pmcol,
                                             uint64_t* band, u128* tab) {
@@ -288,15 +292,15 @@ __device__ __forceinline__ void wide_window(const AlignParams& p, const WideArgs
     last = st.pos_p + static_cast<uint32_t>(wp) == st.m;
     ncols = last ? wt + 1 : min(wt, commit) + 1;
   }
-  wide_masks<G>(ga, r, gbase, st.read, st.pos_p, wp, st.ref, st.pos_t, wt, pmcol);
+  wide_masks<G, WW>(ga, r, gbase, st.read, st.pos_p, wp, st.ref, st.pos_t, wt, pmcol);
   __syncwarp();
   int dmin = -1, cp = 0, ct = 0;
   bool ok = true, over = false;
   // Windows that are not the last: band entries.
   const bool use_band = ga && !last && a.band_top >= 0;
   if (__any_sync(kFull, use_band)) {
-    const int d1 = wide_dc<G, true>(use_band, r, gbase, wp, wt, p.kmax, ncols, a.band_stride,
-                                    kWRows, a.band_top, pmcol, band);
+    const int d1 = wide_dc<G, true, WW>(use_band, r, gbase, wp, wt, p.kmax, ncols, a.band_stride,
+                                        WW + 1, a.band_top, pmcol, band);
     if (use_band) dmin = d1;
   }
   __syncwarp();
@@ -305,7 +309,7 @@ __device__ __forceinline__ void wide_window(const AlignParams& p, const WideArgs
   const uint32_t edits0 = st.edits;
   if (__any_sync(kFull, band_trace)) {
     int c1 = 0, t1 = 0;
-    const bool ok1 = wide_tb<G, true>(band_trace, r, gbase, wp, wt, dmin, last, commit, ncols,
+    const bool ok1 = wide_tb<G, true, WW>(band_trace, r, gbase, wp, wt, dmin, last, commit, ncols,
                                       a.band_stride, a.band_top, p.tb_table, pmcol, band, st.rw,
                                       writer, c1, t1, st.edits, over);
     if (band_trace) {
@@ -324,14 +328,14 @@ __device__ __forceinline__ void wide_window(const AlignParams& p, const WideArgs
   // Last windows, windows without band tables and redone windows: full entries.
   const bool full = ga && (!use_band || over);
   if (__any_sync(kFull, full)) {
-    const int d2 = wide_dc<G, false>(full, r, gbase, wp, wt, p.kmax, ncols, kWStride, kWRows, 0,
+    const int d2 = wide_dc<G, false, WW>(full, r, gbase, wp, wt, p.kmax, ncols, WW + 2, WW + 1, 0,
                                      pmcol, tab);
     if (full) dmin = d2;
     __syncwarp();
     int c2 = 0, t2 = 0;
     bool unused = false;
-    const bool ok2 = wide_tb<G, false>(full && dmin >= 0, r, gbase, wp, wt, dmin, last, commit,
-                                       ncols, kWStride, 0, p.tb_table, pmcol, tab, st.rw, writer,
+    const bool ok2 = wide_tb<G, false, WW>(full && dmin >= 0, r, gbase, wp, wt, dmin, last, commit,
+                                           ncols, WW + 2, 0, p.tb_table, pmcol, tab, st.rw, writer,
                                        c2, t2, st.edits, unused);
     if (full) {
       ok = ok2;
@@ -360,11 +364,11 @@ __device__ __forceinline__ void wide_window(const AlignParams& p, const WideArgs
 // Compiled for two blocks per SM (205 registers: the lowest latency per pair)
 // and for three (168 registers, no spills: 24 resident pairs per SM, the
 // higher throughput once there are more pairs than the two-block grid holds).
-template <int G, int kBlocksPerSm>
+template <int G, int kBlocksPerSm, int WW>
 __global__ void __launch_bounds__(kWThreads, kBlocksPerSm) align_wide_kernel(const AlignParams p,
                                                                              const WideArgs a) {
   constexpr int kGroups = kWThreads / G;
-  __shared__ u128 pmcols[kGroups][kWW];
+  __shared__ u128 pmcols[kGroups][WW];
   const int lane = threadIdx.x & 31;
   const int group = threadIdx.x / G;
   const int r = lane % G;
@@ -385,7 +389,7 @@ __global__ void __launch_bounds__(kWThreads, kBlocksPerSm) align_wide_kernel(con
       else drained = true;
     }
     if (!__any_sync(kFull, st.busy || !drained)) break;
-    if (__any_sync(kFull, st.busy)) wide_window<G>(p, a, r, gbase, st, pmcols[group], band, tab);
+    if (__any_sync(kFull, st.busy)) wide_window<G, WW>(p, a, r, gbase, st, pmcols[group], band, tab);
   }
 }
 
@@ -393,22 +397,33 @@ struct WideLayout {
   size_t queue, hist, order, tables, total;
 };
 
-template <int kBlocksPerSm>
+template <int kBlocksPerSm, int WW>
 cudaError_t wide_blocks(int* blocks) {
   int dev = 0, sms = 0, per_sm = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e == cudaSuccess)
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &per_sm, align_wide_kernel<kWG, kBlocksPerSm>, kWThreads, 0);
+        &per_sm, align_wide_kernel<kWG, kBlocksPerSm, WW>, kWThreads, 0);
   *blocks = per_sm * sms;
   return e;
 }
 
-// Both grids; the workspace holds the tables of the larger.
-cudaError_t wide_grids(int* blocks2, int* blocks3) {
-  cudaError_t e = wide_blocks<2>(blocks2);
-  if (e == cudaSuccess) e = wide_blocks<3>(blocks3);
+// Both grids of the build for windows of W bases (W = 0: the largest grids
+// of either build, which the workspace is sized for).
+cudaError_t wide_grids(int W, int* blocks2, int* blocks3) {
+  int a2 = 0, a3 = 0, c2 = 0, c3 = 0;
+  cudaError_t e = cudaSuccess;
+  if (W == 0 || ww_for(W) == kWW96) {
+    e = wide_blocks<2, kWW96>(&a2);
+    if (e == cudaSuccess) e = wide_blocks<3, kWW96>(&a3);
+  }
+  if (e == cudaSuccess && (W == 0 || ww_for(W) == kWW)) {
+    e = wide_blocks<2, kWW>(&c2);
+    if (e == cudaSuccess) e = wide_blocks<3, kWW>(&c3);
+  }
+  *blocks2 = std::max(a2, c2);
+  *blocks3 = std::max(a3, c3);
   return e;
 }
 
@@ -428,7 +443,7 @@ WideLayout wide_layout(uint32_t n_pairs, int blocks) {
 
 cudaError_t wide_workspace_bytes(uint32_t n_pairs, size_t* bytes) {
   int b2 = 0, b3 = 0;
-  const cudaError_t e = wide_grids(&b2, &b3);
+  const cudaError_t e = wide_grids(0, &b2, &b3);
   if (e != cudaSuccess) return e;
   *bytes = wide_layout(n_pairs, std::max(b2, b3)).total;
   return cudaSuccess;
@@ -438,7 +453,7 @@ cudaError_t launch_wide(const AlignParams& p, bool lpt, void* ws, size_t ws_byte
                         cudaStream_t s) {
   if (p.n_pairs == 0) return cudaSuccess;
   int b2 = 0, b3 = 0;
-  cudaError_t e = wide_grids(&b2, &b3);
+  cudaError_t e = wide_grids(p.W, &b2, &b3);
   if (e != cudaSuccess) return e;
   const WideLayout L = wide_layout(p.n_pairs, std::max(b2, b3));
   if (ws_bytes < L.total || b2 < 1 || b3 < 1) return cudaErrorInvalidValue;
@@ -453,8 +468,13 @@ cudaError_t launch_wide(const AlignParams& p, bool lpt, void* ws, size_t ws_byte
   const WideArgs a{reinterpret_cast<uint32_t*>(w + L.queue), lpt ? order : nullptr,
                    reinterpret_cast<u128*>(w + L.tables), wide_band_top(p.O),
                    wide_band_stride(p.W, p.O)};
-  if (small) align_wide_kernel<kWG, 2><<<b2, kWThreads, 0, s>>>(p, a);
-  else align_wide_kernel<kWG, 3><<<b3, kWThreads, 0, s>>>(p, a);
+  if (ww_for(p.W) == kWW96) {
+    if (small) align_wide_kernel<kWG, 2, kWW96><<<b2, kWThreads, 0, s>>>(p, a);
+    else align_wide_kernel<kWG, 3, kWW96><<<b3, kWThreads, 0, s>>>(p, a);
+  } else {
+    if (small) align_wide_kernel<kWG, 2, kWW><<<b2, kWThreads, 0, s>>>(p, a);
+    else align_wide_kernel<kWG, 3, kWW><<<b3, kWThreads, 0, s>>>(p, a);
+  }
   count_launches(1);
   return cudaGetLastError();
 }

@@ -87,16 +87,18 @@ def test_full_workload(config):
     ga.ga_tuning_set(64, 24, 64, None)
 
 
-def test_full_workload_wide_windows():
-    # Workload 2 at W = 128 (the 128-bit kernel: band tables for windows that are not the
-    # last, full entries for last windows and band overflows), every pair against the oracle.
+@pytest.mark.parametrize("W,O", [(128, 48), (96, 36)])
+def test_full_workload_wide_windows(W, O):
+    # Workload 2 at W = 128 and 96 (the 128-bit kernel's 128- and 96-column builds: band
+    # tables for windows that are not the last, full entries for last windows and band
+    # overflows), every pair against the oracle.
     batch = datagen.make_batch(2, workers=WORKERS)
-    db = DeviceBatch(batch, W=128, O=48, k=128)
+    db = DeviceBatch(batch, W=W, O=O, k=W)
     db.dist.fill_(-9)
     db.run("batched", stats=True)
     torch.cuda.synchronize()
     check_all_pairs(db)
-    compare_batch(batch, db, torch, ga, W=128, O=48, k=128, label="workload 2, W = 128")
+    compare_batch(batch, db, torch, ga, W=W, O=O, k=W, label=f"workload 2, W = {W}")
 
 
 @pytest.mark.parametrize("config", [2, 4])
