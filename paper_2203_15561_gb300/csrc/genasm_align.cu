@@ -243,7 +243,11 @@ cudaError_t launch_plain(const AlignParams& p, cudaStream_t s) {
 // pair and publishes it. The wait for a free slot is bounded: should it run
 // out, the group keeps its pair for another turn and flags the launch, and the
 // reserver of the lost position stops with the others at the end. Every pair
-// not yet finished is held by a running group or published in the ring.
+// not yet finished is held by a running group or published in the ring. A
+// warp whose groups all wait for a pair also waits a bounded time only
+// (behind a lost position published pairs could otherwise be left without a
+// reserver); the pairs a run-out wait leaves unfinished keep the timed-out
+// status that the ring's set-up kernel gives every pair.
 // ---------------------------------------------------------------------------
 
 struct BatchArgs {
