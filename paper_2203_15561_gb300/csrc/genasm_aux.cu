@@ -9,6 +9,7 @@
 
 #include <cuda_runtime.h>
 
+#include "genasm_admit.h"
 #include "genasm_internal.h"
 
 namespace ga {
@@ -95,6 +96,65 @@ __global__ void pack_bytes_kernel(const uint8_t* __restrict__ ascii, uint64_t n,
     out[q] = static_cast<uint8_t>(byte);
   }
   if (n_invalid && bad) atomicAdd(n_invalid, bad);
+}
+
+// Many sequences at once: segment q packs segs[q].bytes ASCII bytes (a
+// multiple of 4, starting 4-aligned) from ascii + segs[q].src into
+// out + segs[q].dst, one output byte per four bases. Block row y handles
+// segments y, y + gridDim.y, ...
+__global__ void pack_segments_kernel(const uint8_t* __restrict__ ascii,
+                                     const PackSegment* __restrict__ segs, uint32_t n_segs,
+                                     uint8_t* __restrict__ out) {
+  for (uint32_t q = blockIdx.y; q < n_segs; q += gridDim.y) {
+    const PackSegment g = segs[q];
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(ascii + g.src);
+    uint8_t* dst = out + g.dst;
+    const uint64_t words = g.bytes / 4;
+    uint32_t bad = 0;
+    for (uint64_t w = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; w < words;
+         w += static_cast<uint64_t>(gridDim.x) * blockDim.x)
+      dst[w] = static_cast<uint8_t>(pack4(__ldcs(src + w), bad));
+  }
+}
+
+cudaError_t launch_pack_segments(const uint8_t* ascii, const PackSegment* segs, uint32_t n_segs,
+                                 uint64_t max_bytes, uint8_t* out, cudaStream_t s) {
+  if (n_segs == 0) return cudaSuccess;
+  const uint64_t words = max_bytes / 4;
+  const uint32_t bx = static_cast<uint32_t>(std::min<uint64_t>((words + 255) / 256, 64));
+  const uint32_t by = std::min<uint32_t>(n_segs, 4096);
+  pack_segments_kernel<<<dim3(bx > 0 ? bx : 1, by), 256, 0, s>>>(ascii, segs, n_segs, out);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+__global__ void scatter_slots_kernel(const SlotRecord* __restrict__ recs, uint32_t n,
+                                     uint64_t* __restrict__ read_off, uint64_t* __restrict__ ref_off,
+                                     uint64_t* __restrict__ cigar_off, uint32_t* __restrict__ read_len,
+                                     uint32_t* __restrict__ ref_len, uint32_t* __restrict__ cigar_cap,
+                                     SlotState* __restrict__ state) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const SlotRecord r = recs[i];
+    read_off[r.slot] = r.read_off;
+    ref_off[r.slot] = r.ref_off;
+    cigar_off[r.slot] = r.cigar_off;
+    read_len[r.slot] = r.read_len;
+    ref_len[r.slot] = r.ref_len;
+    cigar_cap[r.slot] = r.cigar_cap;
+    state[r.slot] = SlotState{};
+  }
+}
+
+cudaError_t launch_scatter_slots(const SlotRecord* recs, uint32_t n, uint64_t* read_off,
+                                 uint64_t* ref_off, uint64_t* cigar_off, uint32_t* read_len,
+                                 uint32_t* ref_len, uint32_t* cigar_cap, SlotState* state,
+                                 cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  const uint32_t blocks = std::min<uint32_t>((n + 255) / 256, 1024);
+  scatter_slots_kernel<<<blocks, 256, 0, s>>>(recs, n, read_off, ref_off, cigar_off, read_len,
+                                              ref_len, cigar_cap, state);
+  count_launches(1);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_pack(const uint8_t* ascii, uint64_t n, uint8_t* packed, uint32_t* n_invalid,

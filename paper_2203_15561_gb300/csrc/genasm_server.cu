@@ -38,54 +38,71 @@
 #include <cuda_runtime.h>
 
 #include "genasm.h"
+#include "genasm_admit.h"
 #include "genasm_internal.h"
 #include "genasm_window.cuh"
 
 namespace {
 
-// First-fit allocator of [0, capacity) in units, with coalescing on release.
+// Best-fit allocator of [0, capacity) in units, with coalescing on release:
+// free ranges indexed by offset (for coalescing) and by size (for the fit),
+// so both calls take O(log ranges) however fragmented the arena is.
 class RangeAlloc {
  public:
   explicit RangeAlloc(uint64_t cap = 0) : cap_(cap) {
-    if (cap) free_[0] = cap;
+    if (cap) insert(0, cap);
   }
   bool alloc(uint64_t n, uint64_t* off) {
     if (n == 0) {
       *off = 0;
       return true;
     }
-    for (auto it = free_.begin(); it != free_.end(); ++it) {
-      if (it->second >= n) {
-        const uint64_t o = it->first, rest = it->second - n;
-        free_.erase(it);
-        if (rest) free_[o + n] = rest;
-        *off = o;
-        return true;
-      }
-    }
-    return false;
+    auto it = by_size_.lower_bound(n);
+    if (it == by_size_.end()) return false;
+    const uint64_t size = it->first, o = it->second;
+    by_size_.erase(it);
+    by_off_.erase(o);
+    if (size > n) insert(o + n, size - n);
+    *off = o;
+    return true;
   }
   void release(uint64_t off, uint64_t n) {
     if (n == 0) return;
-    auto next = free_.lower_bound(off);
-    if (next != free_.end() && off + n == next->first) {
+    auto next = by_off_.lower_bound(off);
+    if (next != by_off_.end() && off + n == next->first) {
       n += next->second;
-      next = free_.erase(next);
+      erase_size(next->second, next->first);
+      next = by_off_.erase(next);
     }
-    if (next != free_.begin()) {
+    if (next != by_off_.begin()) {
       auto prev = std::prev(next);
       if (prev->first + prev->second == off) {
-        prev->second += n;
-        return;
+        erase_size(prev->second, prev->first);
+        off = prev->first;
+        n += prev->second;
+        by_off_.erase(prev);
       }
     }
-    free_[off] = n;
+    insert(off, n);
   }
   uint64_t capacity() const { return cap_; }
 
  private:
+  void insert(uint64_t off, uint64_t n) {
+    by_off_[off] = n;
+    by_size_.emplace(n, off);
+  }
+  void erase_size(uint64_t n, uint64_t off) {
+    auto range = by_size_.equal_range(n);
+    for (auto it = range.first; it != range.second; ++it)
+      if (it->second == off) {
+        by_size_.erase(it);
+        return;
+      }
+  }
   uint64_t cap_;
-  std::map<uint64_t, uint64_t> free_;
+  std::map<uint64_t, uint64_t> by_off_;        // offset -> size
+  std::multimap<uint64_t, uint64_t> by_size_;  // size -> offset
 };
 
 struct Request {
@@ -105,7 +122,9 @@ struct Result {
   ga_result pub{};
   std::vector<int32_t> dist, status, ref_consumed;
   std::vector<uint64_t> cigar_off;
-  std::vector<uint32_t> cigar;
+  std::vector<uint32_t> cigar;   // runs, unless they sit in the pinned result arena
+  uint64_t arena_off = 0, arena_runs = 0;
+  bool in_arena = false;
 };
 
 __global__ void gather_list_kernel(const uint32_t* __restrict__ src, const uint64_t* __restrict__ list,
@@ -116,7 +135,30 @@ __global__ void gather_list_kernel(const uint32_t* __restrict__ src, const uint6
   for (uint64_t p = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; p < n;
        p += warps) {
     const uint64_t s = list[3 * p], d = list[3 * p + 1], c = list[3 * p + 2];
-    for (uint64_t x = lane; x < c; x += 32) dst[d + x] = src[s + x];
+    uint64_t x = lane;
+    for (; x + 96 < c; x += 128) {  // four loads in flight per lane
+      const uint32_t v0 = src[s + x], v1 = src[s + x + 32], v2 = src[s + x + 64], v3 = src[s + x + 96];
+      dst[d + x] = v0;
+      dst[d + x + 32] = v1;
+      dst[d + x + 64] = v2;
+      dst[d + x + 96] = v3;
+    }
+    for (; x < c; x += 32) dst[d + x] = src[s + x];
+  }
+}
+
+// The per-pair outputs of the listed slots, packed: out = [dist n][status n]
+// [ref_consumed n][n_runs n].
+__global__ void gather_slots_kernel(const uint32_t* __restrict__ slots, uint32_t n,
+                                    const int32_t* __restrict__ dist, const int32_t* __restrict__ status,
+                                    const int32_t* __restrict__ ref_consumed,
+                                    const uint32_t* __restrict__ n_runs, int32_t* __restrict__ out) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const uint32_t q = slots[i];
+    out[i] = dist[q];
+    out[n + i] = status[q];
+    out[2ull * n + i] = ref_consumed[q];
+    out[3ull * n + i] = static_cast<int32_t>(n_runs[q]);
   }
 }
 
@@ -166,12 +208,24 @@ struct ga_server {
   uint32_t* h_ctl = nullptr;        // pinned: active count, windows per step
   // pinned host staging
   uint8_t* h_ascii = nullptr;
-  uint64_t* h_meta64 = nullptr;  // 3 arrays of max_slots uint64 (read_off, ref_off, cigar_off)
-  uint32_t* h_meta32 = nullptr;  // 3 arrays of max_slots uint32 (read_len, ref_len, cigar_cap)
+  // one admission's packing segments and slot records (pinned, then device)
+  ga::PackSegment* h_segs = nullptr;
+  ga::SlotRecord* h_recs = nullptr;
+  ga::PackSegment* d_segs = nullptr;
+  ga::SlotRecord* d_recs = nullptr;
   uint32_t *h_active = nullptr, *h_done = nullptr, *h_counters = nullptr;
   uint64_t* h_list = nullptr;
   uint32_t* h_out = nullptr;
-  int32_t* h_small = nullptr;    // 4 arrays of max_slots (dist, status, ref_consumed, n_runs)
+  int32_t* h_small = nullptr;    // a harvest chunk's dist, status, ref_consumed, n_runs
+  uint32_t* h_hslots = nullptr;  // a harvest chunk's slots
+  uint32_t* d_hslots = nullptr;
+  int32_t* d_hsmall = nullptr;
+  int sms = 0;
+  // pinned result arena: the CIGAR runs of results not yet released, copied
+  // there straight from the device (no host copy); a result that finds no
+  // room takes the copy through h_out into its own heap array instead
+  uint32_t* h_res = nullptr;
+  RangeAlloc res_alloc;
   // bookkeeping
   RangeAlloc seq_alloc, cig_alloc, slot_alloc;
   std::deque<Request*> pending;
@@ -216,14 +270,20 @@ void server_free(ga_server* s) {
   cudaFree(s->d_list);
   cudaFree(s->d_out);
   cudaFreeHost(s->h_ascii);
-  cudaFreeHost(s->h_meta64);
-  cudaFreeHost(s->h_meta32);
+  cudaFreeHost(s->h_segs);
+  cudaFreeHost(s->h_recs);
+  cudaFree(s->d_segs);
+  cudaFree(s->d_recs);
   cudaFreeHost(s->h_active);
   cudaFreeHost(s->h_done);
   cudaFreeHost(s->h_counters);
   cudaFreeHost(s->h_list);
   cudaFreeHost(s->h_out);
   cudaFreeHost(s->h_small);
+  cudaFreeHost(s->h_hslots);
+  cudaFree(s->d_hslots);
+  cudaFree(s->d_hsmall);
+  cudaFreeHost(s->h_res);
   cudaFreeHost(s->h_count_map);
   cudaFreeHost(s->h_done_map);
   cudaFreeHost(s->h_ctl);
@@ -251,6 +311,12 @@ constexpr uint64_t kAsciiStagingMin = 16ull << 20;
 constexpr uint64_t kAsciiStagingMax = 256ull << 20;
 constexpr uint64_t kOutRuns = 16ull << 20;        // runs gathered per step (at most, 64 MB)
 constexpr uint64_t kListPairs = 1ull << 16;       // pairs harvested per step (at most)
+constexpr uint32_t kAdmitRequests = 1u << 16;     // requests admitted per admission (at most)
+constexpr uint32_t kAdmitPairs = 1u << 17;        // pairs admitted per admission (at most)
+// Pinned host memory for results' CIGAR runs until they are released: a
+// sixteenth of the budget, between 256 MB and 2 GB.
+constexpr uint64_t kResArenaMin = 256ull << 20;
+constexpr uint64_t kResArenaMax = 2ull << 30;
 
 // The alignment parameters of the step kernel over the server's slots.
 ga::AlignParams step_params(const ga_server* s) {
@@ -340,7 +406,9 @@ extern "C" int ga_server_create(size_t budget_bytes, int W, int O, int k, ga_ser
   const uint64_t per_slot = 8 * 4 + 4 * 6 + 4 * 2 + sizeof(ga::SlotState);
   const uint64_t staging =
       std::min(kAsciiStagingMax, std::max(kAsciiStagingMin, static_cast<uint64_t>(budget_bytes) / 8));
-  const uint64_t fixed = spill_bytes + staging + kOutRuns * 4 + kListPairs * 24 +
+  const uint64_t fixed = spill_bytes + staging + kOutRuns * 4 + kListPairs * (24 + 4 + 16) +
+                         kAdmitRequests * sizeof(ga::PackSegment) +
+                         kAdmitPairs * sizeof(ga::SlotRecord) +
                          static_cast<uint64_t>(s->max_slots) * per_slot;
   if (e == cudaSuccess && budget_bytes < fixed + (64ull << 20)) {
     server_free(s);
@@ -374,14 +442,23 @@ extern "C" int ga_server_create(size_t budget_bytes, int W, int O, int k, ga_ser
   if (e == cudaSuccess) e = dev_alloc(s, &s->d_list, 3 * kListPairs);
   if (e == cudaSuccess) e = dev_alloc(s, &s->d_out, kOutRuns);
   if (e == cudaSuccess) e = cudaMallocHost(&s->h_ascii, staging);
-  if (e == cudaSuccess) e = cudaMallocHost(&s->h_meta64, 8ull * 3 * M);
-  if (e == cudaSuccess) e = cudaMallocHost(&s->h_meta32, 4ull * 3 * M);
+  if (e == cudaSuccess) e = cudaMallocHost(&s->h_segs, sizeof(ga::PackSegment) * kAdmitRequests);
+  if (e == cudaSuccess) e = cudaMallocHost(&s->h_recs, sizeof(ga::SlotRecord) * kAdmitPairs);
+  if (e == cudaSuccess) e = dev_alloc(s, &s->d_segs, kAdmitRequests);
+  if (e == cudaSuccess) e = dev_alloc(s, &s->d_recs, kAdmitPairs);
   if (e == cudaSuccess) e = cudaMallocHost(&s->h_active, 4ull * M);
   if (e == cudaSuccess) e = cudaMallocHost(&s->h_done, 4ull * M);
   if (e == cudaSuccess) e = cudaMallocHost(&s->h_counters, 4ull * 64);
   if (e == cudaSuccess) e = cudaMallocHost(&s->h_list, 24ull * kListPairs);
   if (e == cudaSuccess) e = cudaMallocHost(&s->h_out, 4ull * kOutRuns);
-  if (e == cudaSuccess) e = cudaMallocHost(&s->h_small, 16ull * M);
+  if (e == cudaSuccess) e = cudaMallocHost(&s->h_small, 16ull * kListPairs);
+  if (e == cudaSuccess) e = cudaMallocHost(&s->h_hslots, 4ull * kListPairs);
+  if (e == cudaSuccess) e = dev_alloc(s, &s->d_hslots, kListPairs);
+  if (e == cudaSuccess) e = dev_alloc(s, &s->d_hsmall, 4 * kListPairs);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, s->device);
+  const uint64_t res_bytes =
+      std::min(kResArenaMax, std::max(kResArenaMin, static_cast<uint64_t>(budget_bytes) / 16));
+  if (e == cudaSuccess) e = cudaMallocHost(&s->h_res, res_bytes);
   if (e == cudaSuccess) e = cudaHostAlloc(&s->h_count_map, 64, cudaHostAllocMapped);
   if (e == cudaSuccess) e = cudaHostAlloc(&s->h_done_map, 4ull * M, cudaHostAllocMapped);
   if (e == cudaSuccess) e = cudaMallocHost(&s->h_ctl, 64);
@@ -399,6 +476,7 @@ extern "C" int ga_server_create(size_t budget_bytes, int W, int O, int k, ga_ser
   s->seq_alloc = RangeAlloc(seq_bytes);
   s->cig_alloc = RangeAlloc(cig_runs);
   s->slot_alloc = RangeAlloc(M);
+  s->res_alloc = RangeAlloc(res_bytes / 4);
   s->slot_owner.assign(M, nullptr);
   *out = s;
   return GA_OK;
@@ -452,12 +530,16 @@ namespace {
 
 // Step 1: admission of waiting requests, in arrival order, while they fit.
 // A request without pairs takes no device space and no launch: it is
-// complete at admission and goes straight to `finished`.
+// complete at admission and goes straight to `finished`. The admitted
+// requests' ASCII goes through the pinned staging buffer in one copy; one
+// launch packs all of it into the sequence arena and one writes every
+// admitted pair's slot metadata and zeroes its window state.
 int admit(ga_server* s, std::vector<Request*>& finished) {
-  uint64_t staged = 0;
-  std::vector<Request*> batch;
-  // The pinned staging buffer is reused: the previous admission's copy out of
-  // it must have completed before it is written again.
+  uint64_t staged = 0, max_seg = 0;
+  uint32_t n_segs = 0, n_recs = 0;
+  bool any = false;
+  // The pinned staging buffers are reused: the previous admission's copies
+  // out of them must have completed before they are written again.
   if (s->staged && !s->pending.empty()) {
     if (cudaEventSynchronize(s->ev_staged) != cudaSuccess) return GA_ECUDA;
     s->staged = false;
@@ -471,7 +553,8 @@ int admit(ga_server* s, std::vector<Request*>& finished) {
       continue;
     }
     const uint64_t abytes = r->ascii.size();
-    if (staged + abytes > s->ascii_cap) break;
+    if (staged + abytes > s->ascii_cap || n_segs + 1 > kAdmitRequests || n_recs + r->n > kAdmitPairs)
+      break;
     uint64_t so = 0, co = 0, sl = 0;
     if (!s->seq_alloc.alloc(abytes / 4, &so)) break;
     if (!s->cig_alloc.alloc(r->runs, &co)) {
@@ -489,136 +572,160 @@ int admit(ga_server* s, std::vector<Request*>& finished) {
     r->slot0 = sl;
     r->t_admit = now_ms(s->t0);
     std::memcpy(s->h_ascii + staged, r->ascii.data(), abytes);
-    staged += abytes;
-    batch.push_back(r);
-    s->pending.pop_front();
-  }
-  if (batch.empty()) return GA_OK;
-  cudaStream_t st = s->stream;
-  if (cudaMemcpyAsync(s->d_ascii, s->h_ascii, staged, cudaMemcpyHostToDevice, st) != cudaSuccess ||
-      cudaEventRecord(s->ev_staged, st) != cudaSuccess)
-    return GA_ECUDA;
-  s->staged = true;
-  const uint32_t M = s->max_slots;
-  uint64_t aoff = 0;
-  for (Request* r : batch) {
-    const uint64_t abytes = r->ascii.size();
-    if (ga::launch_pack(s->d_ascii + aoff, abytes, s->d_seq + r->seq_off, nullptr, st) != cudaSuccess)
-      return GA_ECUDA;
-    uint64_t* m64 = s->h_meta64;
-    uint32_t* m32 = s->h_meta32;
-    uint64_t c = r->cig_off;
+    s->h_segs[n_segs++] = ga::PackSegment{staged, so, abytes};
+    max_seg = std::max(max_seg, abytes);
+    uint64_t c = co;
     for (uint32_t p = 0; p < r->n; ++p) {
-      const uint64_t slot = r->slot0 + p;
-      m64[slot] = r->seq_off + r->read_at[p] / 4;
-      m64[M + slot] = r->seq_off + r->ref_at[p] / 4;
-      m64[2ull * M + slot] = c;
-      m32[slot] = r->read_len[p];
-      m32[M + slot] = r->ref_len[p];
-      m32[2ull * M + slot] = r->read_len[p] + r->ref_len[p] + 1;
+      const uint64_t slot = sl + p;
+      ga::SlotRecord& rec = s->h_recs[n_recs++];
+      rec.read_off = so + r->read_at[p] / 4;
+      rec.ref_off = so + r->ref_at[p] / 4;
+      rec.cigar_off = c;
+      rec.slot = static_cast<uint32_t>(slot);
+      rec.read_len = r->read_len[p];
+      rec.ref_len = r->ref_len[p];
+      rec.cigar_cap = r->read_len[p] + r->ref_len[p] + 1;
       c += r->read_len[p] + static_cast<uint64_t>(r->ref_len[p]) + 1;
       s->slot_owner[slot] = r;
       s->active.push_back(static_cast<uint32_t>(slot));
     }
-    const uint64_t a = r->slot0, n = r->n;
-    cudaMemcpyAsync(s->d_read_off + a, m64 + a, 8 * n, cudaMemcpyHostToDevice, st);
-    cudaMemcpyAsync(s->d_ref_off + a, m64 + M + a, 8 * n, cudaMemcpyHostToDevice, st);
-    cudaMemcpyAsync(s->d_cigar_off + a, m64 + 2ull * M + a, 8 * n, cudaMemcpyHostToDevice, st);
-    cudaMemcpyAsync(s->d_read_len + a, m32 + a, 4 * n, cudaMemcpyHostToDevice, st);
-    cudaMemcpyAsync(s->d_ref_len + a, m32 + M + a, 4 * n, cudaMemcpyHostToDevice, st);
-    cudaMemcpyAsync(s->d_cigar_cap + a, m32 + 2ull * M + a, 4 * n, cudaMemcpyHostToDevice, st);
-    if (cudaMemsetAsync(s->d_state + a, 0, sizeof(ga::SlotState) * n, st) != cudaSuccess)
-      return GA_ECUDA;
-    aoff += abytes;
+    staged += abytes;
+    any = true;
+    s->pending.pop_front();
   }
+  if (!any) return GA_OK;
+  cudaStream_t st = s->stream;
+  if (cudaMemcpyAsync(s->d_ascii, s->h_ascii, staged, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(s->d_segs, s->h_segs, sizeof(ga::PackSegment) * n_segs,
+                      cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(s->d_recs, s->h_recs, sizeof(ga::SlotRecord) * n_recs,
+                      cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaEventRecord(s->ev_staged, st) != cudaSuccess)
+    return GA_ECUDA;
+  s->staged = true;
+  if (ga::launch_pack_segments(s->d_ascii, s->d_segs, n_segs, max_seg, s->d_seq, st) != cudaSuccess ||
+      ga::launch_scatter_slots(s->d_recs, n_recs, s->d_read_off, s->d_ref_off, s->d_cigar_off,
+                               s->d_read_len, s->d_ref_len, s->d_cigar_cap, s->d_state,
+                               st) != cudaSuccess)
+    return GA_ECUDA;
   return GA_OK;
 }
 
-// Step 3: results of requests whose pairs are all done.
+// Step 3: results of requests whose pairs are all done, in chunks of at most
+// kListPairs pairs: one launch gathers their distances, statuses, reference
+// ends and run counts from the slot arrays (one copy back), then one launch
+// per run-buffer load gathers their CIGAR runs, copied back straight into the
+// pinned result arena when it has room.
 int harvest(ga_server* s, const std::vector<Request*>& finished) {
-  if (finished.empty()) return GA_OK;
   cudaStream_t st = s->stream;
-  const uint32_t M = s->max_slots;
-  int32_t* hs = s->h_small;
-  for (Request* r : finished) {
-    const uint64_t a = r->slot0, n = r->n;
-    cudaMemcpyAsync(hs + a, s->d_dist + a, 4 * n, cudaMemcpyDeviceToHost, st);
-    cudaMemcpyAsync(hs + M + a, s->d_status + a, 4 * n, cudaMemcpyDeviceToHost, st);
-    cudaMemcpyAsync(hs + 2ull * M + a, s->d_ref_consumed + a, 4 * n, cudaMemcpyDeviceToHost, st);
-    cudaMemcpyAsync(hs + 3ull * M + a, s->d_n_runs + a, 4 * n, cudaMemcpyDeviceToHost, st);
-  }
-  if (cudaStreamSynchronize(st) != cudaSuccess) return GA_ECUDA;
-  // One gather of every finished pair's runs, then one copy to the host.
-  uint64_t pairs = 0, total = 0;
-  size_t first = 0;
-  while (first < finished.size()) {
-    size_t last = first;
-    pairs = 0;
-    total = 0;
-    for (; last < finished.size(); ++last) {
-      Request* r = finished[last];
-      uint64_t runs = 0;
-      for (uint32_t p = 0; p < r->n; ++p) runs += static_cast<uint32_t>(hs[3ull * M + r->slot0 + p]);
-      if (last > first && (pairs + r->n > kListPairs || total + runs > s->out_cap)) break;
-      uint64_t c = r->cig_off;
-      for (uint32_t p = 0; p < r->n; ++p) {
-        const uint32_t cnt = static_cast<uint32_t>(hs[3ull * M + r->slot0 + p]);
-        s->h_list[3 * pairs] = c;
-        s->h_list[3 * pairs + 1] = total;
-        s->h_list[3 * pairs + 2] = cnt;
-        c += r->read_len[p] + static_cast<uint64_t>(r->ref_len[p]) + 1;
-        total += cnt;
-        ++pairs;
-      }
+  size_t i0 = 0;
+  while (i0 < finished.size()) {
+    size_t i1 = i0;
+    uint32_t np = 0;
+    while (i1 < finished.size() && (i1 == i0 || np + finished[i1]->n <= kListPairs)) {
+      np += finished[i1]->n;
+      ++i1;
     }
-    if (pairs > 0) {
-      if (cudaMemcpyAsync(s->d_list, s->h_list, 24 * pairs, cudaMemcpyHostToDevice, st) != cudaSuccess)
+    uint32_t k = 0;
+    for (size_t q = i0; q < i1; ++q)
+      for (uint32_t p = 0; p < finished[q]->n; ++p)
+        s->h_hslots[k++] = static_cast<uint32_t>(finished[q]->slot0 + p);
+    int32_t* hs = s->h_small;  // [dist np][status np][ref_consumed np][n_runs np]
+    if (np > 0) {
+      if (cudaMemcpyAsync(s->d_hslots, s->h_hslots, 4ull * np, cudaMemcpyHostToDevice, st) !=
+          cudaSuccess)
         return GA_ECUDA;
-      int sms = 0;
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
-      const uint64_t want = (pairs * 32 + 255) / 256;
-      const int blocks = static_cast<int>(std::max<uint64_t>(1, std::min<uint64_t>(want, 8ull * sms)));
-      gather_list_kernel<<<blocks, 256, 0, st>>>(s->d_cigar, s->d_list, static_cast<uint32_t>(pairs),
-                                                 s->d_out);
+      const uint32_t blocks = std::min<uint32_t>((np + 255) / 256, 1024);
+      gather_slots_kernel<<<blocks, 256, 0, st>>>(s->d_hslots, np, s->d_dist, s->d_status,
+                                                   s->d_ref_consumed, s->d_n_runs, s->d_hsmall);
       ga::count_launches(1);
-      if (total > 0 &&
-          cudaMemcpyAsync(s->h_out, s->d_out, 4 * total, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+      if (cudaMemcpyAsync(hs, s->d_hsmall, 16ull * np, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+          cudaStreamSynchronize(st) != cudaSuccess)
         return GA_ECUDA;
-      if (cudaStreamSynchronize(st) != cudaSuccess) return GA_ECUDA;
     }
-    uint64_t pos = 0;
-    for (size_t q = first; q < last; ++q) {
-      Request* r = finished[q];
-      Result* res = new Result();
-      const uint64_t a = r->slot0, n = r->n;
-      res->dist.assign(hs + a, hs + a + n);
-      res->status.assign(hs + M + a, hs + M + a + n);
-      res->ref_consumed.assign(hs + 2ull * M + a, hs + 2ull * M + a + n);
-      res->cigar_off.resize(n + 1);
-      res->cigar_off[0] = 0;
-      for (uint64_t p = 0; p < n; ++p)
-        res->cigar_off[p + 1] = res->cigar_off[p] + static_cast<uint32_t>(hs[3ull * M + a + p]);
-      res->cigar.assign(s->h_out + pos, s->h_out + pos + res->cigar_off[n]);
-      pos += res->cigar_off[n];
-      res->pub.ticket = r->ticket;
-      res->pub.tag = r->tag;
-      res->pub.n_pairs = r->n;
-      res->pub.dist = res->dist.data();
-      res->pub.status = res->status.data();
-      res->pub.ref_consumed = res->ref_consumed.data();
-      res->pub.cigar_off = res->cigar_off.data();
-      res->pub.cigar = res->cigar.data();
-      res->pub.submit_ms = r->t_submit;
-      res->pub.admit_ms = r->t_admit;
-      res->pub.done_ms = now_ms(s->t0);
-      s->ready.push_back(res);
-      s->seq_alloc.release(r->seq_off, r->seq_words);
-      s->cig_alloc.release(r->cig_off, r->runs);
-      s->slot_alloc.release(r->slot0, r->n);
-      for (uint64_t p = 0; p < n; ++p) s->slot_owner[a + p] = nullptr;
-      delete r;
+    // CIGAR runs: sub-chunks that fit the run buffer.
+    size_t j0 = i0;
+    uint32_t base = 0;  // index of request j0's first pair in hs
+    while (j0 < i1) {
+      size_t j1 = j0;
+      uint64_t pairs = 0, total = 0;
+      for (; j1 < i1; ++j1) {
+        Request* r = finished[j1];
+        uint64_t runs = 0;
+        for (uint32_t p = 0; p < r->n; ++p) runs += static_cast<uint32_t>(hs[3ull * np + base + pairs + p]);
+        if (j1 > j0 && total + runs > s->out_cap) break;
+        uint64_t c = r->cig_off;
+        for (uint32_t p = 0; p < r->n; ++p) {
+          const uint32_t cnt = static_cast<uint32_t>(hs[3ull * np + base + pairs]);
+          s->h_list[3 * pairs] = c;
+          s->h_list[3 * pairs + 1] = total;
+          s->h_list[3 * pairs + 2] = cnt;
+          c += r->read_len[p] + static_cast<uint64_t>(r->ref_len[p]) + 1;
+          total += cnt;
+          ++pairs;
+        }
+      }
+      if (pairs > 0 && total > 0) {
+        if (cudaMemcpyAsync(s->d_list, s->h_list, 24 * pairs, cudaMemcpyHostToDevice, st) !=
+            cudaSuccess)
+          return GA_ECUDA;
+        const uint64_t want = (pairs * 32 + 255) / 256;
+        const int blocks = static_cast<int>(std::max<uint64_t>(1, std::min<uint64_t>(want, 8ull * s->sms)));
+        gather_list_kernel<<<blocks, 256, 0, st>>>(s->d_cigar, s->d_list, static_cast<uint32_t>(pairs),
+                                                   s->d_out);
+        ga::count_launches(1);
+      }
+      // The runs go straight into the result arena when it has room.
+      uint64_t blk = 0;
+      const bool arena = total > 0 && s->res_alloc.alloc(total, &blk);
+      uint32_t* runs_dst = arena ? s->h_res + blk : s->h_out;
+      if (total > 0 &&
+          (cudaMemcpyAsync(runs_dst, s->d_out, 4 * total, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+           cudaStreamSynchronize(st) != cudaSuccess))
+        return GA_ECUDA;
+      uint64_t pos = 0, at = base;
+      for (size_t q = j0; q < j1; ++q) {
+        Request* r = finished[q];
+        Result* res = new Result();
+        const uint64_t n = r->n;
+        res->dist.assign(hs + at, hs + at + n);
+        res->status.assign(hs + np + at, hs + np + at + n);
+        res->ref_consumed.assign(hs + 2ull * np + at, hs + 2ull * np + at + n);
+        res->cigar_off.resize(n + 1);
+        res->cigar_off[0] = 0;
+        for (uint64_t p = 0; p < n; ++p)
+          res->cigar_off[p + 1] = res->cigar_off[p] + static_cast<uint32_t>(hs[3ull * np + at + p]);
+        if (arena) {
+          res->in_arena = true;
+          res->arena_off = blk + pos;
+          res->arena_runs = res->cigar_off[n];
+        } else {
+          res->cigar.assign(s->h_out + pos, s->h_out + pos + res->cigar_off[n]);
+        }
+        pos += res->cigar_off[n];
+        at += n;
+        res->pub.ticket = r->ticket;
+        res->pub.tag = r->tag;
+        res->pub.n_pairs = r->n;
+        res->pub.dist = res->dist.data();
+        res->pub.status = res->status.data();
+        res->pub.ref_consumed = res->ref_consumed.data();
+        res->pub.cigar_off = res->cigar_off.data();
+        res->pub.cigar = res->in_arena ? s->h_res + res->arena_off : res->cigar.data();
+        res->pub.submit_ms = r->t_submit;
+        res->pub.admit_ms = r->t_admit;
+        res->pub.done_ms = now_ms(s->t0);
+        s->ready.push_back(res);
+        s->seq_alloc.release(r->seq_off, r->seq_words);
+        s->cig_alloc.release(r->cig_off, r->runs);
+        s->slot_alloc.release(r->slot0, r->n);
+        for (uint64_t p = 0; p < n; ++p) s->slot_owner[r->slot0 + p] = nullptr;
+        delete r;
+      }
+      base = static_cast<uint32_t>(at);
+      j0 = j1;
     }
-    first = last;
+    i0 = i1;
   }
   return GA_OK;
 }
@@ -698,7 +805,9 @@ extern "C" int ga_server_release(ga_server* s, uint64_t ticket) {
   if (!s) return GA_EINVAL;
   auto it = s->handed_out.find(ticket);
   if (it == s->handed_out.end()) return GA_EINVAL;
-  delete it->second;
+  Result* r = it->second;
+  if (r->in_arena) s->res_alloc.release(r->arena_off, r->arena_runs);
+  delete r;
   s->handed_out.erase(it);
   return GA_OK;
 }
