@@ -109,6 +109,7 @@ struct Request {
   uint64_t ticket = 0, tag = 0;
   uint32_t n = 0;
   std::vector<uint8_t> ascii;  // every sequence 4-aligned: reads then references
+  uint64_t ascii_bytes = 0;    // bytes of `ascii` in use (a reused buffer may be larger)
   std::vector<uint64_t> read_at, ref_at;  // ASCII offsets inside `ascii`
   std::vector<uint32_t> read_len, ref_len;
   uint64_t runs = 0;            // CIGAR capacity: sum of read + ref + 1
@@ -229,6 +230,9 @@ struct ga_server {
   // bookkeeping
   RangeAlloc seq_alloc, cig_alloc, slot_alloc;
   std::deque<Request*> pending;
+  // ASCII buffers of admitted requests, reused by later submissions (no
+  // allocation and first-touch page faults per request)
+  std::vector<std::vector<uint8_t>> ascii_pool;
   std::vector<Request*> slot_owner;  // per slot
   std::vector<uint32_t> active;
   std::deque<Result*> ready;
@@ -497,7 +501,12 @@ extern "C" int ga_server_submit(ga_server* s, const ga_request* req, uint64_t* t
   r->tag = req->tag;
   uint64_t bytes = 0;
   for (uint32_t p = 0; p < r->n; ++p) bytes += (req->read_len[p] + 3ull) / 4 * 4 + (req->ref_len[p] + 3ull) / 4 * 4;
-  r->ascii.resize(std::max<uint64_t>(bytes, 4), 'A');
+  r->ascii_bytes = std::max<uint64_t>(bytes, 4);
+  if (!s->ascii_pool.empty()) {
+    r->ascii.swap(s->ascii_pool.back());
+    s->ascii_pool.pop_back();
+  }
+  if (r->ascii.size() < r->ascii_bytes) r->ascii.resize(r->ascii_bytes);
   r->read_at.resize(r->n);
   r->ref_at.resize(r->n);
   r->read_len.assign(req->read_len, req->read_len + r->n);
@@ -505,16 +514,18 @@ extern "C" int ga_server_submit(ga_server* s, const ga_request* req, uint64_t* t
   uint64_t at = 0;
   for (uint32_t p = 0; p < r->n; ++p) {
     r->read_at[p] = at;
-    std::memcpy(&r->ascii[at], req->reads + req->read_off[p], req->read_len[p]);
+    std::memcpy(r->ascii.data() + at, req->reads + req->read_off[p], req->read_len[p]);
+    std::memset(r->ascii.data() + at + req->read_len[p], 'A', (4 - req->read_len[p] % 4) % 4);  // padding
     at += (req->read_len[p] + 3ull) / 4 * 4;
     r->ref_at[p] = at;
-    std::memcpy(&r->ascii[at], req->refs + req->ref_off[p], req->ref_len[p]);
+    std::memcpy(r->ascii.data() + at, req->refs + req->ref_off[p], req->ref_len[p]);
+    std::memset(r->ascii.data() + at + req->ref_len[p], 'A', (4 - req->ref_len[p] % 4) % 4);
     at += (req->ref_len[p] + 3ull) / 4 * 4;
     r->runs += static_cast<uint64_t>(req->read_len[p]) + req->ref_len[p] + 1;
   }
   // A request that could never fit the server is refused now.
   if (r->n > s->slot_alloc.capacity() || r->runs > s->cig_alloc.capacity() ||
-      r->ascii.size() / 4 > s->seq_alloc.capacity() || r->ascii.size() > s->ascii_cap ||
+      r->ascii_bytes / 4 > s->seq_alloc.capacity() || r->ascii_bytes > s->ascii_cap ||
       r->runs > s->out_cap || r->n > kListPairs) {
     delete r;
     return GA_ENOMEM;
@@ -552,7 +563,7 @@ int admit(ga_server* s, std::vector<Request*>& finished) {
       s->pending.pop_front();
       continue;
     }
-    const uint64_t abytes = r->ascii.size();
+    const uint64_t abytes = r->ascii_bytes;
     if (staged + abytes > s->ascii_cap || n_segs + 1 > kAdmitRequests || n_recs + r->n > kAdmitPairs)
       break;
     uint64_t so = 0, co = 0, sl = 0;
@@ -572,6 +583,13 @@ int admit(ga_server* s, std::vector<Request*>& finished) {
     r->slot0 = sl;
     r->t_admit = now_ms(s->t0);
     std::memcpy(s->h_ascii + staged, r->ascii.data(), abytes);
+    // The buffer goes back to the pool (a few dozen, none above 64 MB).
+    if (s->ascii_pool.size() < 64 && r->ascii.size() <= (64ull << 20)) {
+      s->ascii_pool.emplace_back();
+      s->ascii_pool.back().swap(r->ascii);
+    } else {
+      std::vector<uint8_t>().swap(r->ascii);
+    }
     s->h_segs[n_segs++] = ga::PackSegment{staged, so, abytes};
     max_seg = std::max(max_seg, abytes);
     uint64_t c = co;
