@@ -318,8 +318,8 @@ constexpr uint64_t kListPairs = 1ull << 16;       // pairs harvested per step (a
 constexpr uint32_t kAdmitRequests = 1u << 16;     // requests admitted per admission (at most)
 constexpr uint32_t kAdmitPairs = 1u << 17;        // pairs admitted per admission (at most)
 // Pinned host memory for results' CIGAR runs until they are released: a
-// sixteenth of the budget, between 256 MB and 2 GB.
-constexpr uint64_t kResArenaMin = 256ull << 20;
+// sixteenth of the budget, between 16 MB and 2 GB.
+constexpr uint64_t kResArenaMin = 16ull << 20;
 constexpr uint64_t kResArenaMax = 2ull << 30;
 
 // The alignment parameters of the step kernel over the server's slots.

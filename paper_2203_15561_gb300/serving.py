@@ -55,12 +55,18 @@ class Server:
     def step(self) -> int:
         return ga_server_step(self.handle)
 
-    def poll(self, max_results: int = 256) -> list[RequestResult]:
+    def poll(self, max_results: int = 256, release: bool = True) -> list[RequestResult]:
+        """Completed requests (copied); with release=False their server-side
+        arrays stay held until release(ticket)."""
         out = []
         for r in ga_server_poll(self.handle, max_results):
             out.append(RequestResult(r))
-            ga_server_release(self.handle, int(r.ticket))
+            if release:
+                ga_server_release(self.handle, int(r.ticket))
         return out
+
+    def release(self, ticket: int) -> None:
+        ga_server_release(self.handle, ticket)
 
     def pending(self):
         return ga_server_pending(self.handle)

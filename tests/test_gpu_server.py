@@ -164,3 +164,32 @@ def test_oversize_request_refused():
         srv.submit(big)
     assert e.value.code == ga.GA_ENOMEM
     srv.close()
+
+
+def test_results_held_past_the_result_arena():
+    # Results stay valid until released. With every result held, a server whose pinned result
+    # arena (a sixteenth of the budget) is smaller than the results' runs must hand the later
+    # ones out through its heap path; all must still equal the oracle.
+    budget = 480 << 20  # a 30 MB result arena; the results' runs take about 45 MB
+    srv = Server(budget, step_windows=64)
+    batches = request_batches(80, seed=13)
+    for t, b in enumerate(batches):
+        srv.submit(b, tag=t)
+    got = {}
+    for _ in range(100000):
+        if len(got) == len(batches):
+            break
+        srv.step()
+        for r in srv.poll(release=False):
+            got[r.tag] = r
+    assert len(got) == len(batches)
+    total_runs = sum(int(r.cigar.size) for r in got.values())
+    assert 4 * total_runs > budget // 16, "the results fit the arena: the heap path was not taken"
+    for t, r in got.items():
+        check_against_oracle(batches[t], r)
+    for r in got.values():
+        srv.release(r.ticket)
+    waiting, active, _ = srv.pending()
+    srv.close()
+    assert waiting == 0 and active == 0
+
