@@ -257,7 +257,9 @@ int ga_align_batch_noalloc(const uint8_t* d_reads, const uint64_t* d_read_off,
  * the budget has room, advances every admitted pair by at most
  * `step_windows` windows (default 32) with its window state kept on the
  * device between steps, and completes every request whose pairs are all done
- * (results copied to host memory, device space freed). Requests that arrive
+ * (results copied to host memory: the CIGAR runs into a pinned arena of a
+ * sixteenth of the budget, 16 MB to 2 GB, held until the result is released,
+ * else into ordinary host memory; device space freed). Requests that arrive
  * while others are in flight join at the next step and share its launch.
  * ga_server_poll hands out completed requests, oldest first (GA_EAGAIN if
  * none); a result's arrays stay valid until ga_server_release(ticket).

@@ -11,16 +11,19 @@
 // ga_server_step
 //   1. waits for the step launched by the previous call and takes the slots
 //      that finished in it (one event wait, no copy);
-//   2. admits waiting requests in arrival order while they fit: H2D of their
-//      ASCII through a pinned staging buffer, 2-bit packing into the arena,
-//      per-slot metadata, zeroed window state (on the copy stream);
+//   2. admits waiting requests in arrival order while they fit: one H2D of
+//      their ASCII through a pinned staging buffer, one launch packing all of
+//      it into the arena, one writing every admitted pair's slot metadata
+//      and zeroing its window state (on the copy stream);
 //   3. launches the next step (after the copies, on the compute stream) and
 //      returns without waiting for it: every admitted pair advances by at
 //      most `max_windows` windows, its window state (positions, edit count,
 //      open CIGAR run) kept on the device;
 //   4. meanwhile, for every request whose pairs are all done, gathers the
-//      CIGAR runs into one buffer, copies distances, statuses and runs to host
-//      memory and frees the request's device space (copy stream);
+//      finished slots' outputs and CIGAR runs on the device and copies them
+//      back (the runs straight into a pinned result arena that holds them
+//      until the result is released), and frees the request's device space
+//      (copy stream);
 //   5. admits requests that arrived meanwhile, so their copies and packing
 //      overlap the running step and they join the next one.
 // Requests admitted at different steps therefore share launches and overlap
