@@ -419,10 +419,11 @@ int ga_align_batch(const uint8_t* d_reads, const uint64_t* d_read_off, const uin
  * reaches the whole pattern within k edits the pair's status is
  * GA_PAIR_EXCEEDS_K. Tuning: the one ga_autotune_locate stored for this
  * device and (W, O, k), else the library default (ga_align_batch_locate_tuned
- * takes an explicit one). Workspace: ga_workspace_size_locate(n_pairs, W, O,
- * k, tuning) bytes. W <= GA_MAX_W_ONCHIP. Asynchronous on `stream`.
- * Errors: GA_EINVAL (also W > GA_MAX_W_ONCHIP or NULL start spans / starts),
- * GA_ENOSPC, GA_ECUDA.
+ * takes an explicit one). Windows of 65..128 bases run the same search and
+ * alignment with 128-bit vectors (tuning ignored). Workspace:
+ * ga_workspace_size_locate(n_pairs, W, O, k, tuning) bytes. Asynchronous on
+ * `stream`. Errors: GA_EINVAL (also NULL start spans / starts), GA_ENOSPC,
+ * GA_ECUDA.
  */
 int ga_align_batch_locate(const uint8_t* d_reads, const uint64_t* d_read_off,
                           const uint32_t* d_read_len, const uint8_t* d_refs,

@@ -8,6 +8,7 @@
 
 #include "genasm.h"
 #include "genasm_internal.h"
+#include "genasm_wide.h"
 #include "genasm_window.cuh"
 
 namespace ga {
@@ -231,7 +232,8 @@ int ga_align_batch_order(const uint8_t* d_reads, const uint64_t* d_read_off,
 
 int ga_workspace_size_locate(uint32_t n_pairs, int W, int O, int k, const ga_tuning* tuning,
                              size_t* bytes_out) {
-  if (!bytes_out || bad_wok(W, O, k) || wide_window(W)) return GA_EINVAL;
+  if (!bytes_out || bad_wok(W, O, k)) return GA_EINVAL;
+  if (wide_window(W)) return cuda_fail(ga::wide_workspace_bytes(n_pairs, bytes_out));
   ga::BatchPlan plan{};
   const int rc = resolve(W, O, k, tuning, &plan, 1);
   if (rc != GA_OK) return rc;
@@ -253,9 +255,16 @@ int ga_align_batch_locate_tuned(const uint8_t* d_reads, const uint64_t* d_read_o
                        O, k, d_dist, d_status, d_ref_consumed, d_cigar, d_cigar_off, d_n_runs,
                        d_n_windows, d_cells, &p);
   if (rc != GA_OK) return rc;
-  if (wide_window(W)) return GA_EINVAL;  // the locate step runs with on-chip windows
   if (n_pairs > 0 && (!d_start_span || !d_ref_start)) return GA_EINVAL;
   if (n_pairs == 0) return GA_OK;
+  if (wide_window(W)) {  // 128-bit windows: the wide locate step and kernel (no tuning)
+    size_t need = 0;
+    const cudaError_t e = ga::wide_workspace_bytes(n_pairs, &need);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (!d_workspace || ws_bytes < need) return GA_ENOSPC;
+    return cuda_fail(ga::launch_wide_locate(p, d_start_span, d_ref_start, d_workspace, ws_bytes,
+                                            reinterpret_cast<cudaStream_t>(stream)));
+  }
   ga::BatchPlan plan{};
   rc = resolve(W, O, k, tuning, &plan, 1);
   if (rc != GA_OK) return rc;

@@ -26,6 +26,7 @@
 #include "genasm_internal.h"
 #include "genasm_pair.cuh"
 #include "genasm_window.cuh"
+#include "genasm_wide.h"
 
 namespace ga {
 
@@ -61,6 +62,24 @@ __device__ __forceinline__ u128 shfl_down128(u128 v, int delta) {
 }
 
 __device__ __forceinline__ bool bit128(u128 v, int b) { return static_cast<bool>((v >> b) & 1u); }
+
+// v << s for a run-time s in 0..127, on the 64-bit halves: a device left
+// shift of the 128-bit type by a run-time amount of 64 or more left the low
+// word's bits s - 64 set in this build (the pattern masks of the locate step
+// came out with each cleared bit j >= 64 also cleared at j - 64).
+__device__ __forceinline__ u128 shl128(u128 v, int s) {
+  const uint64_t lo = static_cast<uint64_t>(v);
+  const uint64_t hi = static_cast<uint64_t>(v >> 64);
+  uint64_t nlo = lo, nhi = hi;
+  if (s >= 64) {
+    nlo = 0;
+    nhi = lo << (s - 64);
+  } else if (s > 0) {
+    nlo = lo << s;
+    nhi = (hi << s) | (lo >> (64 - s));
+  }
+  return (static_cast<u128>(nhi) << 64) | nlo;
+}
 
 __device__ __forceinline__ void stg128(u128* p, u128 v) {
   *reinterpret_cast<ulonglong2*>(p) =
@@ -394,7 +413,7 @@ __global__ void __launch_bounds__(kWThreads, kBlocksPerSm) align_wide_kernel(con
 }
 
 struct WideLayout {
-  size_t queue, hist, order, tables, total;
+  size_t queue, hist, order, locate, tables, total;
 };
 
 template <int kBlocksPerSm, int WW>
@@ -433,10 +452,174 @@ WideLayout wide_layout(uint32_t n_pairs, int blocks) {
   L.queue = 0;
   L.hist = up(L.queue + 256);
   L.order = up(L.hist + sizeof(uint32_t) * kLptBuckets);
-  L.tables = up(L.order + sizeof(uint32_t) * static_cast<size_t>(n_pairs));
+  L.locate = up(L.order + sizeof(uint32_t) * static_cast<size_t>(n_pairs));
+  L.tables = up(L.locate + sizeof(int32_t) * static_cast<size_t>(n_pairs));
   const size_t groups = static_cast<size_t>(blocks) * (kWThreads / kWG);
   L.total = up(L.tables + groups * kWTableEntries * sizeof(u128));
   return L;
+}
+
+// ---------------------------------------------------------------------------
+// Free-start first window for 64 < W <= 128: the locate step of the batched
+// path (genasm_align.cu) with 128-bit vectors. For a pair with start span
+// S > 0 the first read window's pattern (wp = min(W, m) bases) is searched in
+// the reference's first L = min(n, S + W) bases; every start column s =
+// 0..min(S, L) is a candidate (s = L: the empty text, wp insertions) and the
+// leftmost column with the fewest edits is where the alignment begins. One
+// group of 16 lanes per pair; the long text in 128-column chunks from its
+// right end to its left, each by the column-strip wavefront (lane c owns 8
+// columns), a chunk's right neighbour column passed on through shared memory;
+// rows 0..15 first, rows 0..k when no start is found within 15 edits.
+// ---------------------------------------------------------------------------
+
+constexpr int kWLocateGroups = kWThreads / kWG;  // pairs per block
+constexpr int kWLocateCap = 15;
+
+// The smallest (d << 32 | s) over rows d <= rcap and candidate columns
+// s <= smax where the whole pattern is active, or ~0. `nchunks` is
+// warp-uniform; bnd: 2 * kWRows entries of this group.
+__device__ uint64_t wide_locate_pass(int r, bool go, const uint8_t* __restrict__ ref, uint32_t L,
+                                     uint32_t smax, int wp, int rcap, uint32_t nchunks,
+                                     const u128 (&pmc)[4], u128* bnd) {
+  constexpr int G = kWG;
+  constexpr int C = kWW / G;
+  const int c0 = r * C;
+  const u128 ones = ~static_cast<u128>(0);
+  u128* bin = bnd;
+  u128* bout = bnd + kWRows;
+  for (int d = r; d <= rcap; d += G) bin[d] = d >= kWW ? static_cast<u128>(0) : shl128(ones, d);
+  __syncwarp();
+  const uint32_t own = (L + kWW - 1) / kWW;  // this group's chunks
+  uint64_t best = ~0ull;
+  for (uint32_t ck = nchunks; ck-- > 0;) {
+    const bool live = go && ck < own;
+    const uint32_t cb = ck * static_cast<uint32_t>(kWW);
+    u128 pm[C];
+#pragma unroll
+    for (int x = 0; x < C; ++x) {
+      const uint32_t col = cb + static_cast<uint32_t>(c0 + x);
+      const bool in = live && col < L;
+      const uint32_t c = in ? base_at(ref, col) : 0u;
+      const u128 v = c == 0 ? pmc[0] : c == 1 ? pmc[1] : c == 2 ? pmc[2] : pmc[3];
+      pm[x] = in ? v : ones;
+    }
+    u128 P[C], PS[C];
+#pragma unroll
+    for (int x = 0; x < C; ++x) {
+      P[x] = ones;
+      PS[x] = ones;
+    }
+    u128 Pr = ones, PrS = ones, leftmost = ones;
+    for (int t = 0; t < rcap + G; ++t) {
+      const int d = t - (G - 1 - r);
+      const u128 from_right = shfl_down128<G>(leftmost, 1);
+      const u128 right = r == G - 1 ? (d <= rcap ? bin[d] : ones) : from_right;
+      const u128 low = d < 0 ? 1u : 0u;  // rows below 0 are all ones
+      u128 X[C];
+#pragma unroll
+      for (int x = 0; x < C; ++x) {
+        const u128 up_r = x == C - 1 ? Pr : P[x + 1];
+        const u128 up_rs = x == C - 1 ? PrS : PS[x + 1];
+        X[x] = up_rs & PS[x] & up_r;
+      }
+      u128 curS = (right << 1) | low;
+      PrS = curS;
+      Pr = right;
+#pragma unroll
+      for (int x = C - 1; x >= 0; --x) {
+        const u128 nv = (curS | pm[x]) & X[x];
+        curS = (nv << 1) | low;
+        P[x] = nv;
+        PS[x] = curS;
+      }
+      leftmost = P[0];
+      const bool row = d >= 0 && d <= rcap;
+      if (r == 0 && row) bout[d] = P[0];
+      if (live && row) {
+#pragma unroll
+        for (int x = C - 1; x >= 0; --x) {  // leftmost candidate last, so it wins
+          const uint32_t col = cb + static_cast<uint32_t>(c0 + x);
+          const uint64_t key = (static_cast<uint64_t>(d) << 32) | col;
+          if (col <= smax && col < L && !bit128(P[x], wp - 1) && key < best) best = key;
+        }
+      }
+    }
+    __syncwarp();
+    u128* tmp = bin;
+    bin = bout;
+    bout = tmp;
+  }
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) best = min(best, __shfl_xor_sync(kFull, best, o, G));
+  return best;
+}
+
+__global__ void __launch_bounds__(kWThreads) wide_locate_kernel(const AlignParams p,
+                                                                const uint32_t* start_span,
+                                                                int32_t* ref_start,
+                                                                int32_t* locate_d) {
+  constexpr int G = kWG;
+  __shared__ u128 bnd_all[kWLocateGroups][2 * kWRows];
+  const int lane = threadIdx.x & 31;
+  const int group = threadIdx.x / G;
+  const int r = lane % G;
+  const uint32_t pair = blockIdx.x * kWLocateGroups + group;
+  const bool valid = pair < p.n_pairs;
+  uint32_t m = 0, n = 0, S = 0;
+  if (valid) {
+    m = p.read_len[pair];
+    n = p.ref_len[pair];
+    S = start_span[pair];
+  }
+  const bool go = valid && S > 0 && m > 0;
+  const int wp = go ? static_cast<int>(min(m, static_cast<uint32_t>(p.W))) : 1;
+  const uint64_t span_end = static_cast<uint64_t>(S) + static_cast<uint64_t>(p.W);
+  const uint32_t L = go ? static_cast<uint32_t>(min(static_cast<uint64_t>(n), span_end)) : 0u;
+  // Pattern masks of the read's first wp bases: bit j of pmc[c] is clear
+  // where read base wp-1-j is c (bits at and above wp stay set).
+  u128 pmc[4] = {~static_cast<u128>(0), ~static_cast<u128>(0), ~static_cast<u128>(0),
+                 ~static_cast<u128>(0)};
+  if (go) {
+    const uint8_t* read = p.reads + p.read_off[pair];
+    for (int j = 0; j < wp; ++j) {
+      const uint32_t c = base_at(read, static_cast<uint32_t>(wp - 1 - j));
+      const u128 clear = ~shl128(static_cast<u128>(1), j);
+      pmc[0] &= c == 0 ? clear : ~static_cast<u128>(0);
+      pmc[1] &= c == 1 ? clear : ~static_cast<u128>(0);
+      pmc[2] &= c == 2 ? clear : ~static_cast<u128>(0);
+      pmc[3] &= c == 3 ? clear : ~static_cast<u128>(0);
+    }
+  }
+  const uint8_t* ref = valid ? p.refs + p.ref_off[pair] : p.refs;
+  // The empty text (s = L) is a candidate when S reaches it: wp insertions.
+  uint64_t best = ~0ull;
+  if (go && S >= L && wp <= p.kmax) best = (static_cast<uint64_t>(wp) << 32) | L;
+  const int cap1 = min(kWLocateCap, p.kmax);
+  const uint32_t chunks = (L + kWW - 1) / kWW;
+  const uint32_t nchunks = __reduce_max_sync(kFull, chunks);
+  const uint32_t smax = min(S, L);
+  u128* bnd = bnd_all[group];
+  if (__any_sync(kFull, go && L > 0))
+    best = min(best, wide_locate_pass(r, go && L > 0, ref, L, smax, wp, cap1, nchunks, pmc, bnd));
+  // Nothing within cap1 edits: every row up to k.
+  const bool again = go && L > 0 && (best >> 32) > static_cast<uint64_t>(cap1) && p.kmax > cap1;
+  if (__any_sync(kFull, again)) {
+    const uint32_t n2 = __reduce_max_sync(kFull, again ? chunks : 0u);
+    const uint64_t b2 = wide_locate_pass(r, again, ref, L, smax, wp, p.kmax, n2, pmc, bnd);
+    if (again) best = min(best, b2);
+  }
+  if (valid && r == 0) {
+    if (!go) {
+      ref_start[pair] = 0;
+      locate_d[pair] = -1;
+    } else if (best == ~0ull) {
+      ref_start[pair] = -1;
+      locate_d[pair] = -1;
+    } else {
+      ref_start[pair] = static_cast<int32_t>(best & 0xffffffffu);
+      locate_d[pair] = static_cast<int32_t>(best >> 32);
+    }
+  }
 }
 
 }  // namespace
@@ -477,6 +660,26 @@ cudaError_t launch_wide(const AlignParams& p, bool lpt, void* ws, size_t ws_byte
   }
   count_launches(1);
   return cudaGetLastError();
+}
+
+cudaError_t launch_wide_locate(const AlignParams& p, const uint32_t* start_span, int32_t* ref_start,
+                               void* ws, size_t ws_bytes, cudaStream_t s) {
+  if (p.n_pairs == 0) return cudaSuccess;
+  int b2 = 0, b3 = 0;
+  cudaError_t e = wide_grids(p.W, &b2, &b3);
+  if (e != cudaSuccess) return e;
+  const WideLayout L = wide_layout(p.n_pairs, std::max(b2, b3));
+  if (ws_bytes < L.total) return cudaErrorInvalidValue;
+  int32_t* locate_d = reinterpret_cast<int32_t*>(static_cast<char*>(ws) + L.locate);
+  const uint32_t blocks = (p.n_pairs + kWLocateGroups - 1) / kWLocateGroups;
+  wide_locate_kernel<<<blocks, kWThreads, 0, s>>>(p, start_span, ref_start, locate_d);
+  count_launches(1);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  AlignParams q = p;
+  q.start_span = start_span;
+  q.ref_start = ref_start;
+  q.locate_d = locate_d;
+  return launch_wide(q, true, ws, ws_bytes, s);
 }
 
 }  // namespace ga

@@ -86,6 +86,20 @@ def test_locate_window_geometry(W, O):
                 oracle.align(b, W=W, O=O, k=W, start_span=spans), f"W{W}O{O}")
 
 
+@pytest.mark.parametrize("W,O", [(128, 48), (96, 36), (80, 24), (65, 0)])
+def test_locate_wide_windows(W, O):
+    # Windows of 65-128 bases: the locate step with 128-bit vectors, then the wide kernel
+    # from the starts it finds (both builds of the kernel, band and full tables).
+    pairs, spans = flanked_pairs(150, seed=W + O + 1, max_len=600, max_flank=300)
+    b = datagen.from_pairs(pairs)
+    assert_same(b, run_locate(b, spans, W=W, O=O, k=W),
+                oracle.align(b, W=W, O=O, k=W, start_span=spans), f"W{W}O{O}")
+    w = datagen.make_batch(4, pair_ids=list(range(300, 420)))
+    ws = (w.ref_len.astype(np.int64) + 19) // 20
+    assert_same(w, run_locate(w, ws, W=W, O=O, k=W),
+                oracle.align(w, W=W, O=O, k=W, start_span=ws), f"workload 4, W{W}O{O}")
+
+
 def test_locate_error_cap():
     # k below the search's edit count: the pair fails in the locate step.
     pairs, spans = flanked_pairs(200, seed=9, max_len=120)

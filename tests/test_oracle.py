@@ -555,6 +555,22 @@ def test_free_start_equals_textbook_model(W, O):
             assert got == want, (variant, P, T, S)
 
 
+@pytest.mark.parametrize("W,O", [(100, 30), (128, 48)])
+def test_free_start_equals_textbook_model_wide(W, O):
+    # The same restatement for windows of 65-128 bases (128-bit vectors in the oracle).
+    pairs = _flanked_pairs(20, seed=W + O, max_len=3 * W, max_flank=2 * W)
+    b = datagen.from_pairs([(P, T) for P, T, _ in pairs])
+    spans = np.array([S for _, _, S in pairs])
+    r = oracle.align(b, W=W, O=O, k=W, start_span=spans)
+    for p, (P, T, S) in enumerate(pairs):
+        want = pins.windowed_textbook(P.encode(), T.encode(), W, O, start_span=S)
+        got = (int(r.dist[p]), int(r.ref_consumed[p]), int(r.n_windows[p]), int(r.cells[p]),
+               r.cigar_str(p))
+        if S > 0 and P:
+            got += (int(r.ref_start[p]),)
+        assert got == want, (P, T, S)
+
+
 def test_free_start_improved_equals_unimproved_on_workloads():
     for config, ids in ((2, [0, 3, 7]), (3, range(40, 52)), (4, range(200, 260)), (1, range(0, 100))):
         b = datagen.make_batch(config, pair_ids=list(ids))
