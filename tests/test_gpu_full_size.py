@@ -116,3 +116,22 @@ def test_full_workload_free_start(config):
     torch.cuda.synchronize()
     check_all_pairs(db, with_start=True)
     compare_batch(batch, db, torch, ga, label=f"workload {config}, free start", start_span=spans)
+
+
+def test_full_workload_free_start_wide_windows():
+    # Workload 2 with the free-start first window at W = 128 (the 128-bit locate
+    # kernel, then the 128-bit alignment from the start it finds), every pair
+    # against the oracle, the start included.
+    import numpy as np
+    W, O = 128, 48
+    batch = datagen.make_batch(2, workers=WORKERS)
+    spans = (batch.ref_len.astype(np.int64) + 19) // 20
+    db = DeviceBatch(batch, W=W, O=O, k=W)
+    db.pack()
+    for t in (db.dist, db.status, db.ref_consumed, db.n_runs, db.n_windows, db.cells):
+        t.fill_(-9)
+    db.align_locate(spans, stats=True)
+    torch.cuda.synchronize()
+    check_all_pairs(db, with_start=True)
+    compare_batch(batch, db, torch, ga, W=W, O=O, k=W, label="workload 2, W = 128, free start",
+                  start_span=spans)
