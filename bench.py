@@ -770,10 +770,15 @@ def run_free_start(args, batch, db, dev, stream, ga, peak_mix, anchored, barrier
 
 def run_window_sweep(db, dev, ga):
     """The batched alignment of the same batch at other window sizes W (overlap O = 3W/8, the
-    64/24 ratio; no error cap): W <= 64 on the on-chip kernels, W > 64 on the 128-bit kernel."""
+    64/24 ratio; no error cap): W <= 64 on the on-chip kernels, W > 64 on the 128-bit kernel.
+    Each W also with the free-start first window (start span ceil(n / 20), as the free-start
+    leg), whose windows follow the read instead of the random left flank."""
     import torch
 
     n = db.n
+    rl = db.ref_len[:n].to(torch.int64)
+    spans = ((rl + 19) // 20).to(torch.int32)
+    ref_start = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
     rows = []
     for Wv in (32, 48, 64, 96, 128):
         Ov = (3 * Wv) // 8
@@ -792,9 +797,25 @@ def run_window_sweep(db, dev, ga):
         e1.record()
         torch.cuda.synchronize(dev)
         ms = e0.elapsed_time(e1)
-        rows.append({"W": Wv, "O": Ov, "k": Wv, "ms": ms, "pairs_per_s": n / (ms * 1e-3),
-                     "windows": windows, "all_ok": ok,
-                     "kernel": "128-bit, tables in the workspace" if Wv > 64 else "on-chip tables"})
+        row = {"W": Wv, "O": Ov, "k": Wv, "ms": ms, "pairs_per_s": n / (ms * 1e-3),
+               "windows": windows, "all_ok": ok,
+               "kernel": "128-bit, tables in the workspace" if Wv > 64 else "on-chip tables"}
+        del wsb
+        need = ga.ga_workspace_size_locate(n, Wv, Ov, Wv)
+        wsb = torch.empty(max(need, 1), dtype=torch.uint8, device=dev)
+        largs = (*args[:10], spans, ref_start, *args[10:18], wsb, need)
+        ga.ga_align_batch_locate(*largs)  # warm-up, with statistics
+        torch.cuda.synchronize(dev)
+        fwin = int(db.n_windows[:n].sum())
+        fok = bool((db.status[:n] == 0).all())
+        e0.record()
+        ga.ga_align_batch_locate(*largs)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        fms = e0.elapsed_time(e1)
+        row["free_start"] = {"ms": fms, "pairs_per_s": n / (fms * 1e-3), "windows": fwin,
+                             "all_ok": fok}
+        rows.append(row)
         del wsb
     return {"workload": "long-10kb-10000pairs (as the headline)", "rows": rows}
 
