@@ -167,7 +167,8 @@ int ga_tuning_set(int W, int O, int k, const ga_tuning* tuning);
  * ga_autotune_workspace_size(n_pairs, W, O, k) bytes. Synchronous: returns
  * once every run has finished. *best / *best_ms (either may be NULL) receive
  * the choice and its time. The paper gives no tuning procedure.
- * Errors: GA_EINVAL, GA_ENOSPC (no candidate fits the workspace), GA_ECUDA.
+ * Errors: GA_EINVAL (also for W > GA_MAX_W_ONCHIP: the 128-bit kernel has no
+ * tuning), GA_ENOSPC (no candidate fits the workspace), GA_ECUDA.
  */
 int ga_autotune(const uint8_t* d_reads, const uint64_t* d_read_off, const uint32_t* d_read_len,
                 const uint8_t* d_refs, const uint64_t* d_ref_off, const uint32_t* d_ref_len,
@@ -454,7 +455,8 @@ int ga_workspace_size_locate(uint32_t n_pairs, int W, int O, int k, const ga_tun
  * start spans, and the fastest is stored as the device's free-start default
  * for (W, O, k) (kept apart from ga_autotune's). Arguments as
  * ga_align_batch_locate; workspace ga_autotune_workspace_size bytes.
- * Errors: GA_EINVAL, GA_ENOSPC, GA_ECUDA.
+ * Errors: GA_EINVAL (also for W > GA_MAX_W_ONCHIP, as ga_autotune),
+ * GA_ENOSPC, GA_ECUDA.
  */
 int ga_autotune_locate(const uint8_t* d_reads, const uint64_t* d_read_off,
                        const uint32_t* d_read_len, const uint8_t* d_refs,

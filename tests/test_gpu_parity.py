@@ -244,6 +244,12 @@ def test_bad_arguments_rejected():
                           64, 24, 64, db.dist, db.status, db.ref_consumed, db.cigar, db.cigar_off,
                           db.n_runs, None, None)
     assert e.value.code == ga.GA_EINVAL
+    # The autotuner has nothing to tune for windows wider than 64 bases.
+    with pytest.raises(ga.GenasmError) as e:
+        ga.ga_autotune(db.reads, db.read_off, db.read_len, db.refs, db.ref_off, db.ref_len, 4,
+                       128, 48, 128, db.dist, db.status, db.ref_consumed, db.cigar, db.cigar_off,
+                       db.n_runs, db.n_windows, db.cells, db.workspace, db.ws_bytes)
+    assert e.value.code == ga.GA_EINVAL
 
 
 def test_cigar_capacity_overflow():
