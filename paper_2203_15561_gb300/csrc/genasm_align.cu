@@ -708,10 +708,11 @@ cudaError_t launch_batched(const AlignParams& p, const BatchPlan& plan, void* ws
 // neighbour column comes from the chunk processed before it: lane 0 records
 // its leftmost cell of every row in shared memory, and lane G-1 of the next
 // chunk reads it there (two buffers, swapped per chunk). The recurrence runs
-// right to left, so the chunks must all hold the same rows: a first pass
-// computes rows 0..kLocateCap and finds the start whenever some column gets
-// the whole pattern within that many edits; otherwise a second pass computes
-// rows 0..k. Columns past L use all-ones masks, which keep the initial column.
+// right to left, so a chunk holds the rows of every chunk to its left: a
+// first pass computes rows 0..kLocateCap (fewer once a start is found) and
+// finds the start whenever some column gets the whole pattern within that
+// many edits; otherwise a second pass computes rows 0..k. Columns past L use
+// all-ones masks, which keep the initial column.
 // ---------------------------------------------------------------------------
 
 constexpr int kLocateG = 8;
@@ -722,6 +723,12 @@ constexpr int kLocateCap = 15;
 // rows d <= rcap and candidate columns s <= smax with the whole pattern
 // active, or ~0. `nchunks` is warp-uniform; chunks at or past a group's own
 // count are skipped by its predicate. bnd: 2 * kMaxRows words of this group.
+//
+// Once a start on row d0 is known, a chunk further left can only win on a
+// row <= d0 (the same row with a smaller column), so every later chunk stops
+// at row min(rcap, d0): the rows it needs from its right neighbour are rows
+// the previous chunk computed. A step tests its row with one AND over the
+// strip (some column has bit wp-1 clear) and finds the column only then.
 template <int G>
 __device__ uint64_t locate_pass(int r, bool go, const uint8_t* __restrict__ ref, uint32_t L,
                                 uint32_t smax, int wp, int rcap, uint32_t nchunks,
@@ -731,10 +738,10 @@ __device__ uint64_t locate_pass(int r, bool go, const uint8_t* __restrict__ ref,
   const uint64_t msb = 1ull << (wp - 1);
   uint64_t* bin = bnd;
   uint64_t* bout = bnd + kMaxRows;
-  for (int d = r; d <= rcap; d += G) bin[d] = d >= 64 ? 0ull : (~0ull << d);  // the initial column
-  __syncwarp();
   const uint32_t own = (L + 63) / 64;  // this group's chunks
   uint64_t best = ~0ull;
+  int cap = rcap;     // group-uniform: the rows this chunk needs
+  bool fresh = true;  // no chunk of this group done yet: its right neighbour is the initial column
   for (uint32_t ck = nchunks; ck-- > 0;) {
     const bool live = go && ck < own;
     const uint32_t cb = ck * 64u;
@@ -754,10 +761,13 @@ __device__ uint64_t locate_pass(int r, bool go, const uint8_t* __restrict__ ref,
       PS[x] = ~0ull;
     }
     uint64_t Pr = ~0ull, PrS = ~0ull, leftmost = ~0ull;
-    for (int t = 0; t < rcap + G; ++t) {
+    const int steps = __reduce_max_sync(kFull, static_cast<uint32_t>(live ? cap + G : 0));
+    for (int t = 0; t < steps; ++t) {
       const int d = t - (G - 1 - r);
       const uint64_t from_right = __shfl_down_sync(kFull, leftmost, 1, G);
-      const uint64_t right = r == G - 1 ? (d <= rcap ? bin[d] : ~0ull) : from_right;
+      const uint64_t init = d >= 64 ? 0ull : (~0ull << (d & 63));  // R_L[d] (lane G-1: d >= 0)
+      const uint64_t right =
+          r == G - 1 ? (d <= cap ? (fresh ? init : bin[d]) : ~0ull) : from_right;
       const uint32_t low = d < 0 ? 1u : 0u;
       uint64_t X[C];
 #pragma unroll
@@ -777,21 +787,30 @@ __device__ uint64_t locate_pass(int r, bool go, const uint8_t* __restrict__ ref,
         PS[x] = curS;
       }
       leftmost = P[0];
-      const bool row = d >= 0 && d <= rcap;
+      const bool row = d >= 0 && d <= cap;
       if (r == 0 && row) bout[d] = P[0];
-      if (live && row) {
+      uint64_t all = P[0];
 #pragma unroll
-        for (int x = C - 1; x >= 0; --x) {  // leftmost candidate last, so it wins
-          const uint32_t col = cb + static_cast<uint32_t>(c0 + x);
-          const uint64_t key = (static_cast<uint64_t>(d) << 32) | col;
-          if (col <= smax && col < L && !(P[x] & msb) && key < best) best = key;
-        }
+      for (int x = 1; x < C; ++x) all &= P[x];
+      if (live && row && !(all & msb)) {  // some column of the strip is solved on row d
+        int x = C;
+#pragma unroll
+        for (int y = C - 1; y >= 0; --y) x = (P[y] & msb) ? x : y;  // the leftmost one
+        const uint32_t col = cb + static_cast<uint32_t>(c0 + x);
+        const uint64_t key = (static_cast<uint64_t>(d) << 32) | col;
+        if (col <= smax && col < L && key < best) best = key;
       }
     }
     __syncwarp();
     uint64_t* t = bin;
     bin = bout;
     bout = t;
+    fresh = fresh && !live;
+    // The group's best row so far bounds the rows of the chunks to its left.
+    uint64_t gb = best;
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) gb = min(gb, __shfl_xor_sync(kFull, gb, o, G));
+    if (gb != ~0ull) cap = min(cap, static_cast<int>(gb >> 32));
   }
 #pragma unroll
   for (int o = G / 2; o > 0; o >>= 1) best = min(best, __shfl_xor_sync(kFull, best, o, G));

@@ -469,7 +469,9 @@ WideLayout wide_layout(uint32_t n_pairs, int blocks) {
 // group of 16 lanes per pair; the long text in 128-column chunks from its
 // right end to its left, each by the column-strip wavefront (lane c owns 8
 // columns), a chunk's right neighbour column passed on through shared memory;
-// rows 0..15 first, rows 0..k when no start is found within 15 edits.
+// rows 0..15 first, rows 0..k when no start is found within 15 edits; once a
+// start on row d0 is known, the chunks to its left stop at row d0 (see
+// locate_pass in genasm_align.cu).
 // ---------------------------------------------------------------------------
 
 constexpr int kWLocateGroups = kWThreads / kWG;  // pairs per block
@@ -487,10 +489,10 @@ __device__ uint64_t wide_locate_pass(int r, bool go, const uint8_t* __restrict__
   const u128 ones = ~static_cast<u128>(0);
   u128* bin = bnd;
   u128* bout = bnd + kWRows;
-  for (int d = r; d <= rcap; d += G) bin[d] = d >= kWW ? static_cast<u128>(0) : shl128(ones, d);
-  __syncwarp();
   const uint32_t own = (L + kWW - 1) / kWW;  // this group's chunks
   uint64_t best = ~0ull;
+  int cap = rcap;     // group-uniform: the rows this chunk needs
+  bool fresh = true;  // no chunk of this group done yet: its right neighbour is the initial column
   for (uint32_t ck = nchunks; ck-- > 0;) {
     const bool live = go && ck < own;
     const uint32_t cb = ck * static_cast<uint32_t>(kWW);
@@ -510,10 +512,13 @@ __device__ uint64_t wide_locate_pass(int r, bool go, const uint8_t* __restrict__
       PS[x] = ones;
     }
     u128 Pr = ones, PrS = ones, leftmost = ones;
-    for (int t = 0; t < rcap + G; ++t) {
+    const int steps = __reduce_max_sync(kFull, static_cast<uint32_t>(live ? cap + G : 0));
+    for (int t = 0; t < steps; ++t) {
       const int d = t - (G - 1 - r);
       const u128 from_right = shfl_down128<G>(leftmost, 1);
-      const u128 right = r == G - 1 ? (d <= rcap ? bin[d] : ones) : from_right;
+      const u128 init = d >= kWW ? static_cast<u128>(0) : shl128(ones, d & (kWW - 1));  // R_L[d]
+      const u128 right =
+          r == G - 1 ? (d <= cap ? (fresh ? init : bin[d]) : ones) : from_right;
       const u128 low = d < 0 ? 1u : 0u;  // rows below 0 are all ones
       u128 X[C];
 #pragma unroll
@@ -533,21 +538,30 @@ __device__ uint64_t wide_locate_pass(int r, bool go, const uint8_t* __restrict__
         PS[x] = curS;
       }
       leftmost = P[0];
-      const bool row = d >= 0 && d <= rcap;
+      const bool row = d >= 0 && d <= cap;
       if (r == 0 && row) bout[d] = P[0];
-      if (live && row) {
+      u128 all = P[0];
 #pragma unroll
-        for (int x = C - 1; x >= 0; --x) {  // leftmost candidate last, so it wins
-          const uint32_t col = cb + static_cast<uint32_t>(c0 + x);
-          const uint64_t key = (static_cast<uint64_t>(d) << 32) | col;
-          if (col <= smax && col < L && !bit128(P[x], wp - 1) && key < best) best = key;
-        }
+      for (int x = 1; x < C; ++x) all &= P[x];
+      if (live && row && !bit128(all, wp - 1)) {  // some column of the strip is solved on row d
+        int x = C;
+#pragma unroll
+        for (int y = C - 1; y >= 0; --y) x = bit128(P[y], wp - 1) ? x : y;  // the leftmost one
+        const uint32_t col = cb + static_cast<uint32_t>(c0 + x);
+        const uint64_t key = (static_cast<uint64_t>(d) << 32) | col;
+        if (col <= smax && col < L && key < best) best = key;
       }
     }
     __syncwarp();
     u128* tmp = bin;
     bin = bout;
     bout = tmp;
+    fresh = fresh && !live;
+    // The group's best row so far bounds the rows of the chunks to its left.
+    uint64_t gb = best;
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) gb = min(gb, __shfl_xor_sync(kFull, gb, o, G));
+    if (gb != ~0ull) cap = min(cap, static_cast<int>(gb >> 32));
   }
 #pragma unroll
   for (int o = G / 2; o > 0; o >>= 1) best = min(best, __shfl_xor_sync(kFull, best, o, G));
