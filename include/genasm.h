@@ -254,11 +254,13 @@ int ga_align_batch_noalloc(const uint8_t* d_reads, const uint64_t* d_read_off,
  * slots with saved window state, staging buffers. ga_server_submit copies a
  * request (host ASCII, like the inputs of ga_pack_2bit; any offsets) and
  * queues it; it returns GA_ENOMEM if the request could never fit the server.
- * ga_server_step (synchronous) admits queued requests in arrival order while
- * the budget has room, advances every admitted pair by at most
- * `step_windows` windows (default 32) with its window state kept on the
- * device between steps, and completes every request whose pairs are all done
- * (results copied to host memory: the CIGAR runs into a pinned arena of a
+ * ga_server_step waits for the step in flight (if any) and takes its
+ * finished pairs, admits queued requests in arrival order while the budget
+ * has room, and launches the next step (one captured CUDA graph), which
+ * advances every admitted pair by at most `step_windows` windows (default
+ * 32) with its window state kept on the device between steps; it returns
+ * while that step runs. Meanwhile it completes every request whose pairs are
+ * all done (results copied to host memory: the CIGAR runs into a pinned arena of a
  * sixteenth of the budget, 16 MB to 2 GB, held until the result is released,
  * else into ordinary host memory; device space freed). Requests that arrive
  * while others are in flight join at the next step and share its launch.
