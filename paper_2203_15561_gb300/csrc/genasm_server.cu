@@ -31,11 +31,16 @@
 // admission. Every wait is a host-side event or stream synchronization; no
 // kernel waits on another.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
+#include <condition_variable>
 #include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -170,6 +175,99 @@ double now_ms(std::chrono::steady_clock::time_point t0) {
   return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
 }
 
+// Host copies of requests' ASCII, split over a few threads: a request of 32
+// pairs of ~8 kb is ~0.5 MB, and one admission at saturation copies hundreds
+// of them into the pinned staging buffer. The calling thread copies too. A
+// call returns only once every worker has finished with it (so the next call
+// may refill the piece list), and idle workers spin (yielding) for a few
+// milliseconds before they sleep, so back-to-back calls rarely pay a wake-up.
+class CopyPool {
+ public:
+  struct Job {
+    void* dst;
+    const void* src;
+    size_t bytes;
+  };
+  explicit CopyPool(unsigned workers) : n_(workers) {
+    for (unsigned i = 0; i < workers; ++i) threads_.emplace_back([this] { loop(); });
+  }
+  ~CopyPool() {
+    {
+      std::lock_guard<std::mutex> g(m_);
+      stop_.store(true, std::memory_order_relaxed);
+      gen_.fetch_add(1, std::memory_order_release);
+    }
+    cv_.notify_all();
+    for (std::thread& t : threads_) t.join();
+  }
+  // Copies every job; returns when all of them are done.
+  void copy(const std::vector<Job>& jobs) {
+    size_t total = 0;
+    for (const Job& j : jobs) total += j.bytes;
+    if (n_ == 0 || total < kParallelMin) {
+      for (const Job& j : jobs) std::memcpy(j.dst, j.src, j.bytes);
+      return;
+    }
+    pieces_.clear();
+    for (const Job& j : jobs)
+      for (size_t o = 0; o < j.bytes; o += kPiece)
+        pieces_.push_back(Job{static_cast<char*>(j.dst) + o, static_cast<const char*>(j.src) + o,
+                              std::min(kPiece, j.bytes - o)});
+    next_.store(0, std::memory_order_relaxed);
+    acks_.store(0, std::memory_order_relaxed);
+    {
+      std::lock_guard<std::mutex> g(m_);
+      gen_.fetch_add(1, std::memory_order_release);
+    }
+    cv_.notify_all();
+    work();
+    while (acks_.load(std::memory_order_acquire) < n_) std::this_thread::yield();
+  }
+
+ private:
+  static constexpr size_t kPiece = size_t(256) << 10;
+  static constexpr size_t kParallelMin = size_t(256) << 10;  // below: the caller alone
+  static constexpr int kSpins = 20000;
+  void work() {
+    const size_t n = pieces_.size();
+    for (size_t i; (i = next_.fetch_add(1, std::memory_order_relaxed)) < n;)
+      std::memcpy(pieces_[i].dst, pieces_[i].src, pieces_[i].bytes);
+  }
+  void loop() {
+    uint64_t seen = 0;
+    for (;;) {
+      uint64_t g = gen_.load(std::memory_order_acquire);
+      for (int i = 0; g == seen && i < kSpins; ++i) {
+        std::this_thread::yield();
+        g = gen_.load(std::memory_order_acquire);
+      }
+      if (g == seen) {
+        std::unique_lock<std::mutex> lk(m_);
+        cv_.wait(lk, [&] { return gen_.load(std::memory_order_acquire) != seen; });
+        g = gen_.load(std::memory_order_acquire);
+      }
+      seen = g;
+      if (stop_.load(std::memory_order_relaxed)) return;
+      work();
+      acks_.fetch_add(1, std::memory_order_release);  // this worker's copies are done
+    }
+  }
+  const unsigned n_;
+  std::vector<std::thread> threads_;
+  std::vector<Job> pieces_;
+  std::atomic<size_t> next_{0};
+  std::atomic<unsigned> acks_{0};
+  std::atomic<uint64_t> gen_{0};
+  std::atomic<bool> stop_{false};
+  std::mutex m_;
+  std::condition_variable cv_;
+};
+
+unsigned copy_workers() {
+  const unsigned hc = std::thread::hardware_concurrency();
+  return std::min(4u, std::max(1u, hc / 4));
+}
+
 }  // namespace
 
 struct ga_server {
@@ -236,6 +334,8 @@ struct ga_server {
   // ASCII buffers of admitted requests, reused by later submissions (no
   // allocation and first-touch page faults per request)
   std::vector<std::vector<uint8_t>> ascii_pool;
+  std::unique_ptr<CopyPool> copies;         // host ASCII copies (submission, admission)
+  std::vector<CopyPool::Job> copy_jobs;
   std::vector<Request*> slot_owner;  // per slot
   std::vector<uint32_t> active;
   std::deque<Result*> ready;
@@ -387,6 +487,7 @@ extern "C" int ga_server_create(size_t budget_bytes, int W, int O, int k, ga_ser
   s->O = O;
   s->k = k;
   s->t0 = std::chrono::steady_clock::now();
+  s->copies.reset(new CopyPool(copy_workers()));
   cudaError_t e = cudaGetDevice(&s->device);
   // Step kernel tuning: the stored/default tuning when it has a step variant.
   ga_tuning t{};
@@ -515,17 +616,20 @@ extern "C" int ga_server_submit(ga_server* s, const ga_request* req, uint64_t* t
   r->read_len.assign(req->read_len, req->read_len + r->n);
   r->ref_len.assign(req->ref_len, req->ref_len + r->n);
   uint64_t at = 0;
+  std::vector<CopyPool::Job>& jobs = s->copy_jobs;
+  jobs.clear();
   for (uint32_t p = 0; p < r->n; ++p) {
     r->read_at[p] = at;
-    std::memcpy(r->ascii.data() + at, req->reads + req->read_off[p], req->read_len[p]);
+    jobs.push_back(CopyPool::Job{r->ascii.data() + at, req->reads + req->read_off[p], req->read_len[p]});
     std::memset(r->ascii.data() + at + req->read_len[p], 'A', (4 - req->read_len[p] % 4) % 4);  // padding
     at += (req->read_len[p] + 3ull) / 4 * 4;
     r->ref_at[p] = at;
-    std::memcpy(r->ascii.data() + at, req->refs + req->ref_off[p], req->ref_len[p]);
+    jobs.push_back(CopyPool::Job{r->ascii.data() + at, req->refs + req->ref_off[p], req->ref_len[p]});
     std::memset(r->ascii.data() + at + req->ref_len[p], 'A', (4 - req->ref_len[p] % 4) % 4);
     at += (req->ref_len[p] + 3ull) / 4 * 4;
     r->runs += static_cast<uint64_t>(req->read_len[p]) + req->ref_len[p] + 1;
   }
+  s->copies->copy(jobs);
   // A request that could never fit the server is refused now.
   if (r->n > s->slot_alloc.capacity() || r->runs > s->cig_alloc.capacity() ||
       r->ascii_bytes / 4 > s->seq_alloc.capacity() || r->ascii_bytes > s->ascii_cap ||
@@ -552,6 +656,9 @@ int admit(ga_server* s, std::vector<Request*>& finished) {
   uint64_t staged = 0, max_seg = 0;
   uint32_t n_segs = 0, n_recs = 0;
   bool any = false;
+  std::vector<CopyPool::Job>& jobs = s->copy_jobs;
+  jobs.clear();
+  std::vector<Request*> copied;
   // The pinned staging buffers are reused: the previous admission's copies
   // out of them must have completed before they are written again.
   if (s->staged && !s->pending.empty()) {
@@ -585,14 +692,8 @@ int admit(ga_server* s, std::vector<Request*>& finished) {
     r->cig_off = co;
     r->slot0 = sl;
     r->t_admit = now_ms(s->t0);
-    std::memcpy(s->h_ascii + staged, r->ascii.data(), abytes);
-    // The buffer goes back to the pool (a few dozen, none above 64 MB).
-    if (s->ascii_pool.size() < 64 && r->ascii.size() <= (64ull << 20)) {
-      s->ascii_pool.emplace_back();
-      s->ascii_pool.back().swap(r->ascii);
-    } else {
-      std::vector<uint8_t>().swap(r->ascii);
-    }
+    jobs.push_back(CopyPool::Job{s->h_ascii + staged, r->ascii.data(), abytes});
+    copied.push_back(r);
     s->h_segs[n_segs++] = ga::PackSegment{staged, so, abytes};
     max_seg = std::max(max_seg, abytes);
     uint64_t c = co;
@@ -615,6 +716,16 @@ int admit(ga_server* s, std::vector<Request*>& finished) {
     s->pending.pop_front();
   }
   if (!any) return GA_OK;
+  s->copies->copy(jobs);
+  for (Request* r : copied) {
+    // The buffer goes back to the pool (a few dozen, none above 64 MB).
+    if (s->ascii_pool.size() < 64 && r->ascii.size() <= (64ull << 20)) {
+      s->ascii_pool.emplace_back();
+      s->ascii_pool.back().swap(r->ascii);
+    } else {
+      std::vector<uint8_t>().swap(r->ascii);
+    }
+  }
   cudaStream_t st = s->stream;
   if (cudaMemcpyAsync(s->d_ascii, s->h_ascii, staged, cudaMemcpyHostToDevice, st) != cudaSuccess ||
       cudaMemcpyAsync(s->d_segs, s->h_segs, sizeof(ga::PackSegment) * n_segs,
