@@ -497,8 +497,9 @@ def run_serving(args, dev):
     oracle's arrays), each result released once it is checked. Keeping the
     results for a later check would hold the whole span's CIGARs (about 100 GB
     for 60 s) in host memory. A second span offers ten times the load (20,000
-    requests/s) to find the server's capacity and its latency when
-    saturated."""
+    requests/s) to find the server's capacity and its latency when saturated;
+    `kept_up` says whether the server finished within 10% of the span (then
+    the span measured the offered rate, a lower bound of the capacity)."""
     import collections
     import ctypes
     import queue
@@ -640,7 +641,8 @@ def run_serving(args, dev):
                "pairs": pairs, "read_bases": bases, "wall_s": wall, "pairs_per_s": pairs / wall,
                "gbases_per_s": bases / wall / 1e9, "offered_pairs_per_s": sum(len(q) for q in ids) / seconds,
                "steps": steps, "step_windows": STEP_WINDOWS, "budget_bytes": budget,
-               "kernel_launches": launches, **_percentiles(lat)}
+               "kernel_launches": launches, "kept_up": wall <= 1.1 * seconds,
+               **_percentiles(lat)}
         if check:
             out["oracle_check"] = {"requests": n_req, "differing_requests": len(bad),
                                    "pairs": int(sum(len(q) for q in ids)),

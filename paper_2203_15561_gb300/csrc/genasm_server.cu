@@ -28,7 +28,8 @@
 //      overlap the running step and they join the next one.
 // Requests admitted at different steps therefore share launches and overlap
 // on the device, and a finished request's memory is reused by the next
-// admission. Every wait is a host-side event or stream synchronization; no
+// admission. The host copies of request ASCII (at submission, and into the
+// pinned staging buffer at admission) run on a small pool of copy threads. Every wait is a host-side event or stream synchronization; no
 // kernel waits on another.
 #include <algorithm>
 #include <atomic>
