@@ -251,8 +251,10 @@ int ga_align_batch_noalloc(const uint8_t* d_reads, const uint64_t* d_read_off,
  *
  * ga_server_create allocates, once, at most budget_bytes of device memory on
  * the current device: arenas for packed sequences and CIGAR runs, per-pair
- * slots with saved window state, staging buffers. Windows of at most
- * GA_MAX_W_ONCHIP bases, anchored first windows (GA_EINVAL for W above it).
+ * slots with saved window state, staging buffers, and starts up to four host
+ * threads that copy request ASCII (joined by ga_server_destroy). Windows of at
+ * most GA_MAX_W_ONCHIP bases, anchored first windows (GA_EINVAL for W above
+ * it).
  * ga_server_submit copies a
  * request (host ASCII, like the inputs of ga_pack_2bit; any offsets) and
  * queues it; it returns GA_ENOMEM if the request could never fit the server.

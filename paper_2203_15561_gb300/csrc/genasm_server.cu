@@ -189,18 +189,18 @@ class CopyPool {
     const void* src;
     size_t bytes;
   };
-  explicit CopyPool(unsigned workers) : n_(workers) {
-    for (unsigned i = 0; i < workers; ++i) threads_.emplace_back([this] { loop(); });
-  }
-  ~CopyPool() {
-    {
-      std::lock_guard<std::mutex> g(m_);
-      stop_.store(true, std::memory_order_relaxed);
-      gen_.fetch_add(1, std::memory_order_release);
+  // A thread that cannot be started leaves the pool without workers (the
+  // caller then copies alone).
+  explicit CopyPool(unsigned workers) {
+    try {
+      for (unsigned i = 0; i < workers; ++i) threads_.emplace_back([this] { loop(); });
+      n_ = workers;
+    } catch (...) {
+      shutdown();
+      n_ = 0;
     }
-    cv_.notify_all();
-    for (std::thread& t : threads_) t.join();
   }
+  ~CopyPool() { shutdown(); }
   // Copies every job; returns when all of them are done.
   void copy(const std::vector<Job>& jobs) {
     size_t total = 0;
@@ -226,6 +226,16 @@ class CopyPool {
   }
 
  private:
+  void shutdown() {
+    {
+      std::lock_guard<std::mutex> g(m_);
+      stop_.store(true, std::memory_order_relaxed);
+      gen_.fetch_add(1, std::memory_order_release);
+    }
+    cv_.notify_all();
+    for (std::thread& t : threads_) t.join();
+    threads_.clear();
+  }
   static constexpr size_t kPiece = size_t(256) << 10;
   static constexpr size_t kParallelMin = size_t(256) << 10;  // below: the caller alone
   static constexpr int kSpins = 20000;
@@ -253,7 +263,7 @@ class CopyPool {
       acks_.fetch_add(1, std::memory_order_release);  // this worker's copies are done
     }
   }
-  const unsigned n_;
+  unsigned n_ = 0;
   std::vector<std::thread> threads_;
   std::vector<Job> pieces_;
   std::atomic<size_t> next_{0};
