@@ -595,13 +595,16 @@ def run_serving(args, dev):
         nres = ga._i(0)
         launches0 = ga.ga_launch_count()
         t0 = time.perf_counter()
-        nxt = done = inflight = 0
+        nxt = done = inflight = refused = 0
         while done < n_req:
             while done_t:
                 ga.ga_server_release(srv, done_t.popleft())
             now = time.perf_counter() - t0
             while nxt < n_req and arrivals[nxt] <= now:
                 rc = f_submit(srv, ctypes.byref(creqs[nxt]), ctypes.byref(tk))
+                if rc == ga.GA_EAGAIN:  # the server's pending limit: the rest wait (on the client)
+                    refused += 1
+                    break
                 if rc != 0:
                     raise RuntimeError(f"ga_server_submit failed: {rc}")
                 nxt += 1
@@ -642,6 +645,7 @@ def run_serving(args, dev):
                "gbases_per_s": bases / wall / 1e9, "offered_pairs_per_s": sum(len(q) for q in ids) / seconds,
                "steps": steps, "step_windows": STEP_WINDOWS, "budget_bytes": budget,
                "kernel_launches": launches, "kept_up": wall <= 1.1 * seconds,
+               "submissions_refused": refused,
                **_percentiles(lat)}
         if check:
             out["oracle_check"] = {"requests": n_req, "differing_requests": len(bad),

@@ -55,7 +55,7 @@ typedef struct CUstream_st* ga_stream_t; /* = cudaStream_t; NULL = legacy defaul
 #define GA_ECUDA (-3)      /* a CUDA call failed; see ga_last_cuda_error() */
 #define GA_ETIMEDOUT (-4)  /* a bounded wait ran out */
 #define GA_ENOMEM (-5)     /* the server's memory budget cannot hold the request */
-#define GA_EAGAIN (-6)     /* nothing ready yet (server poll) */
+#define GA_EAGAIN (-6)     /* nothing ready yet (server poll), or the server's waiting requests are at their limit (server submit) */
 
 /* Per-pair status written to d_status. */
 #define GA_PAIR_OK 0
@@ -257,7 +257,12 @@ int ga_align_batch_noalloc(const uint8_t* d_reads, const uint64_t* d_read_off,
  * it).
  * ga_server_submit copies a
  * request (host ASCII, like the inputs of ga_pack_2bit; any offsets) and
- * queues it; it returns GA_ENOMEM if the request could never fit the server.
+ * queues it; it returns GA_ENOMEM if the request could never fit the server,
+ * and GA_EAGAIN (nothing copied) while the requests already waiting for
+ * admission hold the server's pending limit of host copies
+ * (ga_server_set_pending_limit, bytes of 2-bit-rounded ASCII; default a
+ * sixteenth of the budget, 64 MB to 2 GB; 0 = none): step, poll and submit
+ * again. A request is always taken when none is waiting.
  * ga_server_step waits for the step in flight (if any) and takes its
  * finished pairs, admits queued requests in arrival order while the budget
  * has room, and launches the next step (one captured CUDA graph), which
@@ -296,6 +301,7 @@ typedef struct {
 } ga_result;
 int ga_server_create(size_t budget_bytes, int W, int O, int k, ga_server** out);
 int ga_server_set_step_windows(ga_server* server, uint32_t step_windows);
+int ga_server_set_pending_limit(ga_server* server, uint64_t bytes);
 int ga_server_submit(ga_server* server, const ga_request* request, uint64_t* ticket);
 int ga_server_step(ga_server* server, uint32_t* n_in_flight);
 int ga_server_poll(ga_server* server, ga_result* out, int max, int* n_out);

@@ -489,6 +489,11 @@ def ga_server_set_step_windows(server: int, step_windows: int) -> int:
     return _check(f(server, step_windows), "ga_server_set_step_windows")
 
 
+def ga_server_set_pending_limit(server: int, limit_bytes: int) -> int:
+    f = _typed("ga_server_set_pending_limit", _i, [_vp, _u64])
+    return _check(f(server, limit_bytes), "ga_server_set_pending_limit")
+
+
 def ga_server_submit(server: int, request: ga_request) -> int:
     f = _typed("ga_server_submit", _i, [_vp, ctypes.POINTER(ga_request), ctypes.POINTER(_u64)])
     t = _u64(0)

@@ -112,7 +112,7 @@ const char* ga_strerror(int code) {
     case GA_ECUDA: return "CUDA error";
     case GA_ETIMEDOUT: return "bounded wait timed out";
     case GA_ENOMEM: return "memory budget exceeded";
-    case GA_EAGAIN: return "nothing ready";
+    case GA_EAGAIN: return "nothing ready, or the server's waiting requests are at their limit (step, then retry)";
     default: return "unknown error";
   }
 }

@@ -345,6 +345,8 @@ struct ga_server {
   // ASCII buffers of admitted requests, reused by later submissions (no
   // allocation and first-touch page faults per request)
   std::vector<std::vector<uint8_t>> ascii_pool;
+  uint64_t pending_bytes = 0;  // host copies of the requests waiting for admission
+  uint64_t pending_cap = 0;    // submissions beyond it are refused (GA_EAGAIN); 0: no limit
   std::unique_ptr<CopyPool> copies;         // host ASCII copies (submission, admission)
   std::vector<CopyPool::Job> copy_jobs;
   std::vector<Request*> slot_owner;  // per slot
@@ -499,6 +501,7 @@ extern "C" int ga_server_create(size_t budget_bytes, int W, int O, int k, ga_ser
   s->k = k;
   s->t0 = std::chrono::steady_clock::now();
   s->copies.reset(new CopyPool(copy_workers()));
+  s->pending_cap = std::min<uint64_t>(std::max<uint64_t>(budget_bytes / 16, 64ull << 20), 2ull << 30);
   cudaError_t e = cudaGetDevice(&s->device);
   // Step kernel tuning: the stored/default tuning when it has a step variant.
   ga_tuning t{};
@@ -601,6 +604,12 @@ extern "C" int ga_server_create(size_t budget_bytes, int W, int O, int k, ga_ser
   return GA_OK;
 }
 
+extern "C" int ga_server_set_pending_limit(ga_server* s, uint64_t bytes) {
+  if (!s) return GA_EINVAL;
+  s->pending_cap = bytes;
+  return GA_OK;
+}
+
 extern "C" int ga_server_set_step_windows(ga_server* s, uint32_t max_windows) {
   if (!s || max_windows == 0) return GA_EINVAL;
   s->max_windows = max_windows;
@@ -611,12 +620,18 @@ extern "C" int ga_server_submit(ga_server* s, const ga_request* req, uint64_t* t
   if (!s || !req || (req->n_pairs > 0 && (!req->reads || !req->read_off || !req->read_len ||
                                            !req->refs || !req->ref_off || !req->ref_len)))
     return GA_EINVAL;
+  uint64_t bytes = 0;
+  for (uint32_t p = 0; p < req->n_pairs; ++p)
+    bytes += (req->read_len[p] + 3ull) / 4 * 4 + (req->ref_len[p] + 3ull) / 4 * 4;
+  bytes = std::max<uint64_t>(bytes, 4);
+  // Backpressure: the waiting requests' copies are bounded (a request is
+  // always taken when none waits, so any request can get in).
+  if (s->pending_cap && !s->pending.empty() && s->pending_bytes + bytes > s->pending_cap)
+    return GA_EAGAIN;
   Request* r = new Request();
   r->n = req->n_pairs;
   r->tag = req->tag;
-  uint64_t bytes = 0;
-  for (uint32_t p = 0; p < r->n; ++p) bytes += (req->read_len[p] + 3ull) / 4 * 4 + (req->ref_len[p] + 3ull) / 4 * 4;
-  r->ascii_bytes = std::max<uint64_t>(bytes, 4);
+  r->ascii_bytes = bytes;
   if (!s->ascii_pool.empty()) {
     r->ascii.swap(s->ascii_pool.back());
     s->ascii_pool.pop_back();
@@ -651,6 +666,7 @@ extern "C" int ga_server_submit(ga_server* s, const ga_request* req, uint64_t* t
   r->ticket = s->next_ticket++;
   r->t_submit = now_ms(s->t0);
   s->pending.push_back(r);
+  s->pending_bytes += r->ascii_bytes;
   if (ticket) *ticket = r->ticket;
   return GA_OK;
 }
@@ -681,6 +697,7 @@ int admit(ga_server* s, std::vector<Request*>& finished) {
     if (r->n == 0) {
       r->t_admit = now_ms(s->t0);
       finished.push_back(r);
+      s->pending_bytes -= r->ascii_bytes;
       s->pending.pop_front();
       continue;
     }
@@ -724,6 +741,7 @@ int admit(ga_server* s, std::vector<Request*>& finished) {
     }
     staged += abytes;
     any = true;
+    s->pending_bytes -= r->ascii_bytes;
     s->pending.pop_front();
   }
   if (!any) return GA_OK;

@@ -5,9 +5,9 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import (OP_CHARS, ga_request, ga_server_create, ga_server_destroy, ga_server_pending,
-               ga_server_poll, ga_server_release, ga_server_set_step_windows, ga_server_step,
-               ga_server_submit)
+from . import (GA_EAGAIN, OP_CHARS, GenasmError, ga_request, ga_server_create, ga_server_destroy,
+               ga_server_pending, ga_server_poll, ga_server_release, ga_server_set_pending_limit,
+               ga_server_set_step_windows, ga_server_step, ga_server_submit)
 
 
 class RequestResult:
@@ -37,11 +37,14 @@ class Server:
     """An alignment server on the current CUDA device."""
 
     def __init__(self, budget_bytes: int, W: int = 64, O: int = 24, k: int = 64,
-                 step_windows: int | None = None):
+                 step_windows: int | None = None, pending_limit: int | None = None):
         self.handle = ga_server_create(budget_bytes, W, O, k)
         if step_windows:
             ga_server_set_step_windows(self.handle, step_windows)
+        if pending_limit is not None:
+            ga_server_set_pending_limit(self.handle, pending_limit)
         self._keep = {}
+        self.refusals = 0  # submissions refused for the pending limit (then retried)
 
     def submit(self, batch, tag: int = 0) -> int:
         """Queues every pair of a datagen.Batch (host ASCII) as one request."""
@@ -50,7 +53,14 @@ class Server:
                   np.ascontiguousarray(batch.ref_off, np.uint64),
                   np.ascontiguousarray(batch.ref_len, np.uint32)]
         req = ga_request(batch.n_pairs, *[a.ctypes.data for a in arrays], tag)
-        return ga_server_submit(self.handle, req)  # the server copies the request
+        while True:  # the server copies the request; at its pending limit, step and retry
+            try:
+                return ga_server_submit(self.handle, req)
+            except GenasmError as e:
+                if e.code != GA_EAGAIN:
+                    raise
+                self.refusals += 1
+                self.step()
 
     def step(self) -> int:
         return ga_server_step(self.handle)

@@ -157,6 +157,25 @@ def test_empty_request_between_real_ones():
     check_against_oracle(batches[1], got[2])
 
 
+def test_pending_limit_refuses_then_takes_every_request():
+    # A pending limit below one request's size: while a request waits for
+    # admission every other submission is refused (GA_EAGAIN, nothing copied);
+    # the wrapper then steps (admitting the waiting one) and submits again.
+    # Every result still equals the oracle.
+    batches = request_batches(8, seed=17)
+    srv = Server(1 << 30, step_windows=16, pending_limit=1)
+    tickets = [srv.submit(b, tag=t) for t, b in enumerate(batches)]
+    assert len(set(tickets)) == len(batches)
+    assert srv.refusals >= len(batches) - 1
+    got = drain(srv, len(batches))
+    waiting, active, _ = srv.pending()
+    srv.close()
+    assert sorted(got) == list(range(len(batches)))
+    assert waiting == 0 and active == 0
+    for t, r in got.items():
+        check_against_oracle(batches[t], r)
+
+
 def test_oversize_request_refused():
     srv = Server(1 << 30)
     big = datagen.from_pairs([("A" * 10_000_000, "C" * 10_000_000)])  # more runs than a step can return
